@@ -1,0 +1,197 @@
+/*
+ * tnc.h -- C ABI of the GB300 tensor-network amplitude executor.
+ *
+ * The executor computes quantum-circuit amplitudes <x| C |0...0> by
+ * contracting the circuit's tensor network along a contraction tree found by
+ * the separator method of Wahl & Strelchuk, "Simulating quantum circuits using
+ * efficient tensor network contraction algorithms with subexponential upper
+ * bound" (arXiv 2208.01498):
+ *
+ *   - the network is the one of the "Classical Simulation of Quantum
+ *     Circuits" section: two-qubit gates are rank-4 tensors, single-qubit
+ *     gates and the boundary vectors are absorbed into them, and each
+ *     two-qubit gate is split by an SVD into two rank-3 tensors joined by a
+ *     bond (proof of Thm. 2);
+ *   - the tree is the separator hierarchy of the proof of Thm. 1, built with
+ *     the Sphere Separator Algorithm (Algorithm 1, Supplemental Material),
+ *     with greedy contraction of the bottom clusters ("Numerical
+ *     implementation" section); index slicing (named as future work in the
+ *     Conclusion) bounds its memory;
+ *   - every tree node is a pairwise contraction costing 2 M scalar operations,
+ *     M the product of the dimensions of all indices of both operands
+ *     (Eq. 3); the executor runs each node on one GPU as a complex GEMM.
+ *
+ * Conventions.  Qubit q has coordinates coords[q*dim .. q*dim+dim).  A gate
+ * matrix is row-major complex (interleaved re, im), rows = outputs; a
+ * two-qubit gate on (a, b) acts on |x_a x_b> with x_a the most significant
+ * bit.  A bitstring is n_qubits bytes, entry q = value (0/1) of qubit q.
+ * Amplitudes are complex128 out[b][j] (interleaved re, im); bit i of j is the
+ * value of open qubit open_qubits[i] after they are sorted ascending.
+ *
+ * Errors.  Every int-returning call returns TNC_OK (0) or a negative status;
+ * tnc_last_error() describes the last failure of the calling thread.
+ * Threading.  A plan may be used by one thread at a time; a server is
+ * thread-safe.
+ */
+#ifndef TNC_H
+#define TNC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- status */
+#define TNC_OK 0
+#define TNC_EINVAL (-1)   /* bad argument: qubit, gate shape, sizes, NULL */
+#define TNC_ENOMEM (-2)   /* plan over mem_cap even after slicing, or ws too small */
+#define TNC_ECUDA (-3)    /* a CUDA runtime call failed */
+#define TNC_ETIMEOUT (-4) /* a bounded device or host wait gave up */
+#define TNC_EBUSY (-5)    /* admission refused: server full */
+#define TNC_ESTATE (-6)   /* call not valid in the object's current state */
+#define TNC_ENOTFOUND (-7)/* unknown server ticket */
+
+/* contraction forms (precision of the pairwise contractions) */
+#define TNC_FP32 0        /* complex64 in/out, FP32 CUDA-core products  */
+#define TNC_3XTF32 1      /* hi/lo TF32 split, 3 products, tensor cores */
+#define TNC_SPLIT_BF16 2  /* hi/lo BF16 split, 3 products, tensor cores */
+
+typedef struct tnc_network tnc_network_t;
+typedef struct tnc_plan tnc_plan_t;
+typedef struct tnc_server tnc_server_t;
+
+/* A circuit as plain data.  The library copies everything it needs. */
+typedef struct {
+  int n_qubits;          /* >= 1 */
+  int dim;               /* embedding dimension of the qubit layout, 1..3 */
+  const double* coords;  /* [n_qubits][dim] */
+  int n_gates;           /* >= 0, in time order */
+  const int* arity;      /* [n_gates], each 1 or 2 */
+  const int* qubits;     /* concatenated qubit lists, sum(arity) entries */
+  const double* mats;    /* concatenated row-major 2x2 / 4x4 complex, FP64 */
+} tnc_network_desc;
+
+typedef struct {
+  int n_open;               /* number of open output qubits (<= 20) */
+  const int* open_qubits;   /* [n_open], any order, distinct */
+  int max_batch;            /* bitstrings per call, 1..65536 (rounded up to 2^k) */
+  size_t mem_cap_bytes;     /* cap on the workspace; 0 = no cap */
+  int form;                 /* TNC_FP32, TNC_3XTF32 or TNC_SPLIT_BF16 */
+  uint64_t seed;            /* seed of the randomised separator search */
+  int ssa_trials;           /* great circles tried per separator (Alg. 1 step 7) */
+  int leaf_size;            /* clusters of at most this many tensors are contracted greedily */
+  int max_group_log2;       /* at most 2^k slices run together in one launch per node */
+} tnc_plan_opts;
+
+typedef struct {
+  double paper_ops;     /* sum over nodes and slices of 2 M (Eq. 3) */
+  double real_flops;    /* 8 M per node and slice: real FP32 flops of the complex products */
+  double bytes;         /* sum over GEMM nodes and slices of 8 (|A| + |B| + |C|) */
+  double peak_bytes;    /* largest live set of intermediates of one slice group */
+  size_t ws_bytes;      /* workspace needed by tnc_contract_amplitudes */
+  double n_slices;      /* total number of slices (2^|S|) */
+  int n_slice_groups;   /* serial iterations (2^|S_serial|) */
+  int n_sliced;         /* |S| */
+  int n_nodes;          /* contraction steps per slice group */
+  int n_leaves;         /* tensors of the network */
+  int max_rank;         /* log2 of the largest intermediate (elements) */
+  int n_launches;       /* kernel launches per slice group */
+  double plan_ms;       /* host time spent planning */
+  double tree_cost_log2;/* log2 of the unsliced tree's paper_ops */
+} tnc_plan_report;
+
+/* Human-readable name of a status code. */
+const char* tnc_status_string(int status);
+/* Message of the last failure on the calling thread ("" if none). */
+const char* tnc_last_error(void);
+
+/* Build the tensor network of <x| C |0> (Classical Simulation section;
+ * Thm. 2 proof for the SVD split).  desc and its arrays are only read during
+ * the call.  *out is owned by the caller (tnc_free_network).
+ * TNC_EINVAL for a qubit out of range, a repeated qubit in a gate, arity not
+ * in {1, 2}, dim not in 1..3 or non-finite numbers. */
+int tnc_load_network(const tnc_network_desc* desc, tnc_network_t** out);
+void tnc_free_network(tnc_network_t* net);
+
+/* Fill *opts with defaults (no open qubits, batch 1, no cap, FP32, 32
+ * trials, leaf size 8, group log2 6). */
+void tnc_plan_opts_default(tnc_plan_opts* opts);
+
+/* Plan the contraction (host only, no GPU needed): separator hierarchy
+ * (Thm. 1 proof, Algorithm 1), greedy leaves, index slicing to meet
+ * mem_cap_bytes, and the compiled node program.  The plan keeps what it needs
+ * from net; net may be freed afterwards.  rep may be NULL.
+ * TNC_ENOMEM if no slicing meets the cap; TNC_EINVAL for bad options. */
+int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** out,
+             tnc_plan_report* rep);
+void tnc_free_plan(tnc_plan_t* plan);
+
+/* Report of an existing plan. */
+int tnc_plan_get_report(const tnc_plan_t* plan, tnc_plan_report* rep);
+
+/* JSON description of the plan for host-side checks: leaves (labels and
+ * FP64 values), tree nodes (children, output labels), sliced labels, batch
+ * and open labels.  Writes at most cap bytes (NUL-terminated) into buf and
+ * the full size (without NUL) into *needed.  buf may be NULL to query. */
+int tnc_plan_export_json(const tnc_plan_t* plan, char* buf, size_t cap, size_t* needed);
+
+/* Copy the plan's leaf tensors and node descriptors to the current CUDA
+ * device (device memory owned by the plan, freed by tnc_free_plan).  Called
+ * automatically by the first contraction if needed.  stream may be NULL. */
+int tnc_plan_upload(tnc_plan_t* plan, void* cuda_stream);
+
+/* Amplitudes for `batch` bitstrings (1 <= batch <= max_batch).
+ * bits: HOST uint8 [batch][n_qubits]; entries of open qubits are ignored.
+ * d_out: DEVICE complex128 [batch][2^n_open], caller-owned, overwritten.
+ * d_ws: DEVICE workspace of ws_bytes >= report.ws_bytes, caller-owned,
+ *       256-byte aligned; its contents are scratch.
+ * Enqueued on cuda_stream (NULL = legacy default stream); asynchronous with
+ * respect to the host except for the staging of bits, which is copied before
+ * the call returns.  TNC_ENOMEM if ws_bytes is too small. */
+int tnc_contract_amplitudes(tnc_plan_t* plan, const uint8_t* bits, int batch, void* d_out,
+                            void* d_ws, size_t ws_bytes, void* cuda_stream);
+
+/* Same, with bits already in DEVICE memory (uint8 [batch][n_qubits]). */
+int tnc_contract_amplitudes_dbits(tnc_plan_t* plan, const uint8_t* d_bits, int batch,
+                                  void* d_out, void* d_ws, size_t ws_bytes, void* cuda_stream);
+
+/* Partial sum over the serial slice groups [group_begin, group_end) only
+ * (0 <= begin <= end <= n_slice_groups): the slice-sharded form used when
+ * several processes each own a range of slices; the partial results add up
+ * (FP64) to the amplitudes.  d_bits in DEVICE memory. */
+int tnc_contract_partial(tnc_plan_t* plan, const uint8_t* d_bits, int batch, int group_begin,
+                         int group_end, void* d_out, void* d_ws, size_t ws_bytes,
+                         void* cuda_stream);
+
+/* ------------------------------------------------------------- serving --
+ * A server owns a host thread and a pool of CUDA streams.  Requests
+ * (plan, bitstrings) are admitted in arrival order while the sum of their
+ * planned workspace bytes fits in the caller-provided device arena; admitted
+ * requests run concurrently on separate streams (continuous batching), and a
+ * finished request frees its bytes for the next.  d_arena (DEVICE,
+ * arena_bytes, 256-byte aligned) stays owned by the caller and must outlive
+ * the server. */
+int tnc_server_create(void* d_arena, size_t arena_bytes, int n_streams, tnc_server_t** out);
+/* Submit a request.  bits (HOST, [batch][n_qubits]) are copied before
+ * returning.  d_out (DEVICE complex128 [batch][2^n_open]) must stay valid
+ * until the request is done.  TNC_EBUSY if the request can never fit the
+ * arena or the queue holds max_queue requests. */
+int tnc_server_submit(tnc_server_t* srv, tnc_plan_t* plan, const uint8_t* bits, int batch,
+                      void* d_out, uint64_t* ticket);
+/* *done = 1 when the result is in d_out (0 otherwise); also returns the
+ * request's status once done.  TNC_ENOTFOUND for an unknown ticket. */
+int tnc_server_poll(tnc_server_t* srv, uint64_t ticket, int* done);
+/* Wait (bounded by timeout_ms) for a ticket; TNC_ETIMEOUT on expiry.
+ * latency_ms (may be NULL) receives submit-to-completion time. */
+int tnc_server_wait(tnc_server_t* srv, uint64_t ticket, int timeout_ms, double* latency_ms);
+/* Cancel a queued (not yet admitted) request: TNC_ESTATE if already running. */
+int tnc_server_cancel(tnc_server_t* srv, uint64_t ticket);
+/* Finish the running requests, drop the queued ones, join the thread. */
+int tnc_server_destroy(tnc_server_t* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNC_H */

@@ -1,0 +1,469 @@
+// C ABI entry points (include/tnc.h): network loading, planning, device
+// upload and the executor loop over slice groups.
+#include <cuda_runtime_api.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <sstream>
+#include <string>
+
+#include "tnc_internal.h"
+
+
+namespace tnc {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return TNC_ECUDA;
+}
+
+// Planning view: fixed final wires are replaced by the beta bits of the
+// bitstring batch; open final wires and beta bits survive to the root.
+static void make_plan_net(const Network& net, const std::vector<int>& open_q, int beta_bits,
+                          PlanNet& pn, std::vector<int>& beta_labels) {
+  pn = PlanNet();
+  pn.dim = net.dim;
+  pn.n_leaves = (int)net.leaves.size();
+  int nlab = (int)net.label_kind.size();
+  beta_labels.clear();
+  for (int b = 0; b < beta_bits; ++b) beta_labels.push_back(nlab + b);
+  pn.n_labels = nlab + beta_bits;
+  std::vector<char> is_open(net.n_qubits, 0);
+  for (int q : open_q) is_open[q] = 1;
+  std::vector<char> fixed_final(nlab, 0);
+  for (int q = 0; q < net.n_qubits; ++q)
+    if (!is_open[q]) fixed_final[net.final_label[q]] = 1;
+  pn.leaf_labels.resize(pn.n_leaves);
+  pn.pos.resize(pn.n_leaves);
+  pn.radius.resize(pn.n_leaves);
+  for (int l = 0; l < pn.n_leaves; ++l) {
+    const Leaf& L = net.leaves[l];
+    bool has_fixed = false;
+    for (int x : L.labels) {
+      if (fixed_final[x])
+        has_fixed = true;
+      else
+        pn.leaf_labels[l].push_back(x);
+    }
+    if (has_fixed)
+      for (int x : beta_labels) pn.leaf_labels[l].push_back(x);
+    for (int k = 0; k < 3; ++k) pn.pos[l][k] = L.pos[k];
+    pn.radius[l] = L.radius;
+  }
+  pn.holders.assign(pn.n_labels, {});
+  for (int l = 0; l < pn.n_leaves; ++l)
+    for (int x : pn.leaf_labels[l]) pn.holders[x].push_back(l);
+  pn.global_out.assign(pn.n_labels, 0);
+  for (int x : beta_labels) pn.global_out[x] = 1;
+  for (int q : open_q) pn.global_out[net.final_label[q]] = 1;
+}
+
+static void fill_report(Plan& p, double plan_ms) {
+  tnc_plan_report& r = p.rep;
+  const double groups = std::exp2((double)p.sliced_serial.size());
+  r.paper_ops = p.prog.paper_ops_per_group * groups;
+  r.real_flops = p.prog.flops_per_group * groups;
+  r.bytes = p.prog.bytes_per_group * groups;
+  r.peak_bytes = p.prog.peak_bytes;
+  r.ws_bytes = p.prog.ws_bytes;
+  r.n_sliced = (int)(p.sliced_serial.size() + p.sliced_par.size());
+  r.n_slices = std::exp2((double)r.n_sliced);
+  r.n_slice_groups = (int)groups;
+  int nodes = 0;
+  for (auto& s : p.prog.steps) nodes += s.kind == ST_GEMM;
+  r.n_nodes = nodes;
+  r.n_leaves = (int)p.net.leaves.size();
+  r.max_rank = p.prog.max_rank;
+  r.n_launches = (int)p.prog.steps.size() + 3;
+  r.plan_ms = plan_ms;
+}
+
+}  // namespace tnc
+
+using namespace tnc;
+
+extern "C" {
+
+const char* tnc_status_string(int s) {
+  switch (s) {
+    case TNC_OK: return "ok";
+    case TNC_EINVAL: return "invalid argument";
+    case TNC_ENOMEM: return "out of memory / workspace too small";
+    case TNC_ECUDA: return "CUDA error";
+    case TNC_ETIMEOUT: return "timed out";
+    case TNC_EBUSY: return "busy";
+    case TNC_ESTATE: return "invalid state";
+    case TNC_ENOTFOUND: return "not found";
+    default: return "unknown status";
+  }
+}
+
+const char* tnc_last_error(void) { return g_err.c_str(); }
+
+int tnc_load_network(const tnc_network_desc* desc, tnc_network_t** out) {
+  if (!out) {
+    set_error("tnc_load_network: out is NULL");
+    return TNC_EINVAL;
+  }
+  *out = nullptr;
+  auto* n = new tnc_network();
+  int rc = build_network(desc, &n->net);
+  if (rc != TNC_OK) {
+    delete n;
+    return rc;
+  }
+  *out = n;
+  return TNC_OK;
+}
+
+void tnc_free_network(tnc_network_t* net) { delete net; }
+
+void tnc_plan_opts_default(tnc_plan_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->max_batch = 1;
+  o->form = TNC_FP32;
+  o->seed = 1;
+  o->ssa_trials = 32;
+  o->leaf_size = 8;
+  o->max_group_log2 = 6;
+}
+
+int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** out, tnc_plan_report* rep) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!net || !opts || !out) {
+    set_error("tnc_plan: NULL argument");
+    return TNC_EINVAL;
+  }
+  *out = nullptr;
+  const Network& N = net->net;
+  if (opts->n_open < 0 || opts->n_open > 20 || (opts->n_open > 0 && !opts->open_qubits) ||
+      opts->max_batch < 1 || opts->max_batch > 65536 || opts->form < 0 || opts->form > 2 ||
+      opts->ssa_trials < 0 || opts->leaf_size < 0 || opts->max_group_log2 < 0 ||
+      opts->max_group_log2 > 16) {
+    set_error("tnc_plan: invalid options");
+    return TNC_EINVAL;
+  }
+  std::vector<int> oq(opts->open_qubits, opts->open_qubits + opts->n_open);
+  std::sort(oq.begin(), oq.end());
+  for (size_t i = 0; i < oq.size(); ++i)
+    if (oq[i] < 0 || oq[i] >= N.n_qubits || (i && oq[i] == oq[i - 1])) {
+      set_error("tnc_plan: invalid open qubit list");
+      return TNC_EINVAL;
+    }
+  auto* tp = new struct tnc_plan();
+  Plan& p = tp->p;
+  p.net = N;
+  p.opts = *opts;
+  p.opts.open_qubits = nullptr;
+  p.open_qubits = oq;
+  if (p.opts.ssa_trials == 0) p.opts.ssa_trials = 32;
+  if (p.opts.leaf_size == 0) p.opts.leaf_size = 8;
+  int bb = 0;
+  while ((1 << bb) < opts->max_batch) ++bb;
+  p.beta_bits = bb;
+  make_plan_net(p.net, p.open_qubits, bb, p.pn, p.beta_labels);
+  PlannerOpts po;
+  po.seed = opts->seed;
+  po.trials = p.opts.ssa_trials;
+  po.leaf_size = p.opts.leaf_size;
+  PlannerStats st;
+  p.tree = plan_tree(p.pn, po, &st);
+  p.rep.tree_cost_log2 = tree_cost_log2(p.tree);
+  int rc = plan_slices(p, opts->mem_cap_bytes);
+  if (rc == TNC_OK) rc = compile_program(p);
+  if (rc == TNC_OK && opts->mem_cap_bytes && p.prog.ws_bytes > opts->mem_cap_bytes * 1.5 + (1 << 20)) {
+    // the compiled arena can exceed the model by fragmentation; stay honest
+    set_error("tnc_plan: compiled workspace %.3g B exceeds mem_cap_bytes", (double)p.prog.ws_bytes);
+    rc = TNC_ENOMEM;
+  }
+  if (rc != TNC_OK) {
+    delete tp;
+    return rc;
+  }
+  double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  fill_report(p, ms);
+  if (rep) *rep = p.rep;
+  *out = tp;
+  return TNC_OK;
+}
+
+int tnc_plan_get_report(const tnc_plan_t* plan, tnc_plan_report* rep) {
+  if (!plan || !rep) {
+    set_error("tnc_plan_get_report: NULL argument");
+    return TNC_EINVAL;
+  }
+  *rep = plan->p.rep;
+  return TNC_OK;
+}
+
+void tnc_free_plan(tnc_plan_t* plan) {
+  if (!plan) return;
+  Plan& p = plan->p;
+  if (p.d_base || p.d_gathers) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (p.device >= 0) cudaSetDevice(p.device);
+    if (p.d_base) cudaFree(p.d_base);
+    if (p.d_gathers) cudaFree(p.d_gathers);
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  delete plan;
+}
+
+int tnc_plan_export_json(const tnc_plan_t* plan, char* buf, size_t cap, size_t* needed) {
+  if (!plan) {
+    set_error("tnc_plan_export_json: NULL plan");
+    return TNC_EINVAL;
+  }
+  const Plan& p = plan->p;
+  std::ostringstream o;
+  o.precision(17);
+  auto vec = [&](const std::vector<int>& v) {
+    o << "[";
+    for (size_t i = 0; i < v.size(); ++i) o << (i ? "," : "") << v[i];
+    o << "]";
+  };
+  o << "{\"n_qubits\":" << p.net.n_qubits << ",\"beta_bits\":" << p.beta_bits;
+  o << ",\"beta_labels\":";
+  vec(p.beta_labels);
+  o << ",\"open_qubits\":";
+  vec(p.open_qubits);
+  o << ",\"final_label\":";
+  vec(p.net.final_label);
+  o << ",\"sliced_serial\":";
+  vec(p.sliced_serial);
+  o << ",\"sliced_par\":";
+  vec(p.sliced_par);
+  o << ",\"leaves\":[";
+  for (size_t l = 0; l < p.net.leaves.size(); ++l) {
+    const Leaf& L = p.net.leaves[l];
+    o << (l ? "," : "") << "{\"labels\":";
+    vec(L.labels);
+    o << ",\"qubit\":" << L.qubit << ",\"re\":[";
+    for (size_t i = 0; i < L.data.size(); ++i) o << (i ? "," : "") << L.data[i].real();
+    o << "],\"im\":[";
+    for (size_t i = 0; i < L.data.size(); ++i) o << (i ? "," : "") << L.data[i].imag();
+    o << "]}";
+  }
+  o << "],\"nodes\":[";
+  for (size_t v = 0; v < p.tree.nodes.size(); ++v) {
+    const TreeNode& nd = p.tree.nodes[v];
+    o << (v ? "," : "") << "{\"left\":" << nd.left << ",\"right\":" << nd.right
+      << ",\"leaf\":" << nd.leaf << ",\"cost_log2\":" << nd.cost_log2 << ",\"out\":";
+    vec(nd.out);
+    o << "}";
+  }
+  o << "],\"root\":" << p.tree.root;
+  // the compiled program, for host-side emulation
+  const Program& pr = p.prog;
+  o << ",\"program\":{\"ws_bytes\":" << pr.ws_bytes << ",\"off_bits\":" << pr.off_bits
+    << ",\"off_ctr\":" << pr.off_ctr << ",\"n_groups\":" << p.rep.n_slice_groups << ",\"base_re\":[";
+  for (size_t i = 0; i < pr.base_host.size(); ++i) o << (i ? "," : "") << pr.base_host[i].real();
+  o << "],\"base_im\":[";
+  for (size_t i = 0; i < pr.base_host.size(); ++i) o << (i ? "," : "") << pr.base_host[i].imag();
+  o << "],\"gathers\":[";
+  for (size_t i = 0; i < pr.gathers.size(); ++i) {
+    const GatherDesc& g = pr.gathers[i];
+    o << (i ? "," : "") << "{\"src\":" << g.src << ",\"dst\":" << g.dst << ",\"out_src\":[";
+    for (int j = 0; j < g.out_rank; ++j) o << (j ? "," : "") << (int)g.out_src[j];
+    o << "],\"fixed_pos\":[";
+    for (int j = 0; j < g.n_fixed; ++j) o << (j ? "," : "") << (int)g.fixed_pos[j];
+    o << "],\"fixed_qubit\":[";
+    for (int j = 0; j < g.n_fixed; ++j) o << (j ? "," : "") << (int)g.fixed_qubit[j];
+    o << "],\"sliced_pos\":[";
+    for (int j = 0; j < g.n_sliced; ++j) o << (j ? "," : "") << (int)g.sliced_pos[j];
+    o << "],\"sliced_bit\":[";
+    for (int j = 0; j < g.n_sliced; ++j) o << (j ? "," : "") << (int)g.sliced_bit[j];
+    o << "]}";
+  }
+  o << "],\"accum\":{\"src\":" << pr.accum.src << ",\"n_open\":" << pr.accum.n_open
+    << ",\"n_beta\":" << pr.accum.n_beta << ",\"n_par\":" << pr.accum.n_par << ",\"role\":[";
+  for (int j = 0; j < pr.accum.rank; ++j) o << (j ? "," : "") << (int)pr.accum.role[j];
+  o << "],\"idx\":[";
+  for (int j = 0; j < pr.accum.rank; ++j) o << (j ? "," : "") << (int)pr.accum.idx[j];
+  o << "]}}";
+  o << ",\"steps\":[";
+  for (size_t i = 0; i < p.prog.steps.size(); ++i) {
+    const Step& s = p.prog.steps[i];
+    o << (i ? "," : "") << "{\"kind\":" << s.kind << ",\"node\":" << s.node;
+    if (s.kind == ST_GEMM) {
+      o << ",\"batch\":" << s.gemm.batch << ",\"M\":" << s.gemm.M << ",\"N\":" << s.gemm.N
+        << ",\"K\":" << s.gemm.K << ",\"kernel\":" << s.gemm.kernel << ",\"tA\":" << s.gemm.transA
+        << ",\"tB\":" << s.gemm.transB << ",\"a\":" << s.gemm.a << ",\"b\":" << s.gemm.b
+        << ",\"c\":" << s.gemm.c << ",\"a_buf\":" << s.gemm.a_buf << ",\"b_buf\":" << s.gemm.b_buf;
+    } else {
+      o << ",\"rank\":" << s.perm.rank << ",\"src\":" << s.perm.src << ",\"dst\":" << s.perm.dst
+        << ",\"src_bit\":[";
+      for (int j = 0; j < s.perm.rank; ++j) o << (j ? "," : "") << (int)s.perm.src_bit[j];
+      o << "]";
+    }
+    o << "}";
+  }
+  o << "]}";
+  std::string s = o.str();
+  if (needed) *needed = s.size();
+  if (buf && cap) {
+    size_t n = std::min(cap - 1, s.size());
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
+  return TNC_OK;
+}
+
+int tnc_plan_upload(tnc_plan_t* plan, void* stream) {
+  if (!plan) {
+    set_error("tnc_plan_upload: NULL plan");
+    return TNC_EINVAL;
+  }
+  Plan& p = plan->p;
+  std::lock_guard<std::mutex> lk(p.mu);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: cudaGetDevice");
+  if (p.d_base && p.device == dev) return TNC_OK;
+  if (p.d_base) {
+    set_error("tnc_plan_upload: plan already resident on device %d", p.device);
+    return TNC_ESTATE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t bb = std::max<size_t>(p.prog.base_elems * 8, 256);
+  e = cudaMalloc(&p.d_base, bb);
+  if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: cudaMalloc");
+  size_t gb = std::max<size_t>(p.prog.gathers.size() * sizeof(GatherDesc), 256);
+  e = cudaMalloc(&p.d_gathers, gb);
+  if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: cudaMalloc");
+  if (p.prog.base_elems) {
+    e = cudaMemcpyAsync(p.d_base, p.prog.base_host.data(), p.prog.base_elems * 8, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: copy leaves");
+  }
+  if (!p.prog.gathers.empty()) {
+    e = cudaMemcpyAsync(p.d_gathers, p.prog.gathers.data(), p.prog.gathers.size() * sizeof(GatherDesc),
+                        cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: copy descriptors");
+  }
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: sync");
+  p.device = dev;
+  return TNC_OK;
+}
+
+// The executor: per serial slice group set the counter, gather the derived
+// leaves, run the node program, accumulate the root in FP64.
+static int run(tnc_plan_t* tp, const uint8_t* bits, bool bits_on_device, int batch, int g0, int g1, void* d_out,
+               void* d_ws, size_t ws_bytes, void* stream) {
+  Plan& p = tp->p;
+  if (!d_out || !d_ws || !bits) {
+    set_error("tnc_contract: NULL pointer argument");
+    return TNC_EINVAL;
+  }
+  const int maxb = 1 << p.beta_bits;
+  if (batch < 1 || batch > maxb || batch > std::max(1, p.opts.max_batch)) {
+    set_error("tnc_contract: batch %d outside 1..%d", batch, p.opts.max_batch);
+    return TNC_EINVAL;
+  }
+  if (ws_bytes < p.prog.ws_bytes) {
+    set_error("tnc_contract: workspace of %zu bytes < required %llu", ws_bytes,
+              (unsigned long long)p.prog.ws_bytes);
+    return TNC_ENOMEM;
+  }
+  if (((uintptr_t)d_ws & 255) != 0) {
+    set_error("tnc_contract: workspace not 256-byte aligned");
+    return TNC_EINVAL;
+  }
+  const int ngroups = p.rep.n_slice_groups;
+  if (g0 < 0 || g1 < g0 || g1 > ngroups) {
+    set_error("tnc_contract: slice groups [%d, %d) outside [0, %d)", g0, g1, ngroups);
+    return TNC_EINVAL;
+  }
+  int rc = tnc_plan_upload(tp, stream);
+  if (rc != TNC_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)d_ws;
+  const int nq = p.net.n_qubits;
+  cudaError_t e;
+  // stage the bitstrings (zero-padded to the padded batch)
+  e = cudaMemsetAsync(ws + p.prog.off_bits, 0, (size_t)maxb * nq, st);
+  if (e != cudaSuccess) return cuda_fail(e, "tnc_contract: memset");
+  e = cudaMemcpyAsync(ws + p.prog.off_bits, bits, (size_t)batch * nq,
+                      bits_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "tnc_contract: copy bits");
+  const size_t out_bytes = (size_t)batch * ((size_t)16 << p.open_qubits.size());
+  e = cudaMemsetAsync(d_out, 0, out_bytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "tnc_contract: memset out");
+  uint64_t* d_ctr = (uint64_t*)(ws + p.prog.off_ctr);
+  for (int g = g0; g < g1; ++g) {
+    int r;
+    if ((r = launch_set_counter(d_ctr, (uint64_t)g, st))) return cuda_fail((cudaError_t)r, "set counter");
+    if (!p.prog.gathers.empty()) {
+      r = launch_gather((const GatherDesc*)p.d_gathers, (int)p.prog.gathers.size(), p.prog.max_gather_rank,
+                        p.d_base, ws, (const uint8_t*)(ws + p.prog.off_bits), nq, d_ctr, st);
+      if (r) return cuda_fail((cudaError_t)r, "gather");
+    }
+    for (const Step& s : p.prog.steps) {
+      if (s.kind == ST_PERMUTE)
+        r = launch_permute(s.perm, ws, st);
+      else
+        r = launch_gemm(s.gemm, p.d_base, ws, st);
+      if (r) return cuda_fail((cudaError_t)r, s.kind == ST_PERMUTE ? "permute" : "gemm");
+    }
+    r = launch_accum(p.prog.accum, ws, d_out, batch, st);
+    if (r) return cuda_fail((cudaError_t)r, "accum");
+  }
+  return TNC_OK;
+}
+
+}  // extern "C"
+
+namespace tnc {
+int run_request(tnc_plan_t* plan, const uint8_t* host_bits, int batch, void* d_out, void* d_ws, size_t ws_bytes,
+                void* stream) {
+  return run(plan, host_bits, false, batch, 0, plan->p.rep.n_slice_groups, d_out, d_ws, ws_bytes, stream);
+}
+}  // namespace tnc
+
+extern "C" {
+
+int tnc_contract_amplitudes(tnc_plan_t* plan, const uint8_t* bits, int batch, void* d_out, void* d_ws,
+                            size_t ws_bytes, void* stream) {
+  if (!plan) {
+    set_error("tnc_contract_amplitudes: NULL plan");
+    return TNC_EINVAL;
+  }
+  return run(plan, bits, false, batch, 0, plan->p.rep.n_slice_groups, d_out, d_ws, ws_bytes, stream);
+}
+
+int tnc_contract_amplitudes_dbits(tnc_plan_t* plan, const uint8_t* d_bits, int batch, void* d_out, void* d_ws,
+                                  size_t ws_bytes, void* stream) {
+  if (!plan) {
+    set_error("tnc_contract_amplitudes_dbits: NULL plan");
+    return TNC_EINVAL;
+  }
+  return run(plan, d_bits, true, batch, 0, plan->p.rep.n_slice_groups, d_out, d_ws, ws_bytes, stream);
+}
+
+int tnc_contract_partial(tnc_plan_t* plan, const uint8_t* d_bits, int batch, int g0, int g1, void* d_out,
+                         void* d_ws, size_t ws_bytes, void* stream) {
+  if (!plan) {
+    set_error("tnc_contract_partial: NULL plan");
+    return TNC_EINVAL;
+  }
+  return run(plan, d_bits, true, batch, g0, g1, d_out, d_ws, ws_bytes, stream);
+}
+
+}  // extern "C"

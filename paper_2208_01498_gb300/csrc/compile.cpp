@@ -1,0 +1,667 @@
+// Index slicing and the compiled node program.
+//
+// Slicing (the index-slicing approach the paper's Conclusion names as future
+// work): a set S of contracted labels is fixed to each of its 2^|S| value
+// combinations; each combination is an independent network with the same
+// tree, and the amplitudes are the sum over all of them.  Labels are added
+// greedily -- the one that gives the smallest total work among those that
+// lower the peak -- until the live intermediates of one slice fit the cap.
+// Up to 2^max_group_log2 slices then run together ("grouped"): their labels
+// are not fixed but carried as batch indices up to the root, where the final
+// FP64 accumulation sums over them; the rest ("serial") loop on the host.
+//
+// The program of one slice group, in execution order:
+//   gather  -- derived leaves: final wires projected onto the requested bits
+//              (the bitstring index beta becomes a batch index), serial
+//              sliced labels fixed to the group's values;
+//   per tree node (post-order, larger subtree first):
+//     permute -- only when an operand cannot be read as [batch][M][K] or
+//                [batch][K][M] (leaves are stored in whatever order their
+//                consumer wants, so only intermediates are ever permuted);
+//     gemm    -- C[b][m][n] = sum_k A[b][m][k] B[b][k][n] (Eq. 3 node);
+//   accum   -- FP64 sum of the root over the grouped slice labels into the
+//              caller's complex128 output.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <set>
+
+#include "tnc_internal.h"
+
+namespace tnc {
+
+namespace {
+
+constexpr uint64_t kAlign = 256;
+uint64_t align_up(uint64_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// first-fit allocator over [0, inf) used to lay out the arena
+struct Arena {
+  std::map<uint64_t, uint64_t> used;  // offset -> size
+  uint64_t peak = 0;
+  uint64_t alloc(uint64_t bytes) {
+    bytes = align_up(std::max<uint64_t>(bytes, 16));
+    uint64_t cur = 0;
+    for (auto& kv : used) {
+      if (kv.first - cur >= bytes) break;
+      cur = std::max(cur, kv.first + kv.second);
+    }
+    used[cur] = bytes;
+    peak = std::max(peak, cur + bytes);
+    return cur;
+  }
+  void release(uint64_t off) { used.erase(off); }
+};
+
+// Can layout L (labels, most significant first) be read as consecutive
+// blocks g[0], g[1], g[2] (label sets)?  Fills the block-internal orders.
+bool view_as(const std::vector<int>& L, const std::vector<std::set<int>>& g,
+             std::vector<std::vector<int>>& ord) {
+  ord.assign(g.size(), {});
+  size_t pos = 0;
+  for (size_t b = 0; b < g.size(); ++b) {
+    for (size_t k = 0; k < g[b].size(); ++k, ++pos) {
+      if (pos >= L.size() || !g[b].count(L[pos])) return false;
+      ord[b].push_back(L[pos]);
+    }
+  }
+  return pos == L.size();
+}
+
+std::vector<int> concat(std::initializer_list<const std::vector<int>*> parts) {
+  std::vector<int> r;
+  for (auto* p : parts) r.insert(r.end(), p->begin(), p->end());
+  return r;
+}
+
+std::vector<int> sorted_vec(const std::set<int>& s) { return std::vector<int>(s.begin(), s.end()); }
+
+// bit position (from the least significant end) of label x in layout L
+int bitpos(const std::vector<int>& L, int x) {
+  for (size_t i = 0; i < L.size(); ++i)
+    if (L[i] == x) return (int)(L.size() - 1 - i);
+  return -1;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- slicing
+namespace {
+
+struct Eval {
+  double peak_bytes = 0;
+  double cost_log2 = 0;   // log2 of paper ops of one group (all nodes)
+  int peak_node = -1;
+};
+
+// live-memory model of one slice group: post-order, larger subtree first;
+// a node holds its operands, its output and operand copies for a permute
+// (plus the split planes of the tensor-core forms).
+Eval evaluate(const PlanNet& pn, Tree& t, int form) {
+  annotate_tree(pn, t);
+  Eval ev;
+  ev.cost_log2 = tree_cost_log2(t);
+  std::function<double(int, int*)> peak = [&](int v, int* at) -> double {
+    const TreeNode& nd = t.nodes[v];
+    double self = std::exp2((double)nd.out.size()) * 8;
+    if (nd.left < 0) {
+      *at = v;
+      return self;
+    }
+    int al, ar;
+    double pl = peak(nd.left, &al), pr = peak(nd.right, &ar);
+    double sl = std::exp2((double)t.nodes[nd.left].out.size()) * 8;
+    double sr = std::exp2((double)t.nodes[nd.right].out.size()) * 8;
+    double p1 = std::max(pl, sl + pr), p2 = std::max(pr, sr + pl);
+    double first = std::min(p1, p2);
+    int fat = (p1 <= p2) ? (pl >= sl + pr ? al : ar) : (pr >= sr + pl ? ar : al);
+    double work = sl + sr + self + std::max(sl, sr);
+    if (form != TNC_FP32) work += sl + sr + 2 * std::min(sl, sr);
+    if (work >= first) {
+      *at = v;
+      return work;
+    }
+    *at = fat;
+    return first;
+  };
+  int at = -1;
+  ev.peak_bytes = peak(t.root, &at);
+  ev.peak_node = at;
+  return ev;
+}
+
+PlanNet exec_net(const PlanNet& base, const std::vector<int>& ser, const std::vector<int>& par) {
+  PlanNet pn = base;
+  std::vector<char> drop(pn.n_labels, 0);
+  for (int x : ser) drop[x] = 1;
+  for (auto& L : pn.leaf_labels) {
+    std::vector<int> r;
+    for (int x : L)
+      if (!drop[x]) r.push_back(x);
+    L.swap(r);
+  }
+  for (int x : ser) pn.holders[x].clear();
+  for (int x : par) pn.global_out[x] = 1;
+  return pn;
+}
+
+}  // namespace
+
+int plan_slices(Plan& p, size_t cap_bytes) {
+  const PlanNet& base = p.pn;
+  p.sliced_serial.clear();
+  p.sliced_par.clear();
+  const int form = p.opts.form;
+  Tree t = p.tree;
+  PlanNet pn = exec_net(base, {}, {});
+  Eval ev = evaluate(pn, t, form);
+  if (cap_bytes == 0 || ev.peak_bytes <= (double)cap_bytes) return TNC_OK;
+  std::vector<int> S;
+  std::vector<char> in_S(base.n_labels, 0);
+  while (ev.peak_bytes > (double)cap_bytes) {
+    // candidates: contracted labels of the node at the peak and its children
+    std::set<int> cand;
+    auto add = [&](int v) {
+      if (v < 0) return;
+      for (int x : t.nodes[v].out)
+        if (!base.global_out[x] && !in_S[x] && base.holders[x].size() >= 2) cand.insert(x);
+    };
+    add(ev.peak_node);
+    if (ev.peak_node >= 0) {
+      add(t.nodes[ev.peak_node].left);
+      add(t.nodes[ev.peak_node].right);
+    }
+    if (cand.empty()) {
+      // widen to every label of the largest intermediate
+      int big = -1;
+      for (size_t v = 0; v < t.nodes.size(); ++v)
+        if (big < 0 || t.nodes[v].out.size() > t.nodes[big].out.size()) big = (int)v;
+      add(big);
+    }
+    if (cand.empty() || S.size() >= 40) {
+      set_error("tnc_plan: cannot slice the plan under mem_cap_bytes = %zu (peak %.3g bytes)",
+                cap_bytes, ev.peak_bytes);
+      return TNC_ENOMEM;
+    }
+    int best = -1;
+    Eval bev;
+    double best_total = 1e300;
+    for (int x : cand) {
+      std::vector<int> S2 = S;
+      S2.push_back(x);
+      PlanNet pn2 = exec_net(base, S2, {});
+      Tree t2 = p.tree;
+      Eval e2 = evaluate(pn2, t2, form);
+      if (e2.peak_bytes >= ev.peak_bytes) continue;
+      double total = e2.cost_log2 + S2.size();  // log2 of total work
+      if (total < best_total - 1e-9 || (std::fabs(total - best_total) <= 1e-9 && e2.peak_bytes < bev.peak_bytes)) {
+        best_total = total;
+        best = x;
+        bev = e2;
+      }
+    }
+    if (best < 0) {
+      set_error("tnc_plan: slicing does not lower the peak under mem_cap_bytes = %zu", cap_bytes);
+      return TNC_ENOMEM;
+    }
+    S.push_back(best);
+    in_S[best] = 1;
+    PlanNet pn2 = exec_net(base, S, {});
+    t = p.tree;
+    ev = evaluate(pn2, t, form);
+  }
+  // group as many sliced labels as fit (most recently chosen first)
+  std::vector<int> ser = S, par;
+  while (!ser.empty() && (int)par.size() < p.opts.max_group_log2) {
+    std::vector<int> ser2(ser.begin(), ser.end() - 1), par2 = par;
+    par2.push_back(ser.back());
+    PlanNet pn2 = exec_net(base, ser2, par2);
+    Tree t2 = p.tree;
+    Eval e2 = evaluate(pn2, t2, form);
+    if (e2.peak_bytes > (double)cap_bytes) break;
+    ser.swap(ser2);
+    par.swap(par2);
+  }
+  p.sliced_serial = ser;
+  p.sliced_par = par;
+  return TNC_OK;
+}
+
+// ----------------------------------------------------------------- compile
+int compile_program(Plan& p) {
+  Program& pr = p.prog;
+  pr = Program();
+  const Network& net = p.net;
+  // execution view: serial sliced labels removed, grouped ones kept to the root
+  PlanNet pn = exec_net(p.pn, p.sliced_serial, p.sliced_par);
+  Tree& t = p.tree;
+  annotate_tree(pn, t);
+  const int form = p.opts.form;
+
+  std::vector<char> is_open(net.n_qubits, 0);
+  for (int q : p.open_qubits) is_open[q] = 1;
+  std::vector<int> ser_index(pn.n_labels, -1), par_index(pn.n_labels, -1), beta_index(pn.n_labels, -1);
+  for (size_t i = 0; i < p.sliced_serial.size(); ++i) ser_index[p.sliced_serial[i]] = (int)i;
+  for (size_t i = 0; i < p.sliced_par.size(); ++i) par_index[p.sliced_par[i]] = (int)i;
+  for (int b = 0; b < p.beta_bits; ++b) beta_index[p.beta_labels[b]] = b;
+
+  // which leaves need a gather (fixed final wire or serial sliced label)
+  const int nL = pn.n_leaves;
+  std::vector<char> derived(nL, 0);
+  for (int l = 0; l < nL; ++l) {
+    for (int x : net.leaves[l].labels) {
+      if (net.label_kind[x] == LK_FINAL) {
+        int q = net.leaves[l].qubit;
+        // the final label belongs to the qubit whose final wire it is
+        for (int qq = 0; qq < net.n_qubits; ++qq)
+          if (net.final_label[qq] == x) q = qq;
+        if (!is_open[q]) derived[l] = 1;
+      }
+      if (ser_index[x] >= 0) derived[l] = 1;
+    }
+  }
+  if (t.nodes[t.root].left < 0) derived[t.nodes[t.root].leaf] = 1;
+
+  // ws layout: bits | counter | derived leaves | arena
+  const int batch_pad = 1 << p.beta_bits;
+  pr.off_bits = 0;
+  uint64_t off = align_up((uint64_t)batch_pad * net.n_qubits);
+  pr.off_ctr = off;
+  off += kAlign;
+  const uint64_t leaf_area = off;
+
+  // execution order: post-order, the child with the larger subtree peak first
+  std::vector<double> sub_peak(t.nodes.size(), 0);
+  std::function<double(int)> speak = [&](int v) -> double {
+    const TreeNode& nd = t.nodes[v];
+    double self = std::exp2((double)nd.out.size());
+    if (nd.left < 0) return sub_peak[v] = self;
+    double a = speak(nd.left), b = speak(nd.right);
+    double sa = std::exp2((double)t.nodes[nd.left].out.size());
+    double sb = std::exp2((double)t.nodes[nd.right].out.size());
+    return sub_peak[v] = std::max({std::min(std::max(a, sa + b), std::max(b, sb + a)), sa + sb + self});
+  };
+  speak(t.root);
+  std::vector<int> order;
+  std::function<void(int)> post = [&](int v) {
+    const TreeNode& nd = t.nodes[v];
+    if (nd.left < 0) return;
+    int a = nd.left, b = nd.right;
+    double sa = std::exp2((double)t.nodes[a].out.size()), sb = std::exp2((double)t.nodes[b].out.size());
+    if (std::max(sub_peak[a], sa + sub_peak[b]) > std::max(sub_peak[b], sb + sub_peak[a])) std::swap(a, b);
+    post(a);
+    post(b);
+    order.push_back(v);
+  };
+  post(t.root);
+
+  // per-node storage
+  std::vector<std::vector<int>> layout(t.nodes.size());
+  std::vector<int> buf(t.nodes.size(), -1);        // 0 workspace, 1 leaf buffer
+  std::vector<uint64_t> loc(t.nodes.size(), 0);    // element offset
+  std::vector<char> placed(t.nodes.size(), 0);
+  Arena arena;
+  std::vector<std::pair<int, std::vector<int>>> leaf_layout;  // (node, order) chosen by consumers
+  std::vector<int> leaf_nodes_derived;
+  std::vector<Step> steps;
+  // arena offsets are relative; fixed up once the leaf area size is known
+  std::vector<std::pair<size_t, int>> fix_a, fix_b, fix_c;  // (step, which field)
+
+  auto nsize = [&](int v) { return (uint64_t)1 << t.nodes[v].out.size(); };
+
+  // place a leaf node in a chosen order
+  uint64_t leaf_ws_off = 0;   // elements, relative to leaf_area
+  std::vector<cd> base_data;  // assembled leaf buffer (FP64, converted at the end)
+  auto place_leaf = [&](int v, const std::vector<int>& ord) {
+    int l = t.nodes[v].leaf;
+    layout[v] = ord;
+    placed[v] = 1;
+    const Leaf& L = net.leaves[l];
+    if (derived[l]) {
+      GatherDesc g;
+      std::memset(&g, 0, sizeof(g));
+      // base data stored in the original order
+      g.src = base_data.size();
+      base_data.insert(base_data.end(), L.data.begin(), L.data.end());
+      g.dst = leaf_ws_off;  // relative, fixed below
+      g.out_rank = (int)ord.size();
+      g.src_rank = (int)L.labels.size();
+      for (int j = 0; j < g.out_rank; ++j) {
+        int x = ord[ord.size() - 1 - j];
+        if (beta_index[x] >= 0)
+          g.out_src[j] = (int8_t)(-1 - beta_index[x]);
+        else
+          g.out_src[j] = (int8_t)bitpos(L.labels, x);
+      }
+      for (int x : L.labels) {
+        if (net.label_kind[x] == LK_FINAL) {
+          int q = -1;
+          for (int qq = 0; qq < net.n_qubits; ++qq)
+            if (net.final_label[qq] == x) q = qq;
+          if (!is_open[q]) {
+            g.fixed_pos[g.n_fixed] = (int8_t)bitpos(L.labels, x);
+            g.fixed_qubit[g.n_fixed] = (int16_t)q;
+            g.n_fixed++;
+          }
+        }
+        if (ser_index[x] >= 0) {
+          g.sliced_pos[g.n_sliced] = (int8_t)bitpos(L.labels, x);
+          g.sliced_bit[g.n_sliced] = (int8_t)ser_index[x];
+          g.n_sliced++;
+        }
+      }
+      pr.gathers.push_back(g);
+      pr.max_gather_rank = std::max(pr.max_gather_rank, g.out_rank);
+      buf[v] = 0;
+      loc[v] = leaf_ws_off;  // relative to the leaf area
+      leaf_nodes_derived.push_back(v);
+      leaf_ws_off += align_up(((uint64_t)1 << ord.size()) * 8) / 8;
+    } else {
+      // store permuted into the consumer's order
+      const int r = (int)ord.size();
+      std::vector<int> srcbit(r);
+      for (int j = 0; j < r; ++j) srcbit[j] = bitpos(L.labels, ord[r - 1 - j]);
+      uint64_t start = base_data.size();
+      base_data.resize(start + ((uint64_t)1 << r));
+      for (uint64_t o = 0; o < ((uint64_t)1 << r); ++o) {
+        uint64_t i = 0;
+        for (int j = 0; j < r; ++j)
+          if ((o >> j) & 1) i |= (uint64_t)1 << srcbit[j];
+        base_data[start + o] = L.data[i];
+      }
+      // keep 32-byte alignment of every leaf
+      while (base_data.size() % 4) base_data.push_back(0);
+      buf[v] = 1;
+      loc[v] = start;
+    }
+  };
+
+  // record arena offsets as relative-to-arena with a tag (buffer 2)
+  constexpr int BUF_ARENA = 2;
+  std::vector<int> last_use(t.nodes.size(), -1);
+
+  double flops = 0, bytes = 0, pops = 0;
+  for (int v : order) {
+    const TreeNode& nd = t.nodes[v];
+    int x = nd.left, y = nd.right;
+    std::set<int> Lx(t.nodes[x].out.begin(), t.nodes[x].out.end());
+    std::set<int> Ly(t.nodes[y].out.begin(), t.nodes[y].out.end());
+    std::set<int> Lv(nd.out.begin(), nd.out.end());
+    std::set<int> bset, kset, fx, fy;
+    for (int a : Lx) {
+      if (Ly.count(a)) {
+        if (Lv.count(a))
+          bset.insert(a);
+        else
+          kset.insert(a);
+      } else {
+        if (!Lv.count(a)) {
+          set_error("tnc_plan: internal error: label %d summed inside one operand", a);
+          return TNC_EINVAL;
+        }
+        fx.insert(a);
+      }
+    }
+    for (int a : Ly)
+      if (!Lx.count(a)) fy.insert(a);
+    struct Opt {
+      int A, B, tA, tB;
+      double cost;
+      bool permA, permB;
+      std::vector<int> ordA, ordB;  // final operand layouts
+      std::vector<int> b, K, M, N;
+      int kernel_pref;
+    };
+    Opt best;
+    best.cost = 1e300;
+    for (int orient = 0; orient < 2; ++orient) {
+      int A = orient ? y : x, B = orient ? x : y;
+      const std::set<int>& fa = orient ? fy : fx;
+      const std::set<int>& fb = orient ? fx : fy;
+      for (int tA = 0; tA < 2; ++tA)
+        for (int tB = 0; tB < 2; ++tB) {
+          Opt o;
+          o.A = A, o.B = B, o.tA = tA, o.tB = tB;
+          o.permA = o.permB = false;
+          std::vector<std::vector<int>> oa, ob;
+          bool fixA = placed[A], fixB = placed[B];
+          bool okA = !fixA || view_as(layout[A], tA ? std::vector<std::set<int>>{bset, kset, fa}
+                                                  : std::vector<std::set<int>>{bset, fa, kset}, oa);
+          bool okB = !fixB || view_as(layout[B], tB ? std::vector<std::set<int>>{bset, fb, kset}
+                                                  : std::vector<std::set<int>>{bset, kset, fb}, ob);
+          std::vector<int> bA, kA, mA, bB, kB, nB;
+          if (fixA && okA) {
+            bA = oa[0];
+            kA = tA ? oa[1] : oa[2];
+            mA = tA ? oa[2] : oa[1];
+          }
+          if (fixB && okB) {
+            bB = ob[0];
+            kB = tB ? ob[2] : ob[1];
+            nB = tB ? ob[1] : ob[2];
+          }
+          double sA = (double)nsize(A), sB = (double)nsize(B);
+          double cost = 0;
+          if (fixA && !okA) o.permA = true, cost += sA;
+          if (fixB && !okB) o.permB = true, cost += sB;
+          // batch and K orders must agree between two fixed, fitting operands
+          if (fixA && okA && fixB && okB && (bA != bB || kA != kB)) {
+            if (sA <= sB)
+              o.permA = true, cost += sA;
+            else
+              o.permB = true, cost += sB;
+          }
+          // resolve the orders
+          auto good = [&](int side) { return side == 0 ? (fixA && !o.permA) : (fixB && !o.permB); };
+          if (good(0)) {
+            o.b = bA, o.K = kA, o.M = mA;
+          } else if (good(1)) {
+            o.b = bB, o.K = kB;
+          } else {
+            o.b = sorted_vec(bset), o.K = sorted_vec(kset);
+          }
+          if (!good(0)) {
+            // keep the relative order of A's free labels if it had a layout
+            if (fixA) {
+              for (int a : layout[A])
+                if (fa.count(a)) o.M.push_back(a);
+            } else {
+              o.M = sorted_vec(fa);
+            }
+          }
+          if (good(1)) {
+            o.N = nB;
+          } else if (fixB) {
+            for (int a : layout[B])
+              if (fb.count(a)) o.N.push_back(a);
+          } else {
+            o.N = sorted_vec(fb);
+          }
+          o.ordA = tA ? concat({&o.b, &o.K, &o.M}) : concat({&o.b, &o.M, &o.K});
+          o.ordB = tB ? concat({&o.b, &o.N, &o.K}) : concat({&o.b, &o.K, &o.N});
+          // prefer the big free side as A (M >= N), then non-transposed forms
+          double M = std::exp2((double)fa.size()), N = std::exp2((double)fb.size());
+          double tie = (M >= N ? 0 : 0.5) + 0.01 * (tA + tB);
+          o.cost = cost + tie;
+          if (o.cost < best.cost) best = o;
+        }
+    }
+    // emit permutes / place leaves
+    auto prepare = [&](int side) -> void {
+      int c = side == 0 ? best.A : best.B;
+      const std::vector<int>& ord = side == 0 ? best.ordA : best.ordB;
+      bool perm = side == 0 ? best.permA : best.permB;
+      if (!placed[c]) {
+        place_leaf(c, ord);
+        return;
+      }
+      if (!perm) return;
+      Step s;
+      std::memset(&s, 0, sizeof(s));
+      s.kind = ST_PERMUTE;
+      s.node = v;
+      const int r = (int)ord.size();
+      s.perm.rank = r;
+      for (int j = 0; j < r; ++j) s.perm.src_bit[j] = (int8_t)bitpos(layout[c], ord[r - 1 - j]);
+      uint64_t dst = arena.alloc(nsize(c) * 8);
+      s.perm.src = loc[c];
+      s.perm.dst = dst / 8;
+      if (buf[c] != 0 && buf[c] != BUF_ARENA) {
+        set_error("tnc_plan: internal error: permute of a leaf");
+        return;
+      }
+      // src may be in the leaf area (buf 0, relative to leaf area) or arena
+      steps.push_back(s);
+      fix_a.push_back({steps.size() - 1, buf[c] == BUF_ARENA ? 10 : 11});  // perm src tag
+      // the permuted copy replaces the operand; the old copy is freed after the gemm
+      if (buf[c] == BUF_ARENA) last_use[c] = v;
+      layout[c] = ord;
+      buf[c] = BUF_ARENA;
+      loc[c] = dst / 8;
+      // remember the temp to free after the gemm (the original arena block)
+    };
+    // track arena blocks of the operands before permutes to free them later
+    std::vector<uint64_t> to_free;
+    for (int c : {best.A, best.B})
+      if (placed[c] && buf[c] == BUF_ARENA) to_free.push_back(loc[c] * 8);
+    prepare(0);
+    prepare(1);
+    for (int c : {best.A, best.B})
+      if (buf[c] == BUF_ARENA) to_free.push_back(loc[c] * 8);
+    // output
+    uint64_t cbytes = nsize(v) * 8;
+    uint64_t coff = arena.alloc(cbytes);
+    Step s;
+    std::memset(&s, 0, sizeof(s));
+    s.kind = ST_GEMM;
+    s.node = v;
+    GemmDesc& g = s.gemm;
+    g.batch = (int64_t)1 << best.b.size();
+    g.M = (int64_t)1 << best.M.size();
+    g.N = (int64_t)1 << best.N.size();
+    g.K = (int64_t)1 << best.K.size();
+    g.transA = best.tA;
+    g.transB = best.tB;
+    g.a = loc[best.A];
+    g.b = loc[best.B];
+    g.a_buf = buf[best.A];
+    g.b_buf = buf[best.B];
+    g.c = coff / 8;
+    g.form = form;
+    // kernel choice by shape (refined by the autotuner at upload)
+    const double MN = (double)g.M * g.N;
+    if (MN <= 16 && g.K >= 512)
+      g.kernel = KG_DOT;
+    else if (g.N <= 16 && g.K <= 16)
+      g.kernel = KG_NARROW;
+    else if (form != TNC_FP32 && g.M >= 128 && g.N >= 32 && g.K >= 32)
+      g.kernel = KG_TC;
+    else if (g.N <= 32)
+      g.kernel = KG_SIMT_64x32;
+    else
+      g.kernel = KG_SIMT_128x64;
+    // per-node scratch
+    uint64_t scratch_bytes = 0;
+    if (g.kernel == KG_DOT) scratch_bytes = (uint64_t)g.batch * g.M * g.N * 16 * 1024;
+    if (g.kernel == KG_TC) {
+      // hi/lo planes: A (batch*M*2K) x 2 and expanded B' (batch*2N*2K) x 2, 2 or 4 bytes each
+      uint64_t es = form == TNC_SPLIT_BF16 ? 2 : 4;
+      scratch_bytes = (uint64_t)g.batch * (g.M * 2 * g.K * 2 + 2 * g.N * 2 * g.K * 2) * es + 4096;
+    }
+    uint64_t soff = scratch_bytes ? arena.alloc(scratch_bytes) : 0;
+    g.scratch = soff / 8;
+    g.scratch_elems = scratch_bytes / 8;
+    steps.push_back(s);
+    {
+      int tagA = g.a_buf == BUF_ARENA ? 20 : (g.a_buf == 0 ? 21 : 22);
+      int tagB = g.b_buf == BUF_ARENA ? 30 : (g.b_buf == 0 ? 31 : 32);
+      fix_b.push_back({steps.size() - 1, tagA * 100 + tagB});
+    }
+    if (scratch_bytes) arena.release(soff);
+    for (uint64_t f : to_free) arena.release(f);
+    layout[v] = concat({&best.b, &best.M, &best.N});
+    buf[v] = BUF_ARENA;
+    loc[v] = coff / 8;
+    placed[v] = 1;
+    double work = (double)g.batch * g.M * g.N * g.K;
+    flops += 8 * work;
+    pops += 2 * work;
+    bytes += 8.0 * ((double)g.batch * (g.M * g.K + g.K * g.N + g.M * g.N));
+  }
+  if (!placed[t.root]) {
+    // single-leaf network
+    std::vector<int> ord = t.nodes[t.root].out;
+    place_leaf(t.root, ord);
+  }
+
+  // fix up offsets: leaf area size known now
+  const uint64_t leaf_bytes = align_up(leaf_ws_off * 8);
+  const uint64_t arena_base = leaf_area + leaf_bytes;  // bytes
+  for (auto& gd : pr.gathers) gd.dst = leaf_area / 8 + gd.dst;
+  auto abs_off = [&](int b, uint64_t rel) -> uint64_t {
+    if (b == BUF_ARENA) return arena_base / 8 + rel;
+    if (b == 0) return leaf_area / 8 + rel;
+    return rel;
+  };
+  for (auto& f : fix_a) {
+    Step& s = steps[f.first];
+    s.perm.src = abs_off(f.second == 10 ? BUF_ARENA : 0, s.perm.src);
+    s.perm.dst = abs_off(BUF_ARENA, s.perm.dst);
+  }
+  for (auto& f : fix_b) {
+    Step& s = steps[f.first];
+    int tagA = f.second / 100, tagB = f.second % 100;
+    int ba = tagA == 20 ? BUF_ARENA : (tagA == 21 ? 0 : 1);
+    int bb = tagB == 30 ? BUF_ARENA : (tagB == 31 ? 0 : 1);
+    s.gemm.a = abs_off(ba, s.gemm.a);
+    s.gemm.b = abs_off(bb, s.gemm.b);
+    s.gemm.a_buf = ba == 1 ? 1 : 0;
+    s.gemm.b_buf = bb == 1 ? 1 : 0;
+    s.gemm.c = abs_off(BUF_ARENA, s.gemm.c);
+    if (s.gemm.scratch_elems) s.gemm.scratch = abs_off(BUF_ARENA, s.gemm.scratch);
+  }
+  pr.steps = std::move(steps);
+
+  // final accumulation from the root
+  AccumDesc& ad = pr.accum;
+  std::memset(&ad, 0, sizeof(ad));
+  const int root = t.root;
+  ad.src = abs_off(buf[root] == BUF_ARENA ? BUF_ARENA : 0, loc[root]);
+  ad.rank = (int)layout[root].size();
+  ad.n_beta = p.beta_bits;
+  ad.n_open = (int)p.open_qubits.size();
+  ad.n_par = (int)p.sliced_par.size();
+  for (int j = 0; j < ad.rank; ++j) {
+    int x = layout[root][ad.rank - 1 - j];
+    if (beta_index[x] >= 0) {
+      ad.role[j] = 0, ad.idx[j] = (int8_t)beta_index[x];
+    } else if (par_index[x] >= 0) {
+      ad.role[j] = 2, ad.idx[j] = (int8_t)par_index[x];
+    } else {
+      int oi = -1;
+      for (size_t i = 0; i < p.open_qubits.size(); ++i)
+        if (net.final_label[p.open_qubits[i]] == x) oi = (int)i;
+      if (oi < 0) {
+        set_error("tnc_plan: internal error: unexpected root label %d", x);
+        return TNC_EINVAL;
+      }
+      ad.role[j] = 1, ad.idx[j] = (int8_t)oi;
+    }
+  }
+
+  pr.ws_bytes = arena_base + align_up(arena.peak);
+  pr.peak_bytes = (double)arena.peak;
+  pr.base_elems = base_data.size();
+  pr.base_host.resize(base_data.size());
+  for (size_t i = 0; i < base_data.size(); ++i)
+    pr.base_host[i] = std::complex<float>((float)base_data[i].real(), (float)base_data[i].imag());
+  pr.flops_per_group = flops;
+  pr.bytes_per_group = bytes;
+  pr.paper_ops_per_group = pops;
+  pr.max_rank = tree_max_rank(t);
+  return TNC_OK;
+}
+
+}  // namespace tnc

@@ -1,0 +1,454 @@
+// CUDA kernels of the executor (sm_103a), CUDA-core forms:
+//   gather   -- derived leaves (bit projection / fixed slice bits);
+//   permute  -- tiled bit permutation of a 2^r complex64 tensor through
+//               shared memory, coalesced on both the read and the write side;
+//   cgemm    -- FP32 complex GEMM on CUDA cores (the reference form), a
+//               register-tiled kernel, a one-row-per-thread kernel for narrow
+//               N, K and a split-K warp-shuffle reduction for tiny outputs;
+//   accum    -- FP64 accumulation of the root into complex128 amplitudes.
+// Every pairwise contraction computes C[b][m][n] = sum_k A[b][m][k] B[b][k][n]
+// (the node cost 2 M of Eq. 3 with M = batch * M * N * K).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "tnc_kernels.h"
+
+namespace tnc {
+
+namespace {
+
+__device__ __forceinline__ float2 cmul_add(float2 acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+  return acc;
+}
+
+// ------------------------------------------------------------------ counter
+__global__ void set_counter_kernel(uint64_t* ctr, uint64_t v) { *ctr = v; }
+
+// ------------------------------------------------------------------ gather
+__global__ void gather_kernel(const GatherDesc* __restrict__ descs, const float2* __restrict__ base,
+                              float2* __restrict__ ws, const uint8_t* __restrict__ bits, int n_qubits,
+                              const uint64_t* __restrict__ ctr) {
+  const GatherDesc& g = descs[blockIdx.y];
+  const uint64_t n = (uint64_t)1 << g.out_rank;
+  const uint64_t slice = *ctr;
+  for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < n;
+       o += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t src = 0, beta = 0;
+    for (int j = 0; j < g.out_rank; ++j) {
+      uint64_t bit = (o >> j) & 1;
+      int s = g.out_src[j];
+      if (s >= 0)
+        src |= bit << s;
+      else
+        beta |= bit << (-1 - s);
+    }
+    for (int f = 0; f < g.n_fixed; ++f)
+      src |= (uint64_t)(bits[beta * n_qubits + g.fixed_qubit[f]] & 1) << g.fixed_pos[f];
+    for (int f = 0; f < g.n_sliced; ++f) src |= ((slice >> g.sliced_bit[f]) & 1) << g.sliced_pos[f];
+    ws[g.dst + o] = base[g.src + src];
+  }
+}
+
+// ------------------------------------------------------------------ permute
+struct PermArgs {
+  uint64_t src, dst;
+  int nU, a, b, n_outer;
+  int8_t t_in_pos[16];   // t bit i (i >= a) -> input bit position
+  int8_t s_t_bit[16];    // s bit i -> t bit
+  int8_t s_out_pos[16];  // s bit i (i >= b) -> output bit position
+  int8_t outer_in[kMaxRank], outer_out[kMaxRank];
+};
+
+constexpr int kPermThreads = 256;
+
+__global__ void __launch_bounds__(kPermThreads) permute_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                             PermArgs p) {
+  extern __shared__ float2 tile[];
+  uint64_t o = blockIdx.x + (uint64_t)blockIdx.y * gridDim.x;
+  uint64_t in_base = 0, out_base = 0;
+  for (int k = 0; k < p.n_outer; ++k) {
+    uint64_t bit = (o >> k) & 1;
+    in_base |= bit << p.outer_in[k];
+    out_base |= bit << p.outer_out[k];
+  }
+  const int nT = 1 << p.nU;
+  const uint32_t amask = (1u << p.a) - 1, bmask = (1u << p.b) - 1;
+  const int sw = p.a;  // swizzle: low 5 bits of the slot xor the bits above a
+  for (int t = threadIdx.x; t < nT; t += blockDim.x) {
+    uint64_t off = in_base | (t & amask);
+    for (int i = p.a; i < p.nU; ++i) off |= (uint64_t)((t >> i) & 1) << p.t_in_pos[i];
+    int slot = t ^ ((t >> sw) & 31);
+    tile[slot] = in[p.src + off];
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < nT; s += blockDim.x) {
+    int t = 0;
+    for (int i = 0; i < p.nU; ++i) t |= ((s >> i) & 1) << p.s_t_bit[i];
+    uint64_t off = out_base | (s & bmask);
+    for (int i = p.b; i < p.nU; ++i) off |= (uint64_t)((s >> i) & 1) << p.s_out_pos[i];
+    int slot = t ^ ((t >> sw) & 31);
+    out[p.dst + off] = tile[slot];
+  }
+}
+
+// ------------------------------------------------------------------ SIMT GEMM
+template <int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    cgemm_simt_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
+                      int64_t M, int64_t N, int64_t K, int transA, int transB, int64_t b0) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int TX = BN / TN;
+  __shared__ __align__(16) float2 As[BK][BM];
+  __shared__ __align__(16) float2 Bs[BK][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int64_t bz = b0 + blockIdx.z;
+  A += bz * M * K;
+  B += bz * K * N;
+  C += bz * M * N;
+  const int64_t mt = (M + BM - 1) / BM;
+  const int64_t m0 = ((int64_t)blockIdx.x % mt) * BM, n0 = ((int64_t)blockIdx.x / mt) * BN;
+  float2 acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int e = tid; e < BM * BK; e += NT) {
+      int mm, kk;
+      if (!transA) {
+        kk = e % BK, mm = e / BK;
+      } else {
+        mm = e % BM, kk = e / BM;
+      }
+      int64_t m = m0 + mm, k = k0 + kk;
+      float2 v = make_float2(0.f, 0.f);
+      if (m < M && k < K) v = transA ? A[k * M + m] : A[m * K + k];
+      As[kk][mm] = v;
+    }
+#pragma unroll
+    for (int e = tid; e < BN * BK; e += NT) {
+      int nn, kk;
+      if (!transB) {
+        nn = e % BN, kk = e / BN;
+      } else {
+        kk = e % BK, nn = e / BK;
+      }
+      int64_t n = n0 + nn, k = k0 + kk;
+      float2 v = make_float2(0.f, 0.f);
+      if (n < N && k < K) v = transB ? B[n * K + k] : B[k * N + n];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float2 a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = cmul_add(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    int64_t m = m0 + ty * TM + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int64_t n = n0 + tx * TN + j;
+      if (n < N) C[m * N + n] = acc[i][j];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ narrow
+// one output row per thread; N, K <= 16; B of the batch in shared memory
+__global__ void __launch_bounds__(256)
+    cgemm_narrow_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
+                        int64_t M, int N, int K, int transA, int transB, int64_t b0) {
+  __shared__ float2 Bs[16 * 16];
+  const int64_t bz = b0 + blockIdx.y;
+  A += bz * M * K;
+  B += bz * (int64_t)K * N;
+  C += bz * M * N;
+  for (int e = threadIdx.x; e < K * N; e += blockDim.x) {
+    int k = e / N, n = e % N;
+    Bs[e] = transB ? B[(int64_t)n * K + k] : B[(int64_t)k * N + n];
+  }
+  __syncthreads();
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+    float2 a[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k < K) a[k] = transA ? A[(int64_t)k * M + m] : A[m * K + k];
+    for (int n = 0; n < N; ++n) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (k < K) acc = cmul_add(acc, a[k], Bs[k * N + n]);
+      C[m * N + n] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ dot
+// split-K for M*N <= 16: FP32 products summed in runs of 32, runs summed in
+// FP64; per-block partials reduced by a second pass.
+constexpr int kDotThreads = 256;
+
+__global__ void __launch_bounds__(kDotThreads)
+    cgemm_dot_kernel(const float2* __restrict__ A, const float2* __restrict__ B, double2* __restrict__ part,
+                     int M, int N, int64_t K, int transA, int transB, int64_t b0) {
+  const int64_t bz = b0 + blockIdx.y;
+  A += bz * (int64_t)M * K;
+  B += bz * K * (int64_t)N;
+  const int MN = M * N;
+  double2 acc64[16];
+  float2 acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc64[i] = make_double2(0, 0), acc[i] = make_float2(0.f, 0.f);
+  int run = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += stride) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if (m >= M) break;
+      float2 a = transA ? A[k * M + m] : A[(int64_t)m * K + k];
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        if (n >= N || m * N + n >= 16) break;
+        float2 b = transB ? B[(int64_t)n * K + k] : B[k * N + n];
+        acc[m * N + n] = cmul_add(acc[m * N + n], a, b);
+      }
+    }
+    if (++run == 32) {
+      run = 0;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        acc64[i].x += acc[i].x, acc64[i].y += acc[i].y;
+        acc[i] = make_float2(0.f, 0.f);
+      }
+    }
+  }
+  __shared__ double2 red[kDotThreads / 32][16];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    double x = acc64[i].x + acc[i].x, y = acc64[i].y + acc[i].y;
+    for (int off = 16; off; off >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, off);
+      y += __shfl_xor_sync(0xffffffffu, y, off);
+    }
+    if (lane == 0) red[wid][i] = make_double2(x, y);
+  }
+  __syncthreads();
+  if (threadIdx.x < MN) {
+    double2 s = make_double2(0, 0);
+    for (int w = 0; w < kDotThreads / 32; ++w) s.x += red[w][threadIdx.x].x, s.y += red[w][threadIdx.x].y;
+    part[(bz * gridDim.x + blockIdx.x) * MN + threadIdx.x] = s;
+  }
+}
+
+__global__ void dot_finish_kernel(const double2* __restrict__ part, float2* __restrict__ C, int nblk, int MN,
+                                  int64_t batch) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= batch * MN) return;
+  int64_t bz = i / MN, e = i % MN;
+  double x = 0, y = 0;
+  for (int b = 0; b < nblk; ++b) {
+    double2 v = part[(bz * nblk + b) * MN + e];
+    x += v.x, y += v.y;
+  }
+  C[bz * MN + e] = make_float2((float)x, (float)y);
+}
+
+// ------------------------------------------------------------------ accum
+__global__ void accum_kernel(const float2* __restrict__ root, double2* __restrict__ out, AccumDesc d, int batch) {
+  const int64_t nopen = (int64_t)1 << d.n_open;
+  const int64_t total = (int64_t)batch * nopen;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t beta = i / nopen, j = i % nopen;
+    uint64_t base = 0;
+    for (int k = 0; k < d.rank; ++k) {
+      if (d.role[k] == 0)
+        base |= (uint64_t)((beta >> d.idx[k]) & 1) << k;
+      else if (d.role[k] == 1)
+        base |= (uint64_t)((j >> d.idx[k]) & 1) << k;
+    }
+    double x = 0, y = 0;
+    const int64_t npar = (int64_t)1 << d.n_par;
+    for (int64_t p = 0; p < npar; ++p) {
+      uint64_t off = base;
+      for (int k = 0; k < d.rank; ++k)
+        if (d.role[k] == 2) off |= (uint64_t)((p >> d.idx[k]) & 1) << k;
+      float2 v = root[d.src + off];
+      x += v.x, y += v.y;
+    }
+    double2 o = out[i];
+    o.x += x, o.y += y;
+    out[i] = o;
+  }
+}
+
+template <int BM, int BN, int BK, int TM, int TN>
+int run_simt(const GemmDesc& d, const float2* A, const float2* B, float2* C, cudaStream_t st) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  const int64_t mt = (d.M + BM - 1) / BM, nt = (d.N + BN - 1) / BN;
+  if (mt * nt > 0x7fffffff) return (int)cudaErrorInvalidConfiguration;
+  for (int64_t b0 = 0; b0 < d.batch; b0 += 65535) {
+    int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
+    dim3 grid((unsigned)(mt * nt), 1, (unsigned)nb);
+    cgemm_simt_kernel<BM, BN, BK, TM, TN><<<grid, NT, 0, st>>>(A, B, C, d.M, d.N, d.K, d.transA, d.transB, b0);
+  }
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+int launch_set_counter(uint64_t* d_ctr, uint64_t value, void* stream) {
+  set_counter_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_ctr, value);
+  return (int)cudaGetLastError();
+}
+
+int launch_zero(void* ptr, size_t bytes, void* stream) {
+  return (int)cudaMemsetAsync(ptr, 0, bytes, (cudaStream_t)stream);
+}
+
+int launch_gather(const GatherDesc* d_descs, int n_descs, int max_out_rank, const void* base, void* ws,
+                  const uint8_t* d_bits, int n_qubits, const uint64_t* d_slice_ctr, void* stream) {
+  if (n_descs <= 0) return 0;
+  if (n_descs > 65535) return (int)cudaErrorInvalidConfiguration;
+  uint64_t n = (uint64_t)1 << max_out_rank;
+  unsigned gx = (unsigned)((n + 255) / 256);
+  if (gx > 4096) gx = 4096;
+  dim3 grid(gx, (unsigned)n_descs);
+  gather_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_descs, (const float2*)base, (float2*)ws, d_bits,
+                                                         n_qubits, d_slice_ctr);
+  return (int)cudaGetLastError();
+}
+
+int launch_permute(const PermDesc& d, void* ws, void* stream) {
+  const int r = d.rank;
+  PermArgs p;
+  memset(&p, 0, sizeof(p));
+  p.src = d.src;
+  p.dst = d.dst;
+  int dst_of[kMaxRank];
+  for (int j = 0; j < r; ++j) dst_of[(int)d.src_bit[j]] = j;
+  int a = r < 5 ? r : 5, b = r < 5 ? r : 5;
+  bool inU[kMaxRank];
+  auto build_u = [&]() {
+    int cnt = 0;
+    for (int i = 0; i < r; ++i) inU[i] = false;
+    for (int i = 0; i < a; ++i) inU[i] = true;
+    for (int j = 0; j < b; ++j) inU[(int)d.src_bit[j]] = true;
+    for (int i = 0; i < r; ++i) cnt += inU[i];
+    return cnt;
+  };
+  int nU = build_u();
+  while (nU < 10 && a < r) {
+    ++a;
+    nU = build_u();
+  }
+  if (nU > 12) return (int)cudaErrorInvalidValue;
+  // t bits: 0..a-1 = input bits 0..a-1, then the extra input bits ascending
+  int tpos_of_in[kMaxRank];
+  for (int i = 0; i < r; ++i) tpos_of_in[i] = -1;
+  for (int i = 0; i < a; ++i) tpos_of_in[i] = i, p.t_in_pos[i] = (int8_t)i;
+  int t = a;
+  for (int i = a; i < r; ++i)
+    if (inU[i]) tpos_of_in[i] = t, p.t_in_pos[t] = (int8_t)i, ++t;
+  // s bits: 0..b-1 = output bits 0..b-1, then the other tile bits
+  int s = 0;
+  for (int j = 0; j < b; ++j) p.s_t_bit[s] = (int8_t)tpos_of_in[(int)d.src_bit[j]], p.s_out_pos[s] = (int8_t)j, ++s;
+  for (int i = 0; i < r; ++i)
+    if (inU[i] && dst_of[i] >= b) p.s_t_bit[s] = (int8_t)tpos_of_in[i], p.s_out_pos[s] = (int8_t)dst_of[i], ++s;
+  int k = 0;
+  for (int i = 0; i < r; ++i)
+    if (!inU[i]) p.outer_in[k] = (int8_t)i, p.outer_out[k] = (int8_t)dst_of[i], ++k;
+  p.nU = nU;
+  p.a = a;
+  p.b = b;
+  p.n_outer = k;
+  uint64_t nblocks = (uint64_t)1 << k;
+  unsigned gx = nblocks > 65536 ? 65536 : (unsigned)nblocks;
+  unsigned gy = (unsigned)(nblocks / gx);
+  dim3 grid(gx, gy);
+  size_t smem = ((size_t)1 << nU) * sizeof(float2);
+  permute_kernel<<<grid, kPermThreads, smem, (cudaStream_t)stream>>>((const float2*)ws, (float2*)ws, p);
+  return (int)cudaGetLastError();
+}
+
+int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* C, void* ws, cudaStream_t st);
+
+int launch_gemm(const GemmDesc& d, const void* base, void* ws, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const float2* A = (const float2*)(d.a_buf ? base : ws) + d.a;
+  const float2* B = (const float2*)(d.b_buf ? base : ws) + d.b;
+  float2* C = (float2*)ws + d.c;
+  switch (d.kernel) {
+    case KG_SIMT_128x64:
+      return run_simt<128, 64, 8, 8, 4>(d, A, B, C, st);
+    case KG_SIMT_64x32:
+      return run_simt<64, 32, 8, 4, 4>(d, A, B, C, st);
+    case KG_SIMT_32x128:
+      return run_simt<32, 128, 8, 4, 4>(d, A, B, C, st);
+    case KG_NARROW: {
+      if (d.N > 16 || d.K > 16) return (int)cudaErrorInvalidValue;
+      int64_t blocks = (d.M + 255) / 256;
+      if (blocks > 152 * 16) blocks = 152 * 16;
+      for (int64_t b0 = 0; b0 < d.batch; b0 += 65535) {
+        int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
+        dim3 grid((unsigned)blocks, (unsigned)nb);
+        cgemm_narrow_kernel<<<grid, 256, 0, st>>>(A, B, C, d.M, (int)d.N, (int)d.K, d.transA, d.transB, b0);
+      }
+      return (int)cudaGetLastError();
+    }
+    case KG_DOT: {
+      if (d.M * d.N > 16 || d.M > 4 || d.N > 4) return run_simt<64, 32, 8, 4, 4>(d, A, B, C, st);
+      double2* part = (double2*)((float2*)ws + d.scratch);
+      const int MN = (int)(d.M * d.N);
+      int64_t nblk = (d.K + kDotThreads * 32 - 1) / (kDotThreads * 32);
+      if (nblk > 1024) nblk = 1024;
+      if (nblk < 1) nblk = 1;
+      if ((uint64_t)d.batch * nblk * MN * 2 > d.scratch_elems) return (int)cudaErrorInvalidValue;
+      for (int64_t b0 = 0; b0 < d.batch; b0 += 65535) {
+        int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
+        dim3 grid((unsigned)nblk, (unsigned)nb);
+        cgemm_dot_kernel<<<grid, kDotThreads, 0, st>>>(A, B, part, (int)d.M, (int)d.N, d.K, d.transA, d.transB,
+                                                        b0);
+      }
+      int64_t tot = d.batch * MN;
+      dot_finish_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, C, (int)nblk, MN, d.batch);
+      return (int)cudaGetLastError();
+    }
+    case KG_TC:
+      return launch_tc_gemm(d, A, B, C, ws, st);
+    default:
+      return (int)cudaErrorInvalidValue;
+  }
+}
+
+int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, void* stream) {
+  int64_t total = (int64_t)batch << d.n_open;
+  unsigned blocks = (unsigned)((total + 255) / 256);
+  if (blocks > 65535) blocks = 65535;
+  accum_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>((const float2*)ws, (double2*)d_out, d, batch);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace tnc

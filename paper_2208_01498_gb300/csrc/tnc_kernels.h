@@ -1,0 +1,91 @@
+// Plain descriptors passed from the host plan compiler to the CUDA kernels,
+// and the host-callable launchers (implemented in kernels.cu / tc_gemm.cu).
+//
+// Every tensor is a dense row-major array of 2^rank complex64 values whose
+// indices are all binary: a tensor index is a bit of the linear offset.  Bit
+// j of an offset is counted from the least significant end (bit 0 = the last,
+// fastest-varying index).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace tnc {
+
+constexpr int kMaxRank = 48;
+
+// Gather of one derived leaf from its base leaf: output bit j comes from
+// base bit out_src[j] (>= 0), or is bit b of the bitstring index beta when
+// out_src[j] = -1 - b.  Base bits not fed by an output bit are fixed: a final
+// wire of qubit q takes bits[beta][q]; a sliced bond takes bit k of the
+// slice-group counter.
+struct GatherDesc {
+  uint64_t src;          // element offset of the base leaf (plan buffer)
+  uint64_t dst;          // element offset of the derived leaf (workspace)
+  int out_rank;
+  int n_fixed;
+  int n_sliced;
+  int src_rank;
+  int8_t out_src[32];
+  int8_t fixed_pos[4];
+  int16_t fixed_qubit[4];
+  int8_t sliced_pos[24];
+  int8_t sliced_bit[24];
+};
+
+// out[j] = in[i] where bit k of i is bit src_bit^-1 ... stated directly:
+// for every output offset j, input offset i has bit src_bit[k] equal to bit
+// k of j (k < rank).
+struct PermDesc {
+  uint64_t src, dst;     // element offsets in the workspace
+  int rank;
+  int8_t src_bit[kMaxRank];
+};
+
+// C[b][m][n] = sum_k A[b][m][k] B[b][k][n]; A stored [b][K][M] if transA,
+// B stored [b][N][K] if transB; C stored [b][M][N].  Buffers: 0 = workspace,
+// 1 = plan leaf buffer.
+struct GemmDesc {
+  uint64_t a, b, c;
+  int64_t batch, M, N, K;
+  int transA, transB;
+  int a_buf, b_buf;
+  int kernel;            // kernel variant chosen by the compiler / autotuner
+  int form;              // TNC_FP32 / TNC_3XTF32 / TNC_SPLIT_BF16
+  uint64_t scratch;      // workspace element offset of per-node scratch (0 if none)
+  uint64_t scratch_elems;
+};
+
+// Final accumulation: out[beta][j] += sum over the bits of the grouped
+// slices of root[...]; root bit k is beta bit (role 0, idx), open bit (role
+// 1, idx) or a grouped-slice bit (role 2, idx).
+struct AccumDesc {
+  uint64_t src;
+  int rank;
+  int n_beta, n_open, n_par;
+  int8_t role[kMaxRank];
+  int8_t idx[kMaxRank];
+};
+
+// ---------------------------------------------------------------- launchers
+// Each returns 0 on success or a cudaError_t value.
+int launch_gather(const GatherDesc* d_descs, int n_descs, int max_out_rank, const void* base,
+                  void* ws, const uint8_t* d_bits, int n_qubits, const uint64_t* d_slice_ctr,
+                  void* stream);
+int launch_permute(const PermDesc& d, void* ws, void* stream);
+int launch_gemm(const GemmDesc& d, const void* base, void* ws, void* stream);
+int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, void* stream);
+int launch_zero(void* ptr, size_t bytes, void* stream);
+int launch_set_counter(uint64_t* d_ctr, uint64_t value, void* stream);
+
+// kernel variants of launch_gemm
+enum GemmKernel {
+  KG_SIMT_128x64 = 0,   // register-tiled CUDA-core cGEMM
+  KG_SIMT_64x32 = 1,
+  KG_NARROW = 2,        // one output row per thread, B in shared memory
+  KG_DOT = 3,           // split-K reduction for tiny outputs (FP64 across threads)
+  KG_TC = 4,            // tcgen05 tensor-core cGEMM (3xTF32 / split-BF16)
+  KG_SIMT_32x128 = 5,
+  KG_COUNT
+};
+
+}  // namespace tnc

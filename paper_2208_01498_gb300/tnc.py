@@ -1,0 +1,266 @@
+"""Thin Python binding of the C ABI in ``include/tnc.h`` (ctypes).
+
+Argument marshalling only: every step of the contraction runs inside
+``libtnc.so`` (planning on the host, kernels on the GPU).  PyTorch provides
+device memory and streams.  Importing this module fails loudly if the library
+has not been built (``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtnc.so")
+
+TNC_OK = 0
+TNC_EINVAL = -1
+TNC_ENOMEM = -2
+TNC_ECUDA = -3
+TNC_ETIMEOUT = -4
+TNC_EBUSY = -5
+TNC_ESTATE = -6
+TNC_ENOTFOUND = -7
+
+FORMS = {"fp32": 0, "3xtf32": 1, "split_bf16": 2}
+
+
+class TncError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class NetworkDesc(C.Structure):
+    _fields_ = [("n_qubits", C.c_int), ("dim", C.c_int), ("coords", C.POINTER(C.c_double)),
+                ("n_gates", C.c_int), ("arity", C.POINTER(C.c_int)), ("qubits", C.POINTER(C.c_int)),
+                ("mats", C.POINTER(C.c_double))]
+
+
+class PlanOpts(C.Structure):
+    _fields_ = [("n_open", C.c_int), ("open_qubits", C.POINTER(C.c_int)), ("max_batch", C.c_int),
+                ("mem_cap_bytes", C.c_size_t), ("form", C.c_int), ("seed", C.c_uint64),
+                ("ssa_trials", C.c_int), ("leaf_size", C.c_int), ("max_group_log2", C.c_int)]
+
+
+class PlanReport(C.Structure):
+    _fields_ = [("paper_ops", C.c_double), ("real_flops", C.c_double), ("bytes", C.c_double),
+                ("peak_bytes", C.c_double), ("ws_bytes", C.c_size_t), ("n_slices", C.c_double),
+                ("n_slice_groups", C.c_int), ("n_sliced", C.c_int), ("n_nodes", C.c_int),
+                ("n_leaves", C.c_int), ("max_rank", C.c_int), ("n_launches", C.c_int),
+                ("plan_ms", C.c_double), ("tree_cost_log2", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTED = [
+    "tnc_status_string", "tnc_last_error", "tnc_load_network", "tnc_free_network",
+    "tnc_plan_opts_default", "tnc_plan", "tnc_free_plan", "tnc_plan_get_report",
+    "tnc_plan_export_json", "tnc_plan_upload", "tnc_contract_amplitudes",
+    "tnc_contract_amplitudes_dbits", "tnc_contract_partial", "tnc_server_create",
+    "tnc_server_submit", "tnc_server_poll", "tnc_server_wait", "tnc_server_cancel",
+    "tnc_server_destroy",
+]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libtnc.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(_LIB_PATH)
+    vp, i, sz, u64 = C.c_void_p, C.c_int, C.c_size_t, C.c_uint64
+    sig = {
+        "tnc_status_string": (C.c_char_p, [i]),
+        "tnc_last_error": (C.c_char_p, []),
+        "tnc_load_network": (i, [C.POINTER(NetworkDesc), C.POINTER(vp)]),
+        "tnc_free_network": (None, [vp]),
+        "tnc_plan_opts_default": (None, [C.POINTER(PlanOpts)]),
+        "tnc_plan": (i, [vp, C.POINTER(PlanOpts), C.POINTER(vp), C.POINTER(PlanReport)]),
+        "tnc_free_plan": (None, [vp]),
+        "tnc_plan_get_report": (i, [vp, C.POINTER(PlanReport)]),
+        "tnc_plan_export_json": (i, [vp, C.c_char_p, sz, C.POINTER(sz)]),
+        "tnc_plan_upload": (i, [vp, vp]),
+        "tnc_contract_amplitudes": (i, [vp, vp, i, vp, vp, sz, vp]),
+        "tnc_contract_amplitudes_dbits": (i, [vp, vp, i, vp, vp, sz, vp]),
+        "tnc_contract_partial": (i, [vp, vp, i, i, i, vp, vp, sz, vp]),
+        "tnc_server_create": (i, [vp, sz, i, C.POINTER(vp)]),
+        "tnc_server_submit": (i, [vp, vp, vp, i, vp, C.POINTER(u64)]),
+        "tnc_server_poll": (i, [vp, u64, C.POINTER(i)]),
+        "tnc_server_wait": (i, [vp, u64, i, C.POINTER(C.c_double)]),
+        "tnc_server_cancel": (i, [vp, u64]),
+        "tnc_server_destroy": (i, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int, what: str):
+    if status != TNC_OK:
+        msg = lib.tnc_last_error().decode(errors="replace")
+        raise TncError(status, f"{what}: {lib.tnc_status_string(status).decode()}: {msg}")
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+class Network:
+    """``tnc_load_network`` on a gate list (``circuits.GateList``) or on the
+    flat arrays (coords, arity, qubits, mats)."""
+
+    def __init__(self, gatelist=None, *, arrays=None):
+        if gatelist is not None:
+            coords, arity, qubits, mats = gatelist.arrays()
+            n = gatelist.n_qubits
+        else:
+            coords, arity, qubits, mats = arrays
+            n = coords.shape[0]
+        coords = np.ascontiguousarray(coords, np.float64)
+        self._keep = (coords, np.ascontiguousarray(arity, np.int32),
+                      np.ascontiguousarray(qubits, np.int32), np.ascontiguousarray(mats, np.float64))
+        c, a, q, m = self._keep
+        desc = NetworkDesc(int(n), int(c.shape[1]) if c.ndim == 2 else 1, _ptr(c, C.c_double),
+                           int(a.shape[0]), _ptr(a, C.c_int), _ptr(q, C.c_int), _ptr(m, C.c_double))
+        h = C.c_void_p()
+        _check(lib.tnc_load_network(C.byref(desc), C.byref(h)), "tnc_load_network")
+        self.handle = h
+        self.n_qubits = int(n)
+
+    def close(self):
+        if self.handle:
+            lib.tnc_free_network(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def load_network(gatelist) -> Network:
+    return Network(gatelist)
+
+
+class Plan:
+    """``tnc_plan``: separator tree, slicing and compiled program."""
+
+    def __init__(self, net: Network, open_qubits=(), max_batch: int = 1, mem_cap_bytes: int = 0,
+                 form: str = "fp32", seed: int = 1, ssa_trials: int = 32, leaf_size: int = 8,
+                 max_group_log2: int = 6):
+        o = PlanOpts()
+        lib.tnc_plan_opts_default(C.byref(o))
+        self._open = np.ascontiguousarray(sorted(int(q) for q in open_qubits), np.int32)
+        o.n_open = len(self._open)
+        o.open_qubits = _ptr(self._open, C.c_int) if len(self._open) else None
+        o.max_batch = int(max_batch)
+        o.mem_cap_bytes = int(mem_cap_bytes)
+        o.form = FORMS[form] if isinstance(form, str) else int(form)
+        o.seed = int(seed)
+        o.ssa_trials = int(ssa_trials)
+        o.leaf_size = int(leaf_size)
+        o.max_group_log2 = int(max_group_log2)
+        rep = PlanReport()
+        h = C.c_void_p()
+        _check(lib.tnc_plan(net.handle, C.byref(o), C.byref(h), C.byref(rep)), "tnc_plan")
+        self.handle = h
+        self.report = rep.as_dict()
+        self.n_qubits = net.n_qubits
+        self.n_open = len(self._open)
+        self.open_qubits = self._open.copy()
+        self.max_batch = int(max_batch)
+        self.form = form
+
+    @property
+    def ws_bytes(self) -> int:
+        return int(self.report["ws_bytes"])
+
+    def export(self) -> dict:
+        need = C.c_size_t()
+        _check(lib.tnc_plan_export_json(self.handle, None, 0, C.byref(need)), "export")
+        buf = C.create_string_buffer(need.value + 1)
+        _check(lib.tnc_plan_export_json(self.handle, buf, need.value + 1, C.byref(need)), "export")
+        return json.loads(buf.value.decode())
+
+    def upload(self, stream=None):
+        _check(lib.tnc_plan_upload(self.handle, _stream_ptr(stream)), "tnc_plan_upload")
+
+    def close(self):
+        if self.handle:
+            lib.tnc_free_plan(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan(net: Network, **kw) -> Plan:
+    return Plan(net, **kw)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def alloc_workspace(p: Plan, device="cuda"):
+    import torch
+    return torch.empty(max(p.ws_bytes, 256), dtype=torch.uint8, device=device)
+
+
+def contract_amplitudes(p: Plan, bits, out=None, ws=None, stream=None):
+    """Amplitudes for host bitstrings ``bits`` (uint8 [batch][n_qubits]).
+    Returns (or fills) a complex128 CUDA tensor [batch][2^n_open]."""
+    import torch
+    bits = np.ascontiguousarray(np.atleast_2d(bits), dtype=np.uint8)
+    batch = bits.shape[0]
+    if out is None:
+        out = torch.empty((batch, 1 << p.n_open), dtype=torch.complex128, device="cuda")
+    if ws is None:
+        ws = alloc_workspace(p)
+    _check(lib.tnc_contract_amplitudes(p.handle, bits.ctypes.data_as(C.c_void_p), batch,
+                                       C.c_void_p(out.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                       ws.numel(), _stream_ptr(stream)), "tnc_contract_amplitudes")
+    return out
+
+
+def contract_amplitudes_dbits(p: Plan, d_bits, out=None, ws=None, stream=None):
+    """Same with a uint8 CUDA tensor of bitstrings."""
+    import torch
+    batch = d_bits.shape[0]
+    if out is None:
+        out = torch.empty((batch, 1 << p.n_open), dtype=torch.complex128, device="cuda")
+    if ws is None:
+        ws = alloc_workspace(p)
+    _check(lib.tnc_contract_amplitudes_dbits(p.handle, C.c_void_p(d_bits.data_ptr()), batch,
+                                             C.c_void_p(out.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                             ws.numel(), _stream_ptr(stream)), "tnc_contract_amplitudes_dbits")
+    return out
+
+
+def contract_partial(p: Plan, d_bits, group_begin: int, group_end: int, out=None, ws=None, stream=None):
+    import torch
+    batch = d_bits.shape[0]
+    if out is None:
+        out = torch.empty((batch, 1 << p.n_open), dtype=torch.complex128, device="cuda")
+    if ws is None:
+        ws = alloc_workspace(p)
+    _check(lib.tnc_contract_partial(p.handle, C.c_void_p(d_bits.data_ptr()), batch, int(group_begin),
+                                    int(group_end), C.c_void_p(out.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                    ws.numel(), _stream_ptr(stream)), "tnc_contract_partial")
+    return out
