@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the separator-tree contraction executor.
+
+Workload (one step = one request): the 5 x 8 IQP circuit (40 qubits; H layer,
+exp(i theta Z) on every qubit, exp(i phi ZZ) on the 177 pairs within
+Manhattan distance 2, H layer; theta, phi ~ U[0, 2 pi)), amplitudes of 256
+seed-random bitstrings per request, contracted along the separator tree in
+the chosen form with the FP64 slice/beta accumulation.  Bitstrings of every
+step are resident on the device before the timed region (``value``); ``e2e``
+repeats the measurement through the public host-buffer call with the
+host->device copy of the bitstrings and the device->host read of the
+amplitudes inside the timed region.
+
+Under torchrun each rank serves its own requests (independent problems:
+weak scaling, no collective on the data path); the timed region is bracketed
+by a barrier and a device synchronisation, and the maximum time over ranks is
+used.  ``--impl reference`` times the FP64 oracle (the column transfer-matrix
+closed form of the IQP amplitudes) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import circuits as C  # noqa: E402
+
+REQ_BATCH = 256
+WORKLOAD = "iqp_5x8_40q_256_bitstrings"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed
+    region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        with open(self.f.name) as g:
+            rows = [r.strip().split(", ") for r in g if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _workload(seed: int, steps: int):
+    gl, _ = C.config_circuit(3, seed)
+    bits = np.stack([C.random_bitstrings(gl.n_qubits, REQ_BATCH, seed * 100003 + i) for i in range(steps)])
+    return gl, bits
+
+
+def _cpu_oracle(gl, bits, max_seconds: float = 20.0):
+    """Time the oracle (transfer-matrix closed form) on a bounded sample."""
+    import oracle as O
+    n_done = 0
+    t0 = time.perf_counter()
+    for req in bits:
+        O.iqp_transfer_amplitudes(gl, req)
+        n_done += req.shape[0]
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return n_done / dt, n_done, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    gl, bits = _workload(args.seed, args.warmup + args.steps)
+    import oracle as O
+    sample = 16  # bitstrings per step: a bounded slice of one request
+    for w in range(args.warmup):
+        O.iqp_transfer_amplitudes(gl, bits[w][:sample])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        O.iqp_transfer_amplitudes(gl, bits[args.warmup + k][:sample])
+    dt = time.perf_counter() - t0
+    val = args.steps * sample / dt
+    line = {
+        "impl": "reference", "metric": "amplitudes/s", "value": val, "unit": "amplitudes/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "bitstrings_per_step": sample, "seed": args.seed},
+        "cpu_baseline": {"value": val, "unit": "amplitudes/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} of the 256 bitstrings of each request, IQP transfer-matrix "
+                                   f"closed form (numpy, single thread; host has {os.cpu_count()} cores)"},
+        "e2e": {"value": val, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2208_01498_gb300 import tnc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    gl, bits = _workload(args.seed + rank, args.warmup + args.steps)
+    net = tnc.Network(gl)
+    plan = tnc.Plan(net, max_batch=REQ_BATCH, form=args.form, seed=1, ssa_trials=64)
+    rep = plan.report
+    ws = tnc.alloc_workspace(plan)
+    out = torch.empty((REQ_BATCH, 1), dtype=torch.complex128, device=dev)
+    d_bits = torch.from_numpy(bits).to(dev)
+    stream = torch.cuda.current_stream()
+    plan.upload(stream)
+
+    for w in range(args.warmup):
+        tnc.contract_amplitudes_dbits(plan, d_bits[w], out=out, ws=ws, stream=stream)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs
+    plan.set_profiling(True)
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        tnc.contract_amplitudes_dbits(plan, d_bits[args.warmup + k], out=out, ws=ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    prof = plan.profile()
+    plan.set_profiling(False)
+    if world > 1:
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    amps = world * args.steps * REQ_BATCH
+    value = amps / (t_ms / 1e3)
+
+    # ---- end to end through the host-buffer API
+    pinned = torch.from_numpy(bits).pin_memory()
+    res = torch.empty((REQ_BATCH, 1), dtype=torch.complex128).pin_memory()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        tnc.contract_amplitudes(plan, pinned[args.warmup + k].numpy(), out=out, ws=ws, stream=stream)
+        res.copy_(out, non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": amps / e2e_s, "unit": "amplitudes/s", "h2d_bytes_per_step": int(REQ_BATCH * gl.n_qubits),
+           "d2h_bytes_per_step": int(REQ_BATCH * 16)}
+
+    # ---- roofline of the dominant kernel family
+    peaks, src = _peaks()
+    kinds = {}
+    for ms, runs, kind, fl, by in zip(prof["ms"], prof["runs"], prof["kind"], prof["flops"], prof["bytes"]):
+        if runs == 0:
+            continue
+        d = kinds.setdefault(int(kind), {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 0})
+        d["ms"] += ms
+        d["flops"] += fl * runs
+        d["bytes"] += by * runs
+        d["launches"] += runs
+    total_ms = sum(d["ms"] for d in kinds.values())
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = kinds[dom]
+    names = {0: "cgemm_simt_128x64", 1: "cgemm_simt_64x32", 2: "cgemm_narrow", 3: "cgemm_dot",
+             4: "cgemm_tc", 5: "cgemm_simt_32x128", 100: "permute"}
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if dom == 100:
+        ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}
+    elif dom == 4:
+        mult = 3.0  # three bf16/tf32 products per useful product
+        ach = mult * d["flops"] / (d["ms"] / 1e3) / 1e12
+        pk = float(peaks["bf16_tflops"]) * (1.0 if args.form == "split_bf16" else 0.5)
+        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s"}
+    else:
+        ach = d["flops"] / (d["ms"] / 1e3) / 1e12
+        pk = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock
+        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = names.get(dom, str(dom))
+    roof["share_of_device_time"] = d["ms"] / total_ms if total_ms else None
+    roof["peak_source"] = src
+
+    line = {
+        "metric": "amplitudes/s", "value": value, "unit": "amplitudes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "c64", "3xtf32": "tf32x3 (fp32 acc)", "split_bf16": "bf16x3 (fp32 acc)"}[args.form],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": args.form, "bitstrings_per_request": REQ_BATCH,
+                   "seed": args.seed, "real_tflop_per_request": rep["real_flops"] / 1e12,
+                   "paper_ops_log2": rep["tree_cost_log2"], "ws_bytes": rep["ws_bytes"],
+                   "l2": f"working set {rep['ws_bytes'] / 1e9:.1f} GB per request > 129 MB L2",
+                   "parallelism": f"dp{world} (independent requests)"},
+        "effective_tflops": world * args.steps * rep["real_flops"] / (t_ms / 1e3) / 1e12,
+        "roofline": roof,
+        "e2e": e2e,
+        "clocks": ck,
+        "gpu_launches": int(args.steps * rep["n_launches"]),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, n_done, dt = _cpu_oracle(gl, bits[args.warmup:args.warmup + 1])
+        line["cpu_baseline"] = {"value": v, "unit": "amplitudes/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{n_done} bitstrings (one request) of the same workload by the IQP "
+                                          f"transfer-matrix closed form, {dt:.1f} s, numpy single thread "
+                                          f"(host has {os.cpu_count()} cores)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=["fp32", "3xtf32", "split_bf16"], default="fp32")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

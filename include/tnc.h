@@ -142,6 +142,22 @@ int tnc_plan_export_json(const tnc_plan_t* plan, char* buf, size_t cap, size_t* 
  * automatically by the first contraction if needed.  stream may be NULL. */
 int tnc_plan_upload(tnc_plan_t* plan, void* cuda_stream);
 
+/* Per-step CUDA-event profiling of the node program.  While enabled, every
+ * contraction records one event before each slice group and one after each
+ * step on the contraction's stream (no host synchronisation).  Disabling
+ * drops the recorded events. */
+int tnc_plan_set_profiling(tnc_plan_t* plan, int enable);
+
+/* Aggregate of the recorded events (synchronises on them): for each of the
+ * n = *n_steps steps of the program (n <= cap), the summed duration in ms
+ * over all recorded runs, the number of runs, the kernel variant
+ * (TNC_STEP_* below), and its algorithmic flops and bytes per launch
+ * (8 M real flops per node, Eq. 3; 8 (|A|+|B|+|C|) bytes; a permutation
+ * moves 16 bytes per element).  Arrays may be NULL to query n. */
+#define TNC_STEP_PERMUTE 100
+int tnc_plan_get_profile(tnc_plan_t* plan, int* n_steps, int cap, double* ms, int* runs, int* kind,
+                         double* flops, double* bytes);
+
 /* Amplitudes for `batch` bitstrings (1 <= batch <= max_batch).
  * bits: HOST uint8 [batch][n_qubits]; entries of open qubits are ignored.
  * d_out: DEVICE complex128 [batch][2^n_open], caller-owned, overwritten.

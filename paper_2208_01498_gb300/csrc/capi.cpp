@@ -89,7 +89,24 @@ static void fill_report(Plan& p, double plan_ms) {
   r.n_nodes = nodes;
   r.n_leaves = (int)p.net.leaves.size();
   r.max_rank = p.prog.max_rank;
-  r.n_launches = (int)p.prog.steps.size() + 3;
+  // kernels of this library launched per request: per slice group the
+  // counter, the gather and the accumulation, plus every step's launches
+  int per_group = 2 + (p.prog.gathers.empty() ? 0 : 1);
+  for (auto& s : p.prog.steps) {
+    if (s.kind == ST_PERMUTE) {
+      per_group += 1;
+      continue;
+    }
+    const GemmDesc& g = s.gemm;
+    int chunks = (int)((g.batch + 65534) / 65535);
+    if (g.kernel == KG_DOT && g.M <= 4 && g.N <= 4)
+      per_group += chunks + 1;
+    else if (g.kernel == KG_TC)
+      per_group += 3;
+    else
+      per_group += chunks;
+  }
+  r.n_launches = (int)(per_group * groups);
   r.plan_ms = plan_ms;
 }
 
@@ -215,6 +232,8 @@ int tnc_plan_get_report(const tnc_plan_t* plan, tnc_plan_report* rep) {
 void tnc_free_plan(tnc_plan_t* plan) {
   if (!plan) return;
   Plan& p = plan->p;
+  for (auto& r : p.prof) cudaEventDestroy((cudaEvent_t)r.ev);
+  p.prof.clear();
   if (p.d_base || p.d_gathers) {
     int prev = -1;
     cudaGetDevice(&prev);
@@ -407,20 +426,34 @@ static int run(tnc_plan_t* tp, const uint8_t* bits, bool bits_on_device, int bat
   e = cudaMemsetAsync(d_out, 0, out_bytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "tnc_contract: memset out");
   uint64_t* d_ctr = (uint64_t*)(ws + p.prog.off_ctr);
+  auto mark = [&](int step) -> int {
+    if (!p.profiling) return TNC_OK;
+    cudaEvent_t ev;
+    cudaError_t ee = cudaEventCreate(&ev);
+    if (ee != cudaSuccess) return cuda_fail(ee, "profiling: cudaEventCreate");
+    ee = cudaEventRecord(ev, st);
+    if (ee != cudaSuccess) return cuda_fail(ee, "profiling: cudaEventRecord");
+    p.prof.push_back({step, (void*)ev});
+    return TNC_OK;
+  };
   for (int g = g0; g < g1; ++g) {
     int r;
+    if ((r = mark(-1)) != TNC_OK) return r;
     if ((r = launch_set_counter(d_ctr, (uint64_t)g, st))) return cuda_fail((cudaError_t)r, "set counter");
     if (!p.prog.gathers.empty()) {
       r = launch_gather((const GatherDesc*)p.d_gathers, (int)p.prog.gathers.size(), p.prog.max_gather_rank,
                         p.d_base, ws, (const uint8_t*)(ws + p.prog.off_bits), nq, d_ctr, st);
       if (r) return cuda_fail((cudaError_t)r, "gather");
     }
-    for (const Step& s : p.prog.steps) {
+    if ((r = mark(-2)) != TNC_OK) return r;
+    for (size_t si = 0; si < p.prog.steps.size(); ++si) {
+      const Step& s = p.prog.steps[si];
       if (s.kind == ST_PERMUTE)
         r = launch_permute(s.perm, ws, st);
       else
         r = launch_gemm(s.gemm, p.d_base, ws, st);
       if (r) return cuda_fail((cudaError_t)r, s.kind == ST_PERMUTE ? "permute" : "gemm");
+      if ((r = mark((int)si)) != TNC_OK) return r;
     }
     r = launch_accum(p.prog.accum, ws, d_out, batch, st);
     if (r) return cuda_fail((cudaError_t)r, "accum");
@@ -438,6 +471,73 @@ int run_request(tnc_plan_t* plan, const uint8_t* host_bits, int batch, void* d_o
 }  // namespace tnc
 
 extern "C" {
+
+static void drop_profile(Plan& p) {
+  for (auto& r : p.prof) cudaEventDestroy((cudaEvent_t)r.ev);
+  p.prof.clear();
+  p.prof_ms.assign(p.prog.steps.size(), 0.0);
+  p.prof_runs.assign(p.prog.steps.size(), 0);
+}
+
+int tnc_plan_set_profiling(tnc_plan_t* plan, int enable) {
+  if (!plan) {
+    set_error("tnc_plan_set_profiling: NULL plan");
+    return TNC_EINVAL;
+  }
+  Plan& p = plan->p;
+  drop_profile(p);
+  p.profiling = enable != 0;
+  return TNC_OK;
+}
+
+int tnc_plan_get_profile(tnc_plan_t* plan, int* n_steps, int cap, double* ms, int* runs, int* kind, double* flops,
+                         double* bytes) {
+  if (!plan || !n_steps) {
+    set_error("tnc_plan_get_profile: NULL argument");
+    return TNC_EINVAL;
+  }
+  Plan& p = plan->p;
+  const int n = (int)p.prog.steps.size();
+  *n_steps = n;
+  if (p.prof_ms.size() != (size_t)n) {
+    p.prof_ms.assign(n, 0.0);
+    p.prof_runs.assign(n, 0);
+  }
+  // fold the recorded events: each step's time is from the previous record
+  cudaEvent_t prev = nullptr;
+  for (auto& r : p.prof) {
+    cudaEvent_t ev = (cudaEvent_t)r.ev;
+    cudaError_t e = cudaEventSynchronize(ev);
+    if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_get_profile: cudaEventSynchronize");
+    if (r.step >= 0 && prev) {
+      float t = 0;
+      e = cudaEventElapsedTime(&t, prev, ev);
+      if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_get_profile: cudaEventElapsedTime");
+      p.prof_ms[r.step] += t;
+      p.prof_runs[r.step] += 1;
+    }
+    prev = (r.step == -1) ? nullptr : ev;
+  }
+  for (auto& r : p.prof) cudaEventDestroy((cudaEvent_t)r.ev);
+  p.prof.clear();
+  for (int i = 0; i < n && i < cap; ++i) {
+    const Step& s = p.prog.steps[i];
+    if (ms) ms[i] = p.prof_ms[i];
+    if (runs) runs[i] = p.prof_runs[i];
+    if (kind) kind[i] = s.kind == ST_PERMUTE ? TNC_STEP_PERMUTE : s.gemm.kernel;
+    double f = 0, b = 0;
+    if (s.kind == ST_GEMM) {
+      const GemmDesc& g = s.gemm;
+      f = 8.0 * g.batch * g.M * g.N * g.K;
+      b = 8.0 * g.batch * ((double)g.M * g.K + (double)g.K * g.N + (double)g.M * g.N);
+    } else {
+      b = 16.0 * std::exp2((double)s.perm.rank);
+    }
+    if (flops) flops[i] = f;
+    if (bytes) bytes[i] = b;
+  }
+  return TNC_OK;
+}
 
 int tnc_contract_amplitudes(tnc_plan_t* plan, const uint8_t* bits, int batch, void* d_out, void* d_ws,
                             size_t ws_bytes, void* stream) {

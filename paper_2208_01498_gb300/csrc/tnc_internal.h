@@ -124,6 +124,16 @@ struct Plan {
   std::vector<int> sliced_serial, sliced_par;
   Program prog;
   tnc_plan_report rep{};
+  // per-step CUDA-event profiling
+  bool profiling = false;
+  struct ProfRec {
+    int step;  // -1 marks the start of a slice group
+    void* ev;
+  };
+  std::vector<ProfRec> prof;
+  std::vector<void*> ev_pool;
+  std::vector<double> prof_ms;
+  std::vector<int> prof_runs;
   // device state
   int device = -1;
   void* d_base = nullptr;        // leaf buffer (complex64)

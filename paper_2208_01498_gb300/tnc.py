@@ -62,7 +62,7 @@ EXPORTED = [
     "tnc_plan_export_json", "tnc_plan_upload", "tnc_contract_amplitudes",
     "tnc_contract_amplitudes_dbits", "tnc_contract_partial", "tnc_server_create",
     "tnc_server_submit", "tnc_server_poll", "tnc_server_wait", "tnc_server_cancel",
-    "tnc_server_destroy",
+    "tnc_server_destroy", "tnc_plan_set_profiling", "tnc_plan_get_profile",
 ]
 
 
@@ -91,6 +91,9 @@ def _load():
         "tnc_server_wait": (i, [vp, u64, i, C.POINTER(C.c_double)]),
         "tnc_server_cancel": (i, [vp, u64]),
         "tnc_server_destroy": (i, [vp]),
+        "tnc_plan_set_profiling": (i, [vp, i]),
+        "tnc_plan_get_profile": (i, [vp, C.POINTER(i), i, C.POINTER(C.c_double), C.POINTER(i),
+                                     C.POINTER(i), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -192,6 +195,24 @@ class Plan:
 
     def upload(self, stream=None):
         _check(lib.tnc_plan_upload(self.handle, _stream_ptr(stream)), "tnc_plan_upload")
+
+    def set_profiling(self, enable: bool):
+        _check(lib.tnc_plan_set_profiling(self.handle, int(bool(enable))), "tnc_plan_set_profiling")
+
+    def profile(self) -> dict:
+        """Per-step event timings: arrays ms, runs, kind, flops, bytes."""
+        n = C.c_int()
+        _check(lib.tnc_plan_get_profile(self.handle, C.byref(n), 0, None, None, None, None, None), "profile")
+        k = n.value
+        ms = np.zeros(k, np.float64)
+        runs = np.zeros(k, np.int32)
+        kind = np.zeros(k, np.int32)
+        fl = np.zeros(k, np.float64)
+        by = np.zeros(k, np.float64)
+        _check(lib.tnc_plan_get_profile(self.handle, C.byref(n), k, _ptr(ms, C.c_double), _ptr(runs, C.c_int),
+                                        _ptr(kind, C.c_int), _ptr(fl, C.c_double), _ptr(by, C.c_double)),
+               "profile")
+        return dict(ms=ms, runs=runs, kind=kind, flops=fl, bytes=by)
 
     def close(self):
         if self.handle:

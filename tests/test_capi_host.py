@@ -27,7 +27,7 @@ def test_library_exports_every_declared_symbol():
     assert len(names) >= 19
     for n in names:
         assert hasattr(tnc.lib, n), n
-    assert set(names) <= set(tnc.EXPORTED) | {"tnc_contract_amplitudes_static"}
+    assert set(names) <= set(tnc.EXPORTED)
 
 
 def test_status_strings():

@@ -1,0 +1,216 @@
+"""Parity of the CUDA path with the FP64 oracle (GPU).
+
+Every test calls the C ABI through the binding and compares amplitudes
+element by element with an oracle evaluated on the same seeded circuit, using
+the benchmark's error measure |a - a_ref| / max(|a_ref|, 2^{-n/2}): at most
+1e-5 for the FP32 and 3xTF32 forms, 1e-4 for split-BF16.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import circuits as C
+import oracle as O
+from oracle.stabilizer import stabilizer_amplitudes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "3xtf32": 1e-5, "split_bf16": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def tnc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_01498_gb300 import tnc as t
+    return t
+
+
+def _run(tnc, gl, bits, oq=(), form="fp32", **kw):
+    p = tnc.Plan(tnc.Network(gl), open_qubits=oq, max_batch=max(1, bits.shape[0]), form=form, **kw)
+    out = tnc.contract_amplitudes(p, bits)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), p
+
+
+def _check(got, ref, n, form="fp32"):
+    err = O.rel_error(got, ref, n)
+    assert err.max() <= TOL[form], f"max rel error {err.max():.3g} ({form})"
+    return err.max()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_config0_single_amplitude(tnc, seed):
+    gl, info = C.config_circuit(0, seed)
+    ref = O.statevector_amplitudes(gl, info["bits"])
+    got, _ = _run(tnc, gl, info["bits"])
+    _check(got, ref, 16)
+
+
+@pytest.mark.parametrize("family", ["rand2d", "sycamore", "iqp", "layered", "ghz"])
+def test_families_batch_and_open_legs(tnc, family):
+    gl = {"rand2d": lambda: C.random_2d(4, 4, 10, 3), "sycamore": lambda: C.sycamore(4, 8, 1),
+          "iqp": lambda: C.iqp(4, 4, 3), "layered": lambda: C.layered_3d(4, 4, 5),
+          "ghz": lambda: C.ghz(4, 4)}[family]()
+    bits = C.random_bitstrings(16, 5, 7)
+    oq = [2, 9, 13]
+    ref = O.statevector_amplitudes(gl, bits, oq)
+    got, _ = _run(tnc, gl, bits, oq)
+    _check(got, ref, 16)
+
+
+def test_batch_smaller_than_planned(tnc):
+    gl = C.random_2d(3, 4, 8, 8)
+    bits = C.random_bitstrings(12, 3, 2)
+    p = tnc.Plan(tnc.Network(gl), open_qubits=[5], max_batch=16)
+    out = tnc.contract_amplitudes(p, bits)
+    ref = O.statevector_amplitudes(gl, bits, [5])
+    _check(out.cpu().numpy(), ref, 12)
+
+
+def test_all_legs_open_normalisation(tnc):
+    gl = C.random_2d(3, 3, 6, 4)
+    got, _ = _run(tnc, gl, np.zeros((1, 9), np.uint8), list(range(9)))
+    assert abs(np.sum(np.abs(got) ** 2) - 1.0) < 1e-5
+    ref = O.statevector_amplitudes(gl, np.zeros((1, 9), np.uint8), list(range(9)))
+    _check(got, ref, 9)
+
+
+def test_single_qubit_and_gate_free_networks(tnc):
+    gl = C.GateList(3, np.zeros((3, 2)))
+    gl.add((0,), C.H)
+    gl.add((1,), C.haar_1q(np.random.default_rng(1)))
+    bits = C.random_bitstrings(3, 4, 1)
+    ref = O.statevector_amplitudes(gl, bits, [1])
+    got, _ = _run(tnc, gl, bits, [1])
+    _check(got, ref, 3)
+
+
+def test_ghz_full_size(tnc):
+    gl = C.ghz(8, 8)
+    bits = np.array([[0] * 64, [1] * 64], np.uint8)
+    got, _ = _run(tnc, gl, bits)
+    assert np.allclose(got.ravel(), [1 / math.sqrt(2)] * 2, rtol=1e-5, atol=0)
+
+
+def test_mirror_identity(tnc):
+    gl = C.mirror(C.random_2d(4, 4, 6, 2))
+    bits = np.vstack([np.zeros((1, 16), np.uint8), C.random_bitstrings(16, 3, 3)])
+    got, _ = _run(tnc, gl, bits)
+    assert abs(got[0, 0] - 1) < 1e-5
+    assert np.abs(got[1:]).max() < 1e-5
+
+
+def test_tree_order_independence(tnc):
+    gl = C.random_2d(4, 5, 10, 6)
+    bits = C.random_bitstrings(20, 4, 5)
+    ref = O.statevector_amplitudes(gl, bits)
+    vals = []
+    for seed in (1, 2, 3):
+        got, _ = _run(tnc, gl, bits, seed=seed)
+        _check(got, ref, 20)
+        vals.append(got)
+    assert O.rel_error(vals[0], vals[1], 20).max() < 2e-5
+    assert O.rel_error(vals[0], vals[2], 20).max() < 2e-5
+
+
+@pytest.mark.parametrize("cap,group", [(1 << 16, 0), (1 << 17, 3), (1 << 18, 6)])
+def test_slicing(tnc, cap, group):
+    gl = C.random_2d(4, 5, 10, 2)
+    bits = C.random_bitstrings(20, 2, 3)
+    oq = [0, 7]
+    ref = O.statevector_amplitudes(gl, bits, oq)
+    got, p = _run(tnc, gl, bits, oq, mem_cap_bytes=cap, max_group_log2=group)
+    assert p.report["n_sliced"] >= 1
+    _check(got, ref, 20)
+
+
+def test_partial_slice_groups_add_up(tnc):
+    gl = C.random_2d(4, 5, 10, 2)
+    bits = C.random_bitstrings(20, 2, 3)
+    p = tnc.Plan(tnc.Network(gl), open_qubits=[1], max_batch=2, mem_cap_bytes=1 << 16, max_group_log2=0)
+    ng = p.report["n_slice_groups"]
+    assert ng >= 4
+    db = torch.from_numpy(bits).cuda()
+    full = tnc.contract_amplitudes_dbits(p, db)
+    a = tnc.contract_partial(p, db, 0, ng // 3)
+    b = tnc.contract_partial(p, db, ng // 3, ng)
+    torch.cuda.synchronize()
+    assert O.rel_error((a + b).cpu().numpy(), full.cpu().numpy(), 20).max() < 1e-9
+
+
+def test_config0_clifford_twin(tnc):
+    gl, _ = C.config_circuit(0, 3, clifford=True)
+    bits = C.random_bitstrings(16, 8, 2)
+    ref = stabilizer_amplitudes(gl, bits, [0, 5])
+    got, _ = _run(tnc, gl, bits, [0, 5])
+    _check(got, ref, 16)
+
+
+def test_config2_reduced(tnc):
+    gl, info = C.config_circuit(2, 0, reduced=True)
+    ref = O.statevector_amplitudes(gl, info["bits"], info["open"])
+    got, _ = _run(tnc, gl, info["bits"], info["open"])
+    _check(got, ref, 16)
+
+
+def test_config3_reduced_wht(tnc):
+    gl, info = C.config_circuit(3, 0, reduced=True)
+    ref = O.iqp_wht_amplitudes(gl, info["bits"])
+    got, _ = _run(tnc, gl, info["bits"])
+    _check(got, ref, 20)
+
+
+@pytest.mark.parametrize("L", [4, 5])
+def test_config4_layered_instances(tnc, L):
+    gl = C.layered_3d(L, 4, seed=100 + L)
+    bits = C.random_bitstrings(L * L, 16, 1)
+    ref = O.statevector_amplitudes(gl, bits)
+    got, _ = _run(tnc, gl, bits)
+    _check(got, ref, L * L)
+
+
+def test_config3_full_size_transfer_matrix(tnc):
+    """40 qubits, 256 bitstrings: the benchmark workload, FP32 form."""
+    gl, info = C.config_circuit(3, 0)
+    ref = O.iqp_transfer_amplitudes(gl, info["bits"])
+    got, _ = _run(tnc, gl, info["bits"])
+    _check(got, ref, 40)
+
+
+def test_config3_full_size_clifford_twin(tnc):
+    gl, info = C.config_circuit(3, 1, clifford=True)
+    bits = info["bits"][:64]
+    ref = stabilizer_amplitudes(gl, bits)
+    got, _ = _run(tnc, gl, bits)
+    _check(got, ref, 40)
+
+
+def test_workspace_errors(tnc):
+    gl = C.random_2d(3, 3, 4, 1)
+    p = tnc.Plan(tnc.Network(gl))
+    small = torch.empty(max(p.ws_bytes // 2, 256), dtype=torch.uint8, device="cuda")
+    with pytest.raises(tnc.TncError) as ei:
+        tnc.contract_amplitudes(p, np.zeros((1, 9), np.uint8), ws=small)
+    assert ei.value.status == tnc.TNC_ENOMEM
+    big = torch.empty(p.ws_bytes + 512, dtype=torch.uint8, device="cuda")
+    with pytest.raises(tnc.TncError) as ei:
+        tnc.contract_amplitudes(p, np.zeros((1, 9), np.uint8), ws=big[8:])
+    assert ei.value.status == tnc.TNC_EINVAL
+    with pytest.raises(tnc.TncError) as ei:
+        tnc.contract_amplitudes(p, np.zeros((2, 9), np.uint8))
+    assert ei.value.status == tnc.TNC_EINVAL
+
+
+def test_profiling_counts_every_step(tnc):
+    gl = C.random_2d(3, 4, 8, 2)
+    p = tnc.Plan(tnc.Network(gl))
+    p.set_profiling(True)
+    for _ in range(3):
+        tnc.contract_amplitudes(p, np.zeros((1, 12), np.uint8))
+    prof = p.profile()
+    assert (prof["runs"] == 3).all()
+    assert (prof["ms"] > 0).all()
+    assert abs(prof["flops"].sum() - p.report["real_flops"]) / p.report["real_flops"] < 1e-12
