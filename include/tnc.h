@@ -158,6 +158,12 @@ int tnc_plan_set_profiling(tnc_plan_t* plan, int enable);
 int tnc_plan_get_profile(tnc_plan_t* plan, int* n_steps, int cap, double* ms, int* runs, int* kind,
                          double* flops, double* bytes);
 
+/* Device-side error flag of the kernels with bounded waits (the tcgen05
+ * pipeline): 0 if no wait has timed out on the current device since load,
+ * else the code of the first timeout.  Synchronising read; *flag receives the
+ * value.  A set flag means the affected contraction results are invalid. */
+int tnc_device_error(int* flag);
+
 /* Amplitudes for `batch` bitstrings (1 <= batch <= max_batch).
  * bits: HOST uint8 [batch][n_qubits]; entries of open qubits are ignored.
  * d_out: DEVICE complex128 [batch][2^n_open], caller-owned, overwritten.

@@ -16,6 +16,8 @@
 
 namespace tnc {
 
+int read_tc_error(int* flag);
+
 static thread_local std::string g_err;
 
 void set_error(const char* fmt, ...) {
@@ -100,6 +102,8 @@ static void fill_report(Plan& p, double plan_ms) {
     const GemmDesc& g = s.gemm;
     int chunks = (int)((g.batch + 65534) / 65535);
     if (g.kernel == KG_DOT && g.M <= 4 && g.N <= 4)
+      per_group += chunks + 1;
+    else if (g.splitk > 1)
       per_group += chunks + 1;
     else if (g.kernel == KG_TC)
       per_group += 3;
@@ -353,7 +357,14 @@ int tnc_plan_upload(tnc_plan_t* plan, void* stream) {
   Plan& p = plan->p;
   std::lock_guard<std::mutex> lk(p.mu);
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  cudaError_t e;
+  if (stream) {
+    e = cudaStreamGetDevice((cudaStream_t)stream, &dev);
+    if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: cudaStreamGetDevice");
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: cudaSetDevice");
+  }
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: cudaGetDevice");
   if (p.d_base && p.device == dev) return TNC_OK;
   if (p.d_base) {
@@ -409,6 +420,19 @@ static int run(tnc_plan_t* tp, const uint8_t* bits, bool bits_on_device, int bat
   if (g0 < 0 || g1 < g0 || g1 > ngroups) {
     set_error("tnc_contract: slice groups [%d, %d) outside [0, %d)", g0, g1, ngroups);
     return TNC_EINVAL;
+  }
+  // the device is the one owning the workspace (this library keeps its own
+  // CUDA runtime state, so it follows the caller's memory, not a global)
+  {
+    cudaPointerAttributes attr;
+    cudaError_t e0 = cudaPointerGetAttributes(&attr, d_ws);
+    if (e0 != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      set_error("tnc_contract: workspace is not device memory");
+      return TNC_EINVAL;
+    }
+    e0 = cudaSetDevice(attr.device);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "tnc_contract: cudaSetDevice");
   }
   int rc = tnc_plan_upload(tp, stream);
   if (rc != TNC_OK) return rc;
@@ -471,6 +495,16 @@ int run_request(tnc_plan_t* plan, const uint8_t* host_bits, int batch, void* d_o
 }  // namespace tnc
 
 extern "C" {
+
+int tnc_device_error(int* flag) {
+  if (!flag) {
+    set_error("tnc_device_error: NULL argument");
+    return TNC_EINVAL;
+  }
+  int r = tnc::read_tc_error(flag);
+  if (r) return cuda_fail((cudaError_t)r, "tnc_device_error");
+  return TNC_OK;
+}
 
 static void drop_profile(Plan& p) {
   for (auto& r : p.prof) cudaEventDestroy((cudaEvent_t)r.ev);

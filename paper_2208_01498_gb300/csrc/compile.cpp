@@ -562,9 +562,19 @@ int compile_program(Plan& p) {
       g.kernel = KG_SIMT_64x32;
     else
       g.kernel = KG_SIMT_128x64;
+    // long FP32 sums over K are cut into chunks summed in FP64 (split-K)
+    g.splitk = 1;
+    const bool simt = g.kernel == KG_SIMT_128x64 || g.kernel == KG_SIMT_64x32 || g.kernel == KG_SIMT_32x128 ||
+                      (g.kernel == KG_DOT && (g.M > 4 || g.N > 4));
+    if (simt && g.K >= 8192 && (double)g.batch * g.M * g.N <= (double)(1 << 20)) {
+      int64_t s = g.K / 2048;
+      while (s > 1 && (double)s * g.batch * g.M * g.N * 8 > (double)(256u << 20)) s >>= 1;
+      g.splitk = (int)std::min<int64_t>(s, 4096);
+    }
     // per-node scratch
     uint64_t scratch_bytes = 0;
     if (g.kernel == KG_DOT) scratch_bytes = (uint64_t)g.batch * g.M * g.N * 16 * 1024;
+    if (g.splitk > 1) scratch_bytes = std::max<uint64_t>(scratch_bytes, (uint64_t)g.splitk * g.batch * g.M * g.N * 8);
     if (g.kernel == KG_TC) {
       // hi/lo planes: A (batch*M*2K) x 2 and expanded B' (batch*2N*2K) x 2, 2 or 4 bytes each
       uint64_t es = form == TNC_SPLIT_BF16 ? 2 : 4;

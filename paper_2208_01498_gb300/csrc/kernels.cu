@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(kPermThreads) permute_kernel(const float2* __r
 template <int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     cgemm_simt_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
-                      int64_t M, int64_t N, int64_t K, int transA, int transB, int64_t b0) {
+                      int64_t M, int64_t N, int64_t K, int transA, int transB, int64_t b0, int64_t kchunk,
+                      int64_t part_stride) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
   __shared__ __align__(16) float2 As[BK][BM];
@@ -111,7 +112,9 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   const int64_t bz = b0 + blockIdx.z;
   A += bz * M * K;
   B += bz * K * N;
-  C += bz * M * N;
+  C += bz * M * N + (int64_t)blockIdx.y * part_stride;
+  const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
+  const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
   const int64_t mt = (M + BM - 1) / BM;
   const int64_t m0 = ((int64_t)blockIdx.x % mt) * BM, n0 = ((int64_t)blockIdx.x / mt) * BN;
   float2 acc[TM][TN];
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = make_float2(0.f, 0.f);
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int e = tid; e < BM * BK; e += NT) {
       int mm, kk;
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       }
       int64_t m = m0 + mm, k = k0 + kk;
       float2 v = make_float2(0.f, 0.f);
-      if (m < M && k < K) v = transA ? A[k * M + m] : A[m * K + k];
+      if (m < M && k < kend) v = transA ? A[k * M + m] : A[m * K + k];
       As[kk][mm] = v;
     }
 #pragma unroll
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       }
       int64_t n = n0 + nn, k = k0 + kk;
       float2 v = make_float2(0.f, 0.f);
-      if (n < N && k < K) v = transB ? B[n * K + k] : B[k * N + n];
+      if (n < N && k < kend) v = transB ? B[n * K + k] : B[k * N + n];
       Bs[kk][nn] = v;
     }
     __syncthreads();
@@ -303,15 +306,40 @@ __global__ void accum_kernel(const float2* __restrict__ root, double2* __restric
   }
 }
 
+__global__ void splitk_reduce_kernel(const float2* __restrict__ part, float2* __restrict__ C, int splits,
+                                     int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double x = 0, y = 0;
+    for (int s = 0; s < splits; ++s) {
+      float2 v = part[(int64_t)s * n + i];
+      x += v.x, y += v.y;
+    }
+    C[i] = make_float2((float)x, (float)y);
+  }
+}
+
 template <int BM, int BN, int BK, int TM, int TN>
-int run_simt(const GemmDesc& d, const float2* A, const float2* B, float2* C, cudaStream_t st) {
+int run_simt(const GemmDesc& d, const float2* A, const float2* B, float2* C, float2* ws, cudaStream_t st) {
   constexpr int NT = (BM / TM) * (BN / TN);
   const int64_t mt = (d.M + BM - 1) / BM, nt = (d.N + BN - 1) / BN;
   if (mt * nt > 0x7fffffff) return (int)cudaErrorInvalidConfiguration;
+  const int splits = d.splitk > 1 ? d.splitk : 1;
+  const int64_t nout = d.batch * d.M * d.N;
+  float2* dst = C;
+  if (splits > 1) {
+    if ((uint64_t)splits * nout > d.scratch_elems) return (int)cudaErrorInvalidValue;
+    dst = ws + d.scratch;
+  }
+  const int64_t kchunk = (d.K + splits - 1) / splits;
   for (int64_t b0 = 0; b0 < d.batch; b0 += 65535) {
     int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
-    dim3 grid((unsigned)(mt * nt), 1, (unsigned)nb);
-    cgemm_simt_kernel<BM, BN, BK, TM, TN><<<grid, NT, 0, st>>>(A, B, C, d.M, d.N, d.K, d.transA, d.transB, b0);
+    dim3 grid((unsigned)(mt * nt), (unsigned)splits, (unsigned)nb);
+    cgemm_simt_kernel<BM, BN, BK, TM, TN><<<grid, NT, 0, st>>>(A, B, dst, d.M, d.N, d.K, d.transA, d.transB, b0,
+                                                                kchunk, nout);
+  }
+  if (splits > 1) {
+    unsigned blocks = (unsigned)((nout + 255) / 256 < 152 * 16 ? (nout + 255) / 256 : 152 * 16);
+    splitk_reduce_kernel<<<blocks, 256, 0, st>>>(dst, C, splits, nout);
   }
   return (int)cudaGetLastError();
 }
@@ -402,11 +430,11 @@ int launch_gemm(const GemmDesc& d, const void* base, void* ws, void* stream) {
   float2* C = (float2*)ws + d.c;
   switch (d.kernel) {
     case KG_SIMT_128x64:
-      return run_simt<128, 64, 8, 8, 4>(d, A, B, C, st);
+      return run_simt<128, 64, 8, 8, 4>(d, A, B, C, (float2*)ws, st);
     case KG_SIMT_64x32:
-      return run_simt<64, 32, 8, 4, 4>(d, A, B, C, st);
+      return run_simt<64, 32, 8, 4, 4>(d, A, B, C, (float2*)ws, st);
     case KG_SIMT_32x128:
-      return run_simt<32, 128, 8, 4, 4>(d, A, B, C, st);
+      return run_simt<32, 128, 8, 4, 4>(d, A, B, C, (float2*)ws, st);
     case KG_NARROW: {
       if (d.N > 16 || d.K > 16) return (int)cudaErrorInvalidValue;
       int64_t blocks = (d.M + 255) / 256;
@@ -419,7 +447,7 @@ int launch_gemm(const GemmDesc& d, const void* base, void* ws, void* stream) {
       return (int)cudaGetLastError();
     }
     case KG_DOT: {
-      if (d.M * d.N > 16 || d.M > 4 || d.N > 4) return run_simt<64, 32, 8, 4, 4>(d, A, B, C, st);
+      if (d.M * d.N > 16 || d.M > 4 || d.N > 4) return run_simt<64, 32, 8, 4, 4>(d, A, B, C, (float2*)ws, st);
       double2* part = (double2*)((float2*)ws + d.scratch);
       const int MN = (int)(d.M * d.N);
       int64_t nblk = (d.K + kDotThreads * 32 - 1) / (kDotThreads * 32);

@@ -150,8 +150,15 @@ int tnc_server_create(void* d_arena, size_t arena_bytes, int n_streams, tnc_serv
     return TNC_EINVAL;
   }
   *out = nullptr;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, d_arena) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    set_error("tnc_server_create: arena is not device memory");
+    return TNC_EINVAL;
+  }
+  cudaSetDevice(attr.device);
   auto* s = new tnc_server();
-  cudaGetDevice(&s->device);
+  s->device = attr.device;
   s->arena = (char*)d_arena;
   s->arena_bytes = arena_bytes;
   for (int i = 0; i < n_streams; ++i) {

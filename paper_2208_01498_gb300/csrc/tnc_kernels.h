@@ -53,6 +53,8 @@ struct GemmDesc {
   int form;              // TNC_FP32 / TNC_3XTF32 / TNC_SPLIT_BF16
   uint64_t scratch;      // workspace element offset of per-node scratch (0 if none)
   uint64_t scratch_elems;
+  int splitk;            // CUDA-core kernels: K split into this many FP32 chunks summed in FP64
+  int pad_;
 };
 
 // Final accumulation: out[beta][j] += sum over the bits of the grouped

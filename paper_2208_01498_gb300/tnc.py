@@ -62,7 +62,7 @@ EXPORTED = [
     "tnc_plan_export_json", "tnc_plan_upload", "tnc_contract_amplitudes",
     "tnc_contract_amplitudes_dbits", "tnc_contract_partial", "tnc_server_create",
     "tnc_server_submit", "tnc_server_poll", "tnc_server_wait", "tnc_server_cancel",
-    "tnc_server_destroy", "tnc_plan_set_profiling", "tnc_plan_get_profile",
+    "tnc_server_destroy", "tnc_plan_set_profiling", "tnc_plan_get_profile", "tnc_device_error",
 ]
 
 
@@ -92,6 +92,7 @@ def _load():
         "tnc_server_cancel": (i, [vp, u64]),
         "tnc_server_destroy": (i, [vp]),
         "tnc_plan_set_profiling": (i, [vp, i]),
+        "tnc_device_error": (i, [C.POINTER(i)]),
         "tnc_plan_get_profile": (i, [vp, C.POINTER(i), i, C.POINTER(C.c_double), C.POINTER(i),
                                      C.POINTER(i), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     }

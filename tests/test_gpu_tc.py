@@ -1,0 +1,73 @@
+"""Parity of the tensor-core forms (split-BF16 and 3xTF32 on tcgen05) with the
+FP64 oracle and with the FP32 CUDA-core form (GPU)."""
+import numpy as np
+import pytest
+
+import circuits as C
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "3xtf32": 1e-5, "split_bf16": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def tnc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_01498_gb300 import tnc as t
+    return t
+
+
+def _run(tnc, gl, bits, form, oq=(), **kw):
+    p = tnc.Plan(tnc.Network(gl), open_qubits=oq, max_batch=bits.shape[0], form=form, **kw)
+    out = tnc.contract_amplitudes(p, bits)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), p
+
+
+def _n_tc(p):
+    return sum(1 for s in p.export()["steps"] if s["kind"] == 1 and s["kernel"] == 4)
+
+
+@pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
+def test_single_tensor_core_node(tnc, form):
+    gl = C.random_2d(4, 5, 10, 2)
+    bits = C.random_bitstrings(20, 16, 4)
+    ref = O.statevector_amplitudes(gl, bits)
+    got, p = _run(tnc, gl, bits, form)
+    assert _n_tc(p) >= 1
+    assert O.rel_error(got, ref, 20).max() <= TOL[form]
+
+
+@pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
+def test_config3_full_size(tnc, form):
+    """The benchmark workload (40 qubits, 256 bitstrings) against the
+    transfer-matrix closed form, and against the FP32 form."""
+    gl, info = C.config_circuit(3, 0)
+    ref = O.iqp_transfer_amplitudes(gl, info["bits"])
+    got, p = _run(tnc, gl, info["bits"], form)
+    assert _n_tc(p) >= 3
+    assert O.rel_error(got, ref, 40).max() <= TOL[form]
+    fp32, _ = _run(tnc, gl, info["bits"], "fp32")
+    assert O.rel_error(got, fp32, 40).max() <= TOL[form] + TOL["fp32"]
+
+
+@pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
+def test_dense_batched_nodes_random_2d(tnc, form):
+    gl = C.random_2d(5, 5, 12, 9)
+    bits = C.random_bitstrings(25, 64, 2)
+    ref = O.statevector_amplitudes(gl, bits)
+    got, p = _run(tnc, gl, bits, form)
+    assert O.rel_error(got, ref, 25).max() <= TOL[form]
+
+
+def test_tensor_core_error_flag_clear(tnc):
+    """No bounded wait of the tcgen05 kernel timed out during the tests."""
+    import ctypes
+    gl = C.random_2d(4, 5, 10, 2)
+    _run(tnc, gl, C.random_bitstrings(20, 16, 4), "split_bf16")
+    flag = ctypes.c_int(-1)
+    assert tnc.lib.tnc_device_error(ctypes.byref(flag)) == 0
+    assert flag.value == 0
