@@ -12,12 +12,13 @@
 // prep kernels write the hi/lo planes K-major into the node's workspace
 // scratch: A' as [b][M][2K], B'^T as [b][2N][2K].  The GEMM kernel computes one
 // 128 x BN output tile per CTA: warp 0 issues TMA loads (128B-swizzled boxes
-// of 128 B rows) into a STAGES-deep shared-memory ring guarded by mbarriers,
-// warp 1 (one lane) issues tcgen05.mma into a 128 x BN FP32 accumulator in
-// TMEM, then all four warps drain TMEM with tcgen05.ld and store C.  Every
-// wait is bounded by a time limit; a timeout sets tc_error and the CTA
-// skips to teardown (waiting, bounded, for its own TMA copies and MMAs, then
-// freeing its TMEM).
+// of 128-byte rows) into a STAGES-deep shared-memory ring guarded by
+// mbarriers, warp 1 (one lane) issues tcgen05.mma into one of two 128 x BN FP32
+// accumulators in TMEM (alternating every 512 k'), and warps 2..5 add each
+// finished accumulator into FP32 registers with tcgen05.ld, then store C.
+// Every wait is bounded by a time limit; a timeout sets tc_error_flag and the
+// CTA skips to teardown (waiting, bounded, for its own TMA copies and MMAs,
+// then freeing its TMEM).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -35,7 +36,6 @@ __device__ int tc_error_flag = 0;
 namespace {
 
 constexpr int BM = 128;
-constexpr int kThreads = 128;
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -158,15 +158,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ------------------------------------------------------------ GEMM kernel
-// D[b][m][n'] = sum_k' A'[b][m][k'] B'^T[b][n'][k'], 3 products per k-step
+// D[b][m][n'] = sum_k' A'[b][m][k'] B'^T[b][n'][k'], 3 products per k-step.
+// Warp 0: TMA producer; warp 1: MMA issuer; warps 2..5: accumulation and
+// epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31).  The K range is cut
+// into chunks of CHUNK k-blocks; chunk c accumulates in TMEM slot c % 2 and
+// the epilogue warps add each finished slot into FP32 registers while the
+// other slot fills, so no tensor-core accumulation chain is longer than one
+// chunk.
+constexpr int kTcThreads = 192;
+
 template <bool kTF32, int BN, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
                    const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
                    float* __restrict__ C, int M, int N2, int K2, int b0) {
   constexpr int ES = kTF32 ? 4 : 2;
   constexpr int BK = 128 / ES;            // elements per 128-byte row
   constexpr int KSTEP = kTF32 ? 8 : 16;   // K of one MMA instruction
+  constexpr int CHUNK = 512 / BK;         // k-blocks per accumulation chunk (512 k')
   constexpr uint32_t A_BYTES = BM * 128, B_BYTES = BN * 128;
   constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   constexpr uint32_t IDESC = instr_desc<kTF32, BN>();
@@ -175,7 +184,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
+  uint64_t* acc_full = empty + STAGES;   // [2]
+  uint64_t* acc_empty = acc_full + 2;    // [2]
+  uint64_t* done = acc_empty + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   int* abort_flag = (int*)(tmem_slot + 1);
 
@@ -185,84 +196,126 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int n0 = (blockIdx.x / tiles_m) * BN;
   const int bz = b0 + blockIdx.z;
   const int nk = K2 / BK;
+  const int nchunks = (nk + CHUNK - 1) / CHUNK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&acc_full[s], 1);
+      mbar_init(&acc_empty[s], 128);
+    }
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(tmem_slot, BN);
+  if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
   int issued = 0;  // producer: k-blocks whose loads were issued
-  if (warp == 0 && lane == 0) {
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) + 1) & 1)) {
-        atomicExch(&tc_error_flag, 1);
-        *(volatile int*)abort_flag = 1;
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) + 1) & 1)) {
+          atomicExch(&tc_error_flag, 1);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        if (*(volatile int*)abort_flag) break;
+        uint8_t* st = smem + s * STAGE_BYTES;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        tma_load_3d(st, &mA_hi, &full[s], kb * BK, m0, bz);
+        tma_load_3d(st + A_BYTES, &mA_lo, &full[s], kb * BK, m0, bz);
+        tma_load_3d(st + 2 * A_BYTES, &mB_hi, &full[s], kb * BK, n0, bz);
+        tma_load_3d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], kb * BK, n0, bz);
+        issued = kb + 1;
       }
-      if (*(volatile int*)abort_flag) break;
-      uint8_t* st = smem + s * STAGE_BYTES;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_3d(st, &mA_hi, &full[s], kb * BK, m0, bz);
-      tma_load_3d(st + A_BYTES, &mA_lo, &full[s], kb * BK, m0, bz);
-      tma_load_3d(st + 2 * A_BYTES, &mB_hi, &full[s], kb * BK, n0, bz);
-      tma_load_3d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], kb * BK, n0, bz);
-      issued = kb + 1;
     }
-  } else if (warp == 1 && lane == 0) {
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
-        atomicExch(&tc_error_flag, 2);
-        *(volatile int*)abort_flag = 1;
-        break;
-      }
-      if (*(volatile int*)abort_flag) break;
-      tc_fence_after();
-      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-      const uint64_t dAh = sw128_desc(sa), dAl = sw128_desc(sa + A_BYTES);
-      const uint64_t dBh = sw128_desc(sa + 2 * A_BYTES), dBl = sw128_desc(sa + 2 * A_BYTES + B_BYTES);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int slot = c & 1;
+        if (c >= 2 && !mbar_wait(&acc_empty[slot], ((c >> 1) + 1) & 1)) {
+          atomicExch(&tc_error_flag, 4);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        const uint32_t dtm = tmem + slot * BN;
+        const int kb_end = (c + 1) * CHUNK < nk ? (c + 1) * CHUNK : nk;
+        for (int kb = c * CHUNK; kb < kb_end; ++kb) {
+          const int s = kb % STAGES;
+          if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+            atomicExch(&tc_error_flag, 2);
+            *(volatile int*)abort_flag = 1;
+            ok = false;
+            break;
+          }
+          if (*(volatile int*)abort_flag) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+          const uint64_t dAh = sw128_desc(sa), dAl = sw128_desc(sa + A_BYTES);
+          const uint64_t dBh = sw128_desc(sa + 2 * A_BYTES), dBl = sw128_desc(sa + 2 * A_BYTES + B_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < BK / KSTEP; ++kk) {
-        const uint64_t adv = (uint64_t)((kk * KSTEP * ES) >> 4);
-        const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-        mma<kTF32>(tmem, dAh + adv, dBh + adv, IDESC, first);
-        mma<kTF32>(tmem, dAh + adv, dBl + adv, IDESC, 1u);
-        mma<kTF32>(tmem, dAl + adv, dBh + adv, IDESC, 1u);
+          for (int kk = 0; kk < BK / KSTEP; ++kk) {
+            const uint64_t adv = (uint64_t)((kk * KSTEP * ES) >> 4);
+            const uint32_t first = (kb == c * CHUNK && kk == 0) ? 0u : 1u;
+            mma<kTF32>(dtm, dAh + adv, dBh + adv, IDESC, first);
+            mma<kTF32>(dtm, dAh + adv, dBl + adv, IDESC, 1u);
+            mma<kTF32>(dtm, dAl + adv, dBh + adv, IDESC, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&acc_full[slot]);
       }
-      mma_commit(&empty[s]);
+      // completion of every MMA issued so far
+      mma_commit(done);
     }
-    // completion of every MMA issued so far
-    mma_commit(done);
-  }
-  // epilogue: TMEM lane = tile row; thread (warp w, lane l) owns row 32 w + l
-  const bool ok = mbar_wait(done, 0);
-  if (!ok) atomicExch(&tc_error_flag, 3);
-  tc_fence_after();
-  if (ok && !*(volatile int*)abort_flag) {
-    const int row = m0 + warp * 32 + lane;
-    float* crow = C + ((int64_t)bz * M + row) * N2 + n0;
-#pragma unroll 1
-    for (int c = 0; c < BN; c += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
-      float4* dst = (float4*)(crow + c);
-      dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-      dst[1] = make_float4(v[4], v[5], v[6], v[7]);
-      dst[2] = make_float4(v[8], v[9], v[10], v[11]);
-      dst[3] = make_float4(v[12], v[13], v[14], v[15]);
+  } else {
+    // accumulation warps: row 32 (warp % 4) + lane of the tile
+    const int quarter = warp & 3;
+    float acc[BN];
+#pragma unroll
+    for (int i = 0; i < BN; ++i) acc[i] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int slot = c & 1;
+      if (!mbar_wait(&acc_full[slot], (c >> 1) & 1)) {
+        atomicExch(&tc_error_flag, 3);
+        *(volatile int*)abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + slot * BN;
+#pragma unroll
+      for (int col = 0; col < BN; col += 16) {
+        float v[16];
+        tmem_ld16(taddr + col, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[col + i] += v[i];
+      }
+      tc_fence_before();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[slot])) : "memory");
+    }
+    if (ok && !*(volatile int*)abort_flag) {
+      const int row = m0 + quarter * 32 + lane;
+      float4* dst = (float4*)(C + ((int64_t)bz * M + row) * N2 + n0);
+#pragma unroll
+      for (int i = 0; i < BN / 4; ++i) dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
     }
   }
+  // all MMAs retired before TMEM is freed
+  if (threadIdx.x == 0 && !mbar_wait(done, 0)) atomicExch(&tc_error_flag, 5);
   tc_fence_before();
   __syncthreads();
   // teardown after an abort: wait (bounded) for TMA copies still in flight
@@ -273,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, BN);
+    tmem_dealloc(tmem, 2 * BN);
   }
 }
 
@@ -378,7 +431,7 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
   if ((r = make_map(&mBh, b_hi, kTF32, K2, N2, nb, BN))) return r;
   if ((r = make_map(&mBl, b_lo, kTF32, K2, N2, nb, BN))) return r;
   constexpr uint32_t STAGE_BYTES = 2 * BM * 128 + 2 * BN * 128;
-  const size_t smem = 1024 + STAGES * STAGE_BYTES + (2 * STAGES + 1) * 8 + 16;
+  const size_t smem = 1024 + STAGES * STAGE_BYTES + (2 * STAGES + 5) * 8 + 16;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kTF32, BN, STAGES>,
@@ -390,7 +443,7 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
   for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
     int64_t cnt = nb - b0 < 65535 ? nb - b0 : 65535;
     dim3 grid((unsigned)tiles, 1, (unsigned)cnt);
-    tc_gemm_kernel<kTF32, BN, STAGES><<<grid, kThreads, smem, st>>>(mAh, mAl, mBh, mBl, C, (int)M, (int)N2,
+    tc_gemm_kernel<kTF32, BN, STAGES><<<grid, kTcThreads, smem, st>>>(mAh, mAl, mBh, mBl, C, (int)M, (int)N2,
                                                                      (int)K2, (int)b0);
   }
   return (int)cudaGetLastError();
