@@ -37,7 +37,8 @@ sys.path.insert(0, ROOT)
 import circuits as C  # noqa: E402
 
 REQ_BATCH = 256
-WORKLOAD = "iqp_5x8_40q_256_bitstrings"
+def workload_name(rows, cols):
+    return f"iqp_{rows}x{cols}_{rows * cols}q_256_bitstrings"
 
 
 def _peaks():
@@ -102,8 +103,8 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _workload(seed: int, steps: int):
-    gl, _ = C.config_circuit(3, seed)
+def _workload(seed: int, steps: int, rows: int = 5, cols: int = 8):
+    gl = C.iqp(rows, cols, seed)
     bits = np.stack([C.random_bitstrings(gl.n_qubits, REQ_BATCH, seed * 100003 + i) for i in range(steps)])
     return gl, bits
 
@@ -126,7 +127,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    gl, bits = _workload(args.seed, args.warmup + args.steps)
+    gl, bits = _workload(args.seed, args.warmup + args.steps, args.rows, args.cols)
     import oracle as O
     sample = 16  # bitstrings per step: a bounded slice of one request
     for w in range(args.warmup):
@@ -140,7 +141,8 @@ def run_reference(args):
         "impl": "reference", "metric": "amplitudes/s", "value": val, "unit": "amplitudes/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "bitstrings_per_step": sample, "seed": args.seed},
+        "config": {"workload": workload_name(args.rows, args.cols), "bitstrings_per_step": sample,
+                   "seed": args.seed},
         "cpu_baseline": {"value": val, "unit": "amplitudes/s", "cores": 1, "kind": "oracle",
                          "sample": f"{sample} of the 256 bitstrings of each request, IQP transfer-matrix "
                                    f"closed form (numpy, single thread; host has {os.cpu_count()} cores)"},
@@ -163,7 +165,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    gl, bits = _workload(args.seed + rank, args.warmup + args.steps)
+    gl, bits = _workload(args.seed + rank, args.warmup + args.steps, args.rows, args.cols)
     net = tnc.Network(gl)
     plan = tnc.Plan(net, max_batch=REQ_BATCH, form=args.form, seed=1, ssa_trials=64)
     rep = plan.report
@@ -229,10 +231,10 @@ def run_ours(args):
         if runs == 0:
             continue
         d = kinds.setdefault(int(kind), {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 0})
-        d["ms"] += ms
-        d["flops"] += fl * runs
-        d["bytes"] += by * runs
-        d["launches"] += runs
+        d["ms"] += float(ms)
+        d["flops"] += float(fl) * int(runs)
+        d["bytes"] += float(by) * int(runs)
+        d["launches"] += int(runs)
     total_ms = sum(d["ms"] for d in kinds.values())
     dom = max(kinds, key=lambda k: kinds[k]["ms"])
     d = kinds[dom]
@@ -256,6 +258,11 @@ def run_ours(args):
     roof["kernel"] = names.get(dom, str(dom))
     roof["share_of_device_time"] = d["ms"] / total_ms if total_ms else None
     roof["peak_source"] = src
+    breakdown = {}
+    for kd, v in sorted(kinds.items(), key=lambda kv: -kv[1]["ms"]):
+        s = v["ms"] / 1e3
+        breakdown[names.get(kd, str(kd))] = {"share": v["ms"] / total_ms, "launches": v["launches"],
+                                              "GB/s": v["bytes"] / s / 1e9, "TFLOP/s": v["flops"] / s / 1e12}
 
     line = {
         "metric": "amplitudes/s", "value": value, "unit": "amplitudes/s", "n_gpus": world,
@@ -263,13 +270,14 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "c64", "3xtf32": "tf32x3 (fp32 acc)", "split_bf16": "bf16x3 (fp32 acc)"}[args.form],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": args.form, "bitstrings_per_request": REQ_BATCH,
+        "config": {"workload": workload_name(args.rows, args.cols), "form": args.form, "bitstrings_per_request": REQ_BATCH,
                    "seed": args.seed, "real_tflop_per_request": rep["real_flops"] / 1e12,
                    "paper_ops_log2": rep["tree_cost_log2"], "ws_bytes": rep["ws_bytes"],
                    "l2": f"working set {rep['ws_bytes'] / 1e9:.1f} GB per request > 129 MB L2",
                    "parallelism": f"dp{world} (independent requests)"},
         "effective_tflops": world * args.steps * rep["real_flops"] / (t_ms / 1e3) / 1e12,
         "roofline": roof,
+        "kernel_breakdown": breakdown,
         "e2e": e2e,
         "clocks": ck,
         "gpu_launches": int(args.steps * rep["n_launches"]),
@@ -296,6 +304,8 @@ def main():
     ap.add_argument("--form", choices=["fp32", "3xtf32", "split_bf16"], default="fp32")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", type=int, default=5, help="IQP lattice rows (the benchmark uses 5 x 8)")
+    ap.add_argument("--cols", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -14,8 +14,9 @@
 // 128 x BN output tile per CTA: warp 0 issues TMA loads (128B-swizzled boxes
 // of 128-byte rows) into a STAGES-deep shared-memory ring guarded by
 // mbarriers, warp 1 (one lane) issues tcgen05.mma into one of two 128 x BN FP32
-// accumulators in TMEM (alternating every 512 k'), and warps 2..5 add each
-// finished accumulator into FP32 registers with tcgen05.ld, then store C.
+// accumulators in TMEM (alternating every 512 k' for bf16, 128 k' for tf32),
+// and warps 2..5 add each finished accumulator into FP32 registers with
+// tcgen05.ld, then store C.
 // Every wait is bounded by a time limit; a timeout sets tc_error_flag and the
 // CTA skips to teardown (waiting, bounded, for its own TMA copies and MMAs,
 // then freeing its TMEM).
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   constexpr int ES = kTF32 ? 4 : 2;
   constexpr int BK = 128 / ES;            // elements per 128-byte row
   constexpr int KSTEP = kTF32 ? 8 : 16;   // K of one MMA instruction
-  constexpr int CHUNK = 512 / BK;         // k-blocks per accumulation chunk (512 k')
+  constexpr int CHUNK = (kTF32 ? 128 : 512) / BK;  // k-blocks per accumulation chunk
   constexpr uint32_t A_BYTES = BM * 128, B_BYTES = BN * 128;
   constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   constexpr uint32_t IDESC = instr_desc<kTF32, BN>();
