@@ -179,6 +179,26 @@ int tnc_contract_amplitudes(tnc_plan_t* plan, const uint8_t* bits, int batch, vo
 int tnc_contract_amplitudes_dbits(tnc_plan_t* plan, const uint8_t* d_bits, int batch,
                                   void* d_out, void* d_ws, size_t ws_bytes, void* cuda_stream);
 
+/* Same as tnc_contract_amplitudes, for callers that cannot allocate device
+ * memory when they need amplitudes (code running while a CUDA graph is being
+ * captured, a host framework whose allocator owns all device memory, a
+ * plugin whose host forbids allocation after start-up).  The paper has no
+ * counterpart: this is a deployment variant of the same contraction.
+ * The workspace is a 64 MiB array that the library holds statically on every
+ * GPU that loads it, until exit; nothing is allocated by the call.
+ * - The plan must already be resident on d_out's device (tnc_plan_upload),
+ *   else TNC_ESTATE; profiling must be off, else TNC_ESTATE.
+ * - A plan whose workspace (report.ws_bytes) exceeds 64 MiB: TNC_ENOMEM.
+ * - The first call on a device looks up the array's device address once;
+ *   make that first call before any stream capture.
+ * - All calls share the array and it keeps the last call's contents; each
+ *   call re-initialises what must start at zero.  Calls whose GPU work
+ *   overlaps (several streams or threads) race on it: serialise them.
+ * bits: HOST uint8 [batch][n_qubits]; d_out: DEVICE complex128
+ * [batch][2^n_open]; enqueued on cuda_stream like tnc_contract_amplitudes. */
+int tnc_contract_amplitudes_static(tnc_plan_t* plan, const uint8_t* bits, int batch, void* d_out,
+                                   void* cuda_stream);
+
 /* Partial sum over the serial slice groups [group_begin, group_end) only
  * (0 <= begin <= end <= n_slice_groups): the slice-sharded form used when
  * several processes each own a range of slices; the partial results add up

@@ -63,6 +63,7 @@ EXPORTED = [
     "tnc_contract_amplitudes_dbits", "tnc_contract_partial", "tnc_server_create",
     "tnc_server_submit", "tnc_server_poll", "tnc_server_wait", "tnc_server_cancel",
     "tnc_server_destroy", "tnc_plan_set_profiling", "tnc_plan_get_profile", "tnc_device_error",
+    "tnc_contract_amplitudes_static",
 ]
 
 
@@ -93,6 +94,7 @@ def _load():
         "tnc_server_destroy": (i, [vp]),
         "tnc_plan_set_profiling": (i, [vp, i]),
         "tnc_device_error": (i, [C.POINTER(i)]),
+        "tnc_contract_amplitudes_static": (i, [vp, vp, i, vp, vp]),
         "tnc_plan_get_profile": (i, [vp, C.POINTER(i), i, C.POINTER(C.c_double), C.POINTER(i),
                                      C.POINTER(i), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     }
@@ -285,4 +287,16 @@ def contract_partial(p: Plan, d_bits, group_begin: int, group_end: int, out=None
     _check(lib.tnc_contract_partial(p.handle, C.c_void_p(d_bits.data_ptr()), batch, int(group_begin),
                                     int(group_end), C.c_void_p(out.data_ptr()), C.c_void_p(ws.data_ptr()),
                                     ws.numel(), _stream_ptr(stream)), "tnc_contract_partial")
+    return out
+
+
+def contract_amplitudes_static(p: Plan, bits, out, stream=None):
+    """``tnc_contract_amplitudes_static``: same result as
+    :func:`contract_amplitudes` with the library's static 64 MiB workspace;
+    the plan must be uploaded first and ``out`` preallocated (nothing is
+    allocated by this call)."""
+    bits = np.ascontiguousarray(np.atleast_2d(bits), dtype=np.uint8)
+    _check(lib.tnc_contract_amplitudes_static(p.handle, bits.ctypes.data_as(C.c_void_p), bits.shape[0],
+                                              C.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+           "tnc_contract_amplitudes_static")
     return out
