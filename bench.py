@@ -205,6 +205,31 @@ def run_ours(args):
     amps = world * args.steps * REQ_BATCH
     value = amps / (t_ms / 1e3)
 
+    last_out = out.clone()
+
+    # ---- the FP32 CUDA-core form on the same requests (the metric's reference form)
+    fp32_form = None
+    if args.form != "fp32":
+        p32 = tnc.Plan(net, max_batch=REQ_BATCH, form="fp32", seed=1, ssa_trials=64)
+        ws32 = tnc.alloc_workspace(p32)
+        out32 = torch.empty_like(out)
+        for w in range(args.warmup):
+            tnc.contract_amplitudes_dbits(p32, d_bits[w], out=out32, ws=ws32, stream=stream)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for k in range(args.steps):
+            tnc.contract_amplitudes_dbits(p32, d_bits[args.warmup + k], out=out32, ws=ws32, stream=stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t32 = f0.elapsed_time(f1)
+        a, r = last_out.cpu().numpy(), out32.cpu().numpy()
+        floor = 2.0 ** (-gl.n_qubits / 2)
+        rel = float(np.max(np.abs(a - r) / np.maximum(np.abs(r), floor)))
+        fp32_form = {"value": world * args.steps * REQ_BATCH / (t32 / 1e3), "unit": "amplitudes/s",
+                     "ms_per_step": t32 / args.steps, "max_rel_err_vs_fp32": rel}
+        del ws32
+
     # ---- end to end through the host-buffer API
     pinned = torch.from_numpy(bits).pin_memory()
     res = torch.empty((REQ_BATCH, 1), dtype=torch.complex128).pin_memory()
@@ -278,6 +303,7 @@ def run_ours(args):
         "effective_tflops": world * args.steps * rep["real_flops"] / (t_ms / 1e3) / 1e12,
         "roofline": roof,
         "kernel_breakdown": breakdown,
+        "fp32_form": fp32_form,
         "e2e": e2e,
         "clocks": ck,
         "gpu_launches": int(args.steps * rep["n_launches"]),
@@ -301,7 +327,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["fp32", "3xtf32", "split_bf16"], default="fp32")
+    ap.add_argument("--form", choices=["fp32", "3xtf32", "split_bf16"], default="split_bf16")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows", type=int, default=5, help="IQP lattice rows (the benchmark uses 5 x 8)")
