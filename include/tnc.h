@@ -119,6 +119,23 @@ void tnc_free_network(tnc_network_t* net);
  * trials, leaf size 8, group log2 6). */
 void tnc_plan_opts_default(tnc_plan_opts* opts);
 
+/* ------------------------------------------------- planner primitives (host)
+ * tnc_ssa_separate: one application of the Sphere Separator Algorithm
+ * (Algorithm 1, Supplemental Material) to n spheres in R^dim (dim 1..3),
+ * centres pos[n][dim], radii rad[n].  side[i] receives the class of sphere i
+ * with respect to the separator kept: 0 inside (Gamma_I), 1 outside
+ * (Gamma_E), 2 intersected (Gamma_O).  *valid = 1 if it satisfies Eqs. (1)
+ * and (2) of the Sphere Separator Theorem (|Gamma_O| <= c_d k^(1/d)
+ * n^(1-1/d), |Gamma_E|, |Gamma_I| <= (d+1)/(d+2) n), 0 if no trial did and a
+ * fallback split was kept; *k receives the overlap number used in Eq. (1)
+ * (most spheres containing one sphere centre). */
+int tnc_ssa_separate(const double* pos, const double* rad, int n, int dim, uint64_t seed, int trials, int* side,
+                     int* valid, int* k);
+
+/* tnc_centerpoint: approximate centerpoint (Algorithm 1 step 2) of n points
+ * in R^D (D <= 4), pts[n][D], by iterated Radon points; c[D] receives it. */
+int tnc_centerpoint(const double* pts, int n, int D, uint64_t seed, double* c);
+
 /* Plan the contraction (host only, no GPU needed): separator hierarchy
  * (Thm. 1 proof, Algorithm 1), greedy leaves, index slicing to meet
  * mem_cap_bytes, and the compiled node program.  The plan keeps what it needs
@@ -157,6 +174,32 @@ int tnc_plan_set_profiling(tnc_plan_t* plan, int enable);
 #define TNC_STEP_PERMUTE 100
 int tnc_plan_get_profile(tnc_plan_t* plan, int* n_steps, int cap, double* ms, int* runs, int* kind,
                          double* flops, double* bytes);
+
+/* ------------------------------------------------- kernel-level entry points
+ * The two steps of one tree node, callable on their own (for unit tests and
+ * micro-benchmarks of the kernels).  All pointers DEVICE; enqueued on
+ * cuda_stream; the device is the one owning the output pointer.
+ *
+ * tnc_permute: the index permutation of a node operand.  A dense complex64
+ * tensor of 2^rank elements with binary indices (rank <= 40); out[j] = in[i]
+ * where bit src_bit[k] of i equals bit k of j (bits counted from the least
+ * significant end; src_bit a permutation of 0..rank-1).  d_in and d_out must
+ * not overlap.  TNC_EINVAL for a bad permutation. */
+int tnc_permute(const void* d_in, void* d_out, int rank, const int* src_bit, void* cuda_stream);
+
+/* Scratch bytes tnc_cgemm needs for this shape and form (0 if none). */
+size_t tnc_cgemm_scratch_bytes(int64_t batch, int64_t M, int64_t N, int64_t K, int form);
+
+/* tnc_cgemm: one pairwise contraction (Eq. 3: M_paper = batch*M*N*K
+ * multiplications) as a batched complex GEMM,
+ * C[b][m][n] = sum_k A[b][m][k] B[b][k][n], complex64 in and out; A stored
+ * [b][M][K] ([b][K][M] if transA), B stored [b][K][N] ([b][N][K] if transB),
+ * C stored [b][M][N].  form as in tnc_plan_opts; the kernel variant is chosen
+ * by shape exactly as in a plan (tensor cores only for power-of-two shapes with
+ * M >= 128, N >= 32, K >= 32).  d_scratch: scratch_bytes >=
+ * tnc_cgemm_scratch_bytes(), 256-byte aligned (may be NULL if that is 0). */
+int tnc_cgemm(const void* d_A, const void* d_B, void* d_C, int64_t batch, int64_t M, int64_t N, int64_t K,
+              int transA, int transB, int form, void* d_scratch, size_t scratch_bytes, void* cuda_stream);
 
 /* Device-side error flag of the kernels with bounded waits (the tcgen05
  * pipeline): 0 if no wait has timed out on the current device since load,

@@ -154,6 +154,23 @@ int tnc_load_network(const tnc_network_desc* desc, tnc_network_t** out) {
 
 void tnc_free_network(tnc_network_t* net) { delete net; }
 
+int tnc_ssa_separate(const double* pos, const double* rad, int n, int dim, uint64_t seed, int trials, int* side,
+                     int* valid, int* k) {
+  if (!pos || !rad || !side || !valid || !k || n < 2 || dim < 1 || dim > 3 || trials < 1) {
+    set_error("tnc_ssa_separate: invalid argument");
+    return TNC_EINVAL;
+  }
+  return ssa_separate_points(pos, rad, n, dim, seed, trials, side, valid, k);
+}
+
+int tnc_centerpoint(const double* pts, int n, int D, uint64_t seed, double* c) {
+  if (!pts || !c || n < 1 || D < 1 || D > 4) {
+    set_error("tnc_centerpoint: invalid argument");
+    return TNC_EINVAL;
+  }
+  return centerpoint_points(pts, n, D, seed, c);
+}
+
 void tnc_plan_opts_default(tnc_plan_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
@@ -329,7 +346,10 @@ int tnc_plan_export_json(const tnc_plan_t* plan, char* buf, size_t cap, size_t* 
       o << ",\"batch\":" << s.gemm.batch << ",\"M\":" << s.gemm.M << ",\"N\":" << s.gemm.N
         << ",\"K\":" << s.gemm.K << ",\"kernel\":" << s.gemm.kernel << ",\"tA\":" << s.gemm.transA
         << ",\"tB\":" << s.gemm.transB << ",\"a\":" << s.gemm.a << ",\"b\":" << s.gemm.b
-        << ",\"c\":" << s.gemm.c << ",\"a_buf\":" << s.gemm.a_buf << ",\"b_buf\":" << s.gemm.b_buf;
+        << ",\"c\":" << s.gemm.c << ",\"a_buf\":" << s.gemm.a_buf << ",\"b_buf\":" << s.gemm.b_buf
+        << ",\"c_ident\":" << s.gemm.c_ident << ",\"c_pos\":[";
+      for (int j = 0; j < s.gemm.nN + s.gemm.nM + s.gemm.nB; ++j) o << (j ? "," : "") << (int)s.gemm.c_pos[j];
+      o << "]";
     } else {
       o << ",\"rank\":" << s.perm.rank << ",\"src\":" << s.perm.src << ",\"dst\":" << s.perm.dst
         << ",\"src_bit\":[";
@@ -495,6 +515,79 @@ int run_request(tnc_plan_t* plan, const uint8_t* host_bits, int batch, void* d_o
 }  // namespace tnc
 
 extern "C" {
+
+static int device_of(const void* p, const char* who) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    set_error("%s: pointer is not device memory", who);
+    return TNC_EINVAL;
+  }
+  cudaError_t e = cudaSetDevice(attr.device);
+  if (e != cudaSuccess) return cuda_fail(e, who);
+  return TNC_OK;
+}
+
+int tnc_permute(const void* d_in, void* d_out, int rank, const int* src_bit, void* stream) {
+  if (!d_in || !d_out || rank < 0 || rank > 40 || (rank > 0 && !src_bit)) {
+    set_error("tnc_permute: invalid argument");
+    return TNC_EINVAL;
+  }
+  PermDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.rank = rank;
+  unsigned long long seen = 0;
+  for (int j = 0; j < rank; ++j) {
+    if (src_bit[j] < 0 || src_bit[j] >= rank || ((seen >> src_bit[j]) & 1)) {
+      set_error("tnc_permute: src_bit is not a permutation of 0..%d", rank - 1);
+      return TNC_EINVAL;
+    }
+    seen |= 1ull << src_bit[j];
+    d.src_bit[j] = (int8_t)src_bit[j];
+  }
+  int rc = device_of(d_out, "tnc_permute");
+  if (rc != TNC_OK) return rc;
+  int r = launch_permute_ptr(d, d_in, d_out, stream);
+  return r ? cuda_fail((cudaError_t)r, "tnc_permute") : TNC_OK;
+}
+
+static GemmDesc make_gemm(int64_t batch, int64_t M, int64_t N, int64_t K, int tA, int tB, int form) {
+  GemmDesc g;
+  std::memset(&g, 0, sizeof(g));
+  g.batch = batch, g.M = M, g.N = N, g.K = K, g.transA = tA, g.transB = tB, g.form = form;
+  g.c_ident = 1;  // C stored [b][M][N]
+  choose_gemm_kernel(g);
+  return g;
+}
+
+size_t tnc_cgemm_scratch_bytes(int64_t batch, int64_t M, int64_t N, int64_t K, int form) {
+  if (batch < 1 || M < 1 || N < 1 || K < 1 || form < 0 || form > 2) return 0;
+  return (size_t)gemm_scratch_bytes(make_gemm(batch, M, N, K, 0, 0, form));
+}
+
+int tnc_cgemm(const void* A, const void* B, void* Cp, int64_t batch, int64_t M, int64_t N, int64_t K, int tA,
+              int tB, int form, void* scratch, size_t scratch_bytes, void* stream) {
+  if (!A || !B || !Cp || batch < 1 || M < 1 || N < 1 || K < 1 || form < 0 || form > 2 || (tA & ~1) ||
+      (tB & ~1)) {
+    set_error("tnc_cgemm: invalid argument");
+    return TNC_EINVAL;
+  }
+  GemmDesc g = make_gemm(batch, M, N, K, tA, tB, form);
+  const uint64_t need = gemm_scratch_bytes(g);
+  if (need > scratch_bytes || (need && !scratch)) {
+    set_error("tnc_cgemm: scratch of %zu bytes < required %llu", scratch_bytes, (unsigned long long)need);
+    return TNC_ENOMEM;
+  }
+  if (need && ((uintptr_t)scratch & 255)) {
+    set_error("tnc_cgemm: scratch not 256-byte aligned");
+    return TNC_EINVAL;
+  }
+  g.scratch_elems = need / 8;
+  int rc = device_of(Cp, "tnc_cgemm");
+  if (rc != TNC_OK) return rc;
+  int r = launch_gemm_ptr(g, A, B, Cp, scratch, stream);
+  return r ? cuda_fail((cudaError_t)r, "tnc_cgemm") : TNC_OK;
+}
 
 int tnc_device_error(int* flag) {
   if (!flag) {

@@ -87,6 +87,46 @@ int bitpos(const std::vector<int>& L, int x) {
 
 }  // namespace
 
+// Kernel variant by shape: tiny outputs with long K -> split-K dot; narrow
+// N and K -> one row per thread; dense enough nodes of the tensor-core forms
+// -> tcgen05; otherwise the register-tiled CUDA-core kernel.  Long FP32 sums
+// over K are cut into chunks summed in FP64 (split-K) when the output is small
+// enough for the partials.
+void choose_gemm_kernel(GemmDesc& g) {
+  const double MN = (double)g.M * g.N;
+  const bool pow2 = !(g.M & (g.M - 1)) && !(g.N & (g.N - 1)) && !(g.K & (g.K - 1));
+  if (MN <= 16 && g.K >= 512)
+    g.kernel = KG_DOT;
+  else if (g.N <= 16 && g.K <= 16)
+    g.kernel = KG_NARROW;
+  else if (g.form != TNC_FP32 && pow2 && g.M >= 128 && g.N >= 32 && g.K >= 32)
+    g.kernel = KG_TC;
+  else if (g.N <= 32)
+    g.kernel = KG_SIMT_64x32;
+  else
+    g.kernel = KG_SIMT_128x64;
+  g.splitk = 1;
+  const bool simt = g.kernel == KG_SIMT_128x64 || g.kernel == KG_SIMT_64x32 || g.kernel == KG_SIMT_32x128 ||
+                    (g.kernel == KG_DOT && (g.M > 4 || g.N > 4));
+  if (simt && g.K >= 8192 && (double)g.batch * g.M * g.N <= (double)(1 << 20)) {
+    int64_t s = g.K / 2048;
+    while (s > 1 && (double)s * g.batch * g.M * g.N * 8 > (double)(256u << 20)) s >>= 1;
+    g.splitk = (int)std::min<int64_t>(s, 4096);
+  }
+}
+
+uint64_t gemm_scratch_bytes(const GemmDesc& g) {
+  uint64_t bytes = 0;
+  if (g.kernel == KG_DOT) bytes = (uint64_t)g.batch * g.M * g.N * 16 * 1024;
+  if (g.kernel == KG_TC) {
+    // hi/lo planes of A' (batch x M x 2K) and B'^T (batch x 2N x 2K), 2 or 4 bytes each
+    const uint64_t es = g.form == TNC_SPLIT_BF16 ? 2 : 4;
+    bytes = (uint64_t)g.batch * (g.M * 2 * g.K * 2 + 2 * g.N * 2 * g.K * 2) * es + 4096;
+  }
+  if (g.splitk > 1) bytes = std::max<uint64_t>(bytes, (uint64_t)g.splitk * g.batch * g.M * g.N * 8);
+  return bytes;
+}
+
 // ----------------------------------------------------------------- slicing
 namespace {
 
@@ -297,26 +337,57 @@ int compile_program(Plan& p) {
   };
   post(t.root);
 
+  // ---- layouts, top down: every tensor is stored in the order its consumer
+  // reads.  A node reads both operands K-major, [batch][free][K]; its GEMM
+  // writes its output through the epilogue's scatter directly into the order
+  // its own consumer asked for, so no tensor is ever permuted.
+  std::vector<std::vector<int>> want(t.nodes.size());
+  {
+    std::vector<int> ro = t.nodes[t.root].out;
+    std::sort(ro.begin(), ro.end());
+    want[t.root] = ro;
+    std::function<void(int)> down = [&](int v) {
+      const TreeNode& nd = t.nodes[v];
+      if (nd.left < 0) return;
+      const int x = nd.left, y = nd.right;
+      std::set<int> Lx(t.nodes[x].out.begin(), t.nodes[x].out.end());
+      std::set<int> Ly(t.nodes[y].out.begin(), t.nodes[y].out.end());
+      std::set<int> Lv(nd.out.begin(), nd.out.end());
+      std::vector<int> b, fx, fy, K;
+      for (int a : want[v]) {
+        if (Lx.count(a) && Ly.count(a))
+          b.push_back(a);
+        else if (Lx.count(a))
+          fx.push_back(a);
+        else
+          fy.push_back(a);
+      }
+      for (int a : Lx)
+        if (Ly.count(a) && !Lv.count(a)) K.push_back(a);
+      want[x] = concat({&b, &fx, &K});
+      want[y] = concat({&b, &fy, &K});
+      down(x);
+      down(y);
+    };
+    down(t.root);
+  }
+
   // per-node storage
-  std::vector<std::vector<int>> layout(t.nodes.size());
-  std::vector<int> buf(t.nodes.size(), -1);        // 0 workspace, 1 leaf buffer
+  std::vector<int> buf(t.nodes.size(), -1);        // 0 leaf area, 1 leaf buffer, 2 arena
   std::vector<uint64_t> loc(t.nodes.size(), 0);    // element offset
   std::vector<char> placed(t.nodes.size(), 0);
   Arena arena;
-  std::vector<std::pair<int, std::vector<int>>> leaf_layout;  // (node, order) chosen by consumers
-  std::vector<int> leaf_nodes_derived;
   std::vector<Step> steps;
-  // arena offsets are relative; fixed up once the leaf area size is known
-  std::vector<std::pair<size_t, int>> fix_a, fix_b, fix_c;  // (step, which field)
+  std::vector<std::pair<size_t, int>> fix_b;  // (step, operand buffer tags)
 
   auto nsize = [&](int v) { return (uint64_t)1 << t.nodes[v].out.size(); };
 
-  // place a leaf node in a chosen order
+  // place a leaf in the order its consumer reads
   uint64_t leaf_ws_off = 0;   // elements, relative to leaf_area
   std::vector<cd> base_data;  // assembled leaf buffer (FP64, converted at the end)
-  auto place_leaf = [&](int v, const std::vector<int>& ord) {
+  auto place_leaf = [&](int v) {
+    const std::vector<int>& ord = want[v];
     int l = t.nodes[v].leaf;
-    layout[v] = ord;
     placed[v] = 1;
     const Leaf& L = net.leaves[l];
     if (derived[l]) {
@@ -325,6 +396,7 @@ int compile_program(Plan& p) {
       // base data stored in the original order
       g.src = base_data.size();
       base_data.insert(base_data.end(), L.data.begin(), L.data.end());
+      while (base_data.size() % 4) base_data.push_back(0);
       g.dst = leaf_ws_off;  // relative, fixed below
       g.out_rank = (int)ord.size();
       g.src_rank = (int)L.labels.size();
@@ -356,10 +428,8 @@ int compile_program(Plan& p) {
       pr.max_gather_rank = std::max(pr.max_gather_rank, g.out_rank);
       buf[v] = 0;
       loc[v] = leaf_ws_off;  // relative to the leaf area
-      leaf_nodes_derived.push_back(v);
       leaf_ws_off += align_up(((uint64_t)1 << ord.size()) * 8) / 8;
     } else {
-      // store permuted into the consumer's order
       const int r = (int)ord.size();
       std::vector<int> srcbit(r);
       for (int j = 0; j < r; ++j) srcbit[j] = bitpos(L.labels, ord[r - 1 - j]);
@@ -371,166 +441,37 @@ int compile_program(Plan& p) {
           if ((o >> j) & 1) i |= (uint64_t)1 << srcbit[j];
         base_data[start + o] = L.data[i];
       }
-      // keep 32-byte alignment of every leaf
-      while (base_data.size() % 4) base_data.push_back(0);
+      while (base_data.size() % 4) base_data.push_back(0);  // keep 32-byte alignment
       buf[v] = 1;
       loc[v] = start;
     }
   };
 
-  // record arena offsets as relative-to-arena with a tag (buffer 2)
   constexpr int BUF_ARENA = 2;
-  std::vector<int> last_use(t.nodes.size(), -1);
-
   double flops = 0, bytes = 0, pops = 0;
   for (int v : order) {
     const TreeNode& nd = t.nodes[v];
-    int x = nd.left, y = nd.right;
+    const int x = nd.left, y = nd.right;
+    for (int c : {x, y})
+      if (!placed[c]) place_leaf(c);
     std::set<int> Lx(t.nodes[x].out.begin(), t.nodes[x].out.end());
     std::set<int> Ly(t.nodes[y].out.begin(), t.nodes[y].out.end());
-    std::set<int> Lv(nd.out.begin(), nd.out.end());
-    std::set<int> bset, kset, fx, fy;
+    int nb = 0, nk = 0, nfx = 0, nfy = 0;
     for (int a : Lx) {
-      if (Ly.count(a)) {
-        if (Lv.count(a))
-          bset.insert(a);
-        else
-          kset.insert(a);
-      } else {
-        if (!Lv.count(a)) {
-          set_error("tnc_plan: internal error: label %d summed inside one operand", a);
-          return TNC_EINVAL;
-        }
-        fx.insert(a);
-      }
+      if (Ly.count(a))
+        (std::find(nd.out.begin(), nd.out.end(), a) != nd.out.end() ? nb : nk)++;
+      else
+        ++nfx;
     }
     for (int a : Ly)
-      if (!Lx.count(a)) fy.insert(a);
-    struct Opt {
-      int A, B, tA, tB;
-      double cost;
-      bool permA, permB;
-      std::vector<int> ordA, ordB;  // final operand layouts
-      std::vector<int> b, K, M, N;
-      int kernel_pref;
-    };
-    Opt best;
-    best.cost = 1e300;
-    for (int orient = 0; orient < 2; ++orient) {
-      int A = orient ? y : x, B = orient ? x : y;
-      const std::set<int>& fa = orient ? fy : fx;
-      const std::set<int>& fb = orient ? fx : fy;
-      for (int tA = 0; tA < 2; ++tA)
-        for (int tB = 0; tB < 2; ++tB) {
-          Opt o;
-          o.A = A, o.B = B, o.tA = tA, o.tB = tB;
-          o.permA = o.permB = false;
-          std::vector<std::vector<int>> oa, ob;
-          bool fixA = placed[A], fixB = placed[B];
-          bool okA = !fixA || view_as(layout[A], tA ? std::vector<std::set<int>>{bset, kset, fa}
-                                                  : std::vector<std::set<int>>{bset, fa, kset}, oa);
-          bool okB = !fixB || view_as(layout[B], tB ? std::vector<std::set<int>>{bset, fb, kset}
-                                                  : std::vector<std::set<int>>{bset, kset, fb}, ob);
-          std::vector<int> bA, kA, mA, bB, kB, nB;
-          if (fixA && okA) {
-            bA = oa[0];
-            kA = tA ? oa[1] : oa[2];
-            mA = tA ? oa[2] : oa[1];
-          }
-          if (fixB && okB) {
-            bB = ob[0];
-            kB = tB ? ob[2] : ob[1];
-            nB = tB ? ob[1] : ob[2];
-          }
-          double sA = (double)nsize(A), sB = (double)nsize(B);
-          double cost = 0;
-          if (fixA && !okA) o.permA = true, cost += sA;
-          if (fixB && !okB) o.permB = true, cost += sB;
-          // batch and K orders must agree between two fixed, fitting operands
-          if (fixA && okA && fixB && okB && (bA != bB || kA != kB)) {
-            if (sA <= sB)
-              o.permA = true, cost += sA;
-            else
-              o.permB = true, cost += sB;
-          }
-          // resolve the orders
-          auto good = [&](int side) { return side == 0 ? (fixA && !o.permA) : (fixB && !o.permB); };
-          if (good(0)) {
-            o.b = bA, o.K = kA, o.M = mA;
-          } else if (good(1)) {
-            o.b = bB, o.K = kB;
-          } else {
-            o.b = sorted_vec(bset), o.K = sorted_vec(kset);
-          }
-          if (!good(0)) {
-            // keep the relative order of A's free labels if it had a layout
-            if (fixA) {
-              for (int a : layout[A])
-                if (fa.count(a)) o.M.push_back(a);
-            } else {
-              o.M = sorted_vec(fa);
-            }
-          }
-          if (good(1)) {
-            o.N = nB;
-          } else if (fixB) {
-            for (int a : layout[B])
-              if (fb.count(a)) o.N.push_back(a);
-          } else {
-            o.N = sorted_vec(fb);
-          }
-          o.ordA = tA ? concat({&o.b, &o.K, &o.M}) : concat({&o.b, &o.M, &o.K});
-          o.ordB = tB ? concat({&o.b, &o.N, &o.K}) : concat({&o.b, &o.K, &o.N});
-          // prefer the big free side as A (M >= N), then non-transposed forms
-          double M = std::exp2((double)fa.size()), N = std::exp2((double)fb.size());
-          double tie = (M >= N ? 0 : 0.5) + 0.01 * (tA + tB);
-          o.cost = cost + tie;
-          if (o.cost < best.cost) best = o;
-        }
-    }
-    // emit permutes / place leaves
-    auto prepare = [&](int side) -> void {
-      int c = side == 0 ? best.A : best.B;
-      const std::vector<int>& ord = side == 0 ? best.ordA : best.ordB;
-      bool perm = side == 0 ? best.permA : best.permB;
-      if (!placed[c]) {
-        place_leaf(c, ord);
-        return;
-      }
-      if (!perm) return;
-      Step s;
-      std::memset(&s, 0, sizeof(s));
-      s.kind = ST_PERMUTE;
-      s.node = v;
-      const int r = (int)ord.size();
-      s.perm.rank = r;
-      for (int j = 0; j < r; ++j) s.perm.src_bit[j] = (int8_t)bitpos(layout[c], ord[r - 1 - j]);
-      uint64_t dst = arena.alloc(nsize(c) * 8);
-      s.perm.src = loc[c];
-      s.perm.dst = dst / 8;
-      if (buf[c] != 0 && buf[c] != BUF_ARENA) {
-        set_error("tnc_plan: internal error: permute of a leaf");
-        return;
-      }
-      // src may be in the leaf area (buf 0, relative to leaf area) or arena
-      steps.push_back(s);
-      fix_a.push_back({steps.size() - 1, buf[c] == BUF_ARENA ? 10 : 11});  // perm src tag
-      // the permuted copy replaces the operand; the old copy is freed after the gemm
-      if (buf[c] == BUF_ARENA) last_use[c] = v;
-      layout[c] = ord;
-      buf[c] = BUF_ARENA;
-      loc[c] = dst / 8;
-      // remember the temp to free after the gemm (the original arena block)
-    };
-    // track arena blocks of the operands before permutes to free them later
-    std::vector<uint64_t> to_free;
-    for (int c : {best.A, best.B})
-      if (placed[c] && buf[c] == BUF_ARENA) to_free.push_back(loc[c] * 8);
-    prepare(0);
-    prepare(1);
-    for (int c : {best.A, best.B})
-      if (buf[c] == BUF_ARENA) to_free.push_back(loc[c] * 8);
-    // output
+      if (!Lx.count(a)) ++nfy;
+    // orientation by shape: the larger free side is M
+    const int A = nfx >= nfy ? x : y, B = nfx >= nfy ? y : x;
+    const int nM = nfx >= nfy ? nfx : nfy, nN = nfx >= nfy ? nfy : nfx;
+    // operand layouts are [b][free][K]: A as [b][M][K], B as [b][N][K]
+    const std::vector<int>& LA = want[A];
+    const std::vector<int>& LB = want[B];
+    const std::vector<int>& LC = want[v];
     uint64_t cbytes = nsize(v) * 8;
     uint64_t coff = arena.alloc(cbytes);
     Step s;
@@ -538,60 +479,40 @@ int compile_program(Plan& p) {
     s.kind = ST_GEMM;
     s.node = v;
     GemmDesc& g = s.gemm;
-    g.batch = (int64_t)1 << best.b.size();
-    g.M = (int64_t)1 << best.M.size();
-    g.N = (int64_t)1 << best.N.size();
-    g.K = (int64_t)1 << best.K.size();
-    g.transA = best.tA;
-    g.transB = best.tB;
-    g.a = loc[best.A];
-    g.b = loc[best.B];
-    g.a_buf = buf[best.A];
-    g.b_buf = buf[best.B];
+    g.batch = (int64_t)1 << nb;
+    g.M = (int64_t)1 << nM;
+    g.N = (int64_t)1 << nN;
+    g.K = (int64_t)1 << nk;
+    g.transA = 0;
+    g.transB = 1;
+    g.a = loc[A];
+    g.b = loc[B];
+    g.a_buf = buf[A];
+    g.b_buf = buf[B];
     g.c = coff / 8;
     g.form = form;
-    // kernel choice by shape (refined by the autotuner at upload)
-    const double MN = (double)g.M * g.N;
-    if (MN <= 16 && g.K >= 512)
-      g.kernel = KG_DOT;
-    else if (g.N <= 16 && g.K <= 16)
-      g.kernel = KG_NARROW;
-    else if (form != TNC_FP32 && g.M >= 128 && g.N >= 32 && g.K >= 32)
-      g.kernel = KG_TC;
-    else if (g.N <= 32)
-      g.kernel = KG_SIMT_64x32;
-    else
-      g.kernel = KG_SIMT_128x64;
-    // long FP32 sums over K are cut into chunks summed in FP64 (split-K)
-    g.splitk = 1;
-    const bool simt = g.kernel == KG_SIMT_128x64 || g.kernel == KG_SIMT_64x32 || g.kernel == KG_SIMT_32x128 ||
-                      (g.kernel == KG_DOT && (g.M > 4 || g.N > 4));
-    if (simt && g.K >= 8192 && (double)g.batch * g.M * g.N <= (double)(1 << 20)) {
-      int64_t s = g.K / 2048;
-      while (s > 1 && (double)s * g.batch * g.M * g.N * 8 > (double)(256u << 20)) s >>= 1;
-      g.splitk = (int)std::min<int64_t>(s, 4096);
+    // output scatter: n bits (B's free labels, least significant first), then
+    // m bits (A's free labels), then batch bits, to their places in LC
+    g.nN = nN, g.nM = nM, g.nB = nb;
+    {
+      int i = 0;
+      for (int j = nN - 1; j >= 0; --j) g.c_pos[i++] = (int8_t)bitpos(LC, LB[nb + j]);
+      for (int j = nM - 1; j >= 0; --j) g.c_pos[i++] = (int8_t)bitpos(LC, LA[nb + j]);
+      for (int j = nb - 1; j >= 0; --j) g.c_pos[i++] = (int8_t)bitpos(LC, LA[j]);
+      bool ident = true;
+      for (int k = 0; k < i; ++k) ident &= g.c_pos[k] == k;
+      g.c_ident = ident ? 1 : 0;
     }
-    // per-node scratch
-    uint64_t scratch_bytes = 0;
-    if (g.kernel == KG_DOT) scratch_bytes = (uint64_t)g.batch * g.M * g.N * 16 * 1024;
-    if (g.splitk > 1) scratch_bytes = std::max<uint64_t>(scratch_bytes, (uint64_t)g.splitk * g.batch * g.M * g.N * 8);
-    if (g.kernel == KG_TC) {
-      // hi/lo planes: A (batch*M*2K) x 2 and expanded B' (batch*2N*2K) x 2, 2 or 4 bytes each
-      uint64_t es = form == TNC_SPLIT_BF16 ? 2 : 4;
-      scratch_bytes = (uint64_t)g.batch * (g.M * 2 * g.K * 2 + 2 * g.N * 2 * g.K * 2) * es + 4096;
-    }
+    choose_gemm_kernel(g);
+    const uint64_t scratch_bytes = gemm_scratch_bytes(g);
     uint64_t soff = scratch_bytes ? arena.alloc(scratch_bytes) : 0;
     g.scratch = soff / 8;
     g.scratch_elems = scratch_bytes / 8;
     steps.push_back(s);
-    {
-      int tagA = g.a_buf == BUF_ARENA ? 20 : (g.a_buf == 0 ? 21 : 22);
-      int tagB = g.b_buf == BUF_ARENA ? 30 : (g.b_buf == 0 ? 31 : 32);
-      fix_b.push_back({steps.size() - 1, tagA * 100 + tagB});
-    }
+    fix_b.push_back({steps.size() - 1, 0});
     if (scratch_bytes) arena.release(soff);
-    for (uint64_t f : to_free) arena.release(f);
-    layout[v] = concat({&best.b, &best.M, &best.N});
+    for (int c : {A, B})
+      if (buf[c] == BUF_ARENA) arena.release(loc[c] * 8);
     buf[v] = BUF_ARENA;
     loc[v] = coff / 8;
     placed[v] = 1;
@@ -600,11 +521,8 @@ int compile_program(Plan& p) {
     pops += 2 * work;
     bytes += 8.0 * ((double)g.batch * (g.M * g.K + g.K * g.N + g.M * g.N));
   }
-  if (!placed[t.root]) {
-    // single-leaf network
-    std::vector<int> ord = t.nodes[t.root].out;
-    place_leaf(t.root, ord);
-  }
+  if (!placed[t.root]) place_leaf(t.root);  // single-leaf network
+  const std::vector<std::vector<int>>& layout = want;
 
   // fix up offsets: leaf area size known now
   const uint64_t leaf_bytes = align_up(leaf_ws_off * 8);
@@ -615,20 +533,12 @@ int compile_program(Plan& p) {
     if (b == 0) return leaf_area / 8 + rel;
     return rel;
   };
-  for (auto& f : fix_a) {
-    Step& s = steps[f.first];
-    s.perm.src = abs_off(f.second == 10 ? BUF_ARENA : 0, s.perm.src);
-    s.perm.dst = abs_off(BUF_ARENA, s.perm.dst);
-  }
   for (auto& f : fix_b) {
     Step& s = steps[f.first];
-    int tagA = f.second / 100, tagB = f.second % 100;
-    int ba = tagA == 20 ? BUF_ARENA : (tagA == 21 ? 0 : 1);
-    int bb = tagB == 30 ? BUF_ARENA : (tagB == 31 ? 0 : 1);
-    s.gemm.a = abs_off(ba, s.gemm.a);
-    s.gemm.b = abs_off(bb, s.gemm.b);
-    s.gemm.a_buf = ba == 1 ? 1 : 0;
-    s.gemm.b_buf = bb == 1 ? 1 : 0;
+    s.gemm.a = abs_off(s.gemm.a_buf, s.gemm.a);
+    s.gemm.b = abs_off(s.gemm.b_buf, s.gemm.b);
+    s.gemm.a_buf = s.gemm.a_buf == 1 ? 1 : 0;
+    s.gemm.b_buf = s.gemm.b_buf == 1 ? 1 : 0;
     s.gemm.c = abs_off(BUF_ARENA, s.gemm.c);
     if (s.gemm.scratch_elems) s.gemm.scratch = abs_off(BUF_ARENA, s.gemm.scratch);
   }

@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <cstdio>
 
+#include "outmap.cuh"
 #include "tnc_kernels.h"
 
 namespace tnc {
@@ -102,7 +103,7 @@ template <int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     cgemm_simt_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
                       int64_t M, int64_t N, int64_t K, int transA, int transB, int64_t b0, int64_t kchunk,
-                      int64_t part_stride) {
+                      int64_t part_stride, const __grid_constant__ OutMap om) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
   __shared__ __align__(16) float2 As[BK][BM];
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   const int64_t bz = b0 + blockIdx.z;
   A += bz * M * K;
   B += bz * K * N;
-  C += bz * M * N + (int64_t)blockIdx.y * part_stride;
+  C += (int64_t)blockIdx.y * part_stride;
   const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
   const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
   const int64_t mt = (M + BM - 1) / BM;
@@ -164,14 +165,21 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     }
     __syncthreads();
   }
+  uint64_t coff[TN];
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    int64_t n = n0 + tx * TN + j;
+    coff[j] = n < N ? om.col(n) : 0;
+  }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     int64_t m = m0 + ty * TM + i;
     if (m >= M) continue;
+    const uint64_t roff = om.row(bz, m, M, N);
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       int64_t n = n0 + tx * TN + j;
-      if (n < N) C[m * N + n] = acc[i][j];
+      if (n < N) C[roff + coff[j]] = acc[i][j];
     }
   }
 }
@@ -180,12 +188,14 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 // one output row per thread; N, K <= 16; B of the batch in shared memory
 __global__ void __launch_bounds__(256)
     cgemm_narrow_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
-                        int64_t M, int N, int K, int transA, int transB, int64_t b0) {
+                        int64_t M, int N, int K, int transA, int transB, int64_t b0,
+                        const __grid_constant__ OutMap om) {
   __shared__ float2 Bs[16 * 16];
+  __shared__ uint64_t coff[16];
   const int64_t bz = b0 + blockIdx.y;
   A += bz * M * K;
   B += bz * (int64_t)K * N;
-  C += bz * M * N;
+  if (threadIdx.x < N) coff[threadIdx.x] = om.col(threadIdx.x);
   for (int e = threadIdx.x; e < K * N; e += blockDim.x) {
     int k = e / N, n = e % N;
     Bs[e] = transB ? B[(int64_t)n * K + k] : B[(int64_t)k * N + n];
@@ -196,12 +206,13 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int k = 0; k < 16; ++k)
       if (k < K) a[k] = transA ? A[(int64_t)k * M + m] : A[m * K + k];
+    const uint64_t roff = om.row(bz, m, M, N);
     for (int n = 0; n < N; ++n) {
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < 16; ++k)
         if (k < K) acc = cmul_add(acc, a[k], Bs[k * N + n]);
-      C[m * N + n] = acc;
+      C[roff + coff[n]] = acc;
     }
   }
 }
@@ -264,8 +275,9 @@ __global__ void __launch_bounds__(kDotThreads)
   }
 }
 
-__global__ void dot_finish_kernel(const double2* __restrict__ part, float2* __restrict__ C, int nblk, int MN,
-                                  int64_t batch) {
+__global__ void dot_finish_kernel(const double2* __restrict__ part, float2* __restrict__ C, int nblk, int M, int N,
+                                  int64_t batch, const __grid_constant__ OutMap om) {
+  const int MN = M * N;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= batch * MN) return;
   int64_t bz = i / MN, e = i % MN;
@@ -274,7 +286,7 @@ __global__ void dot_finish_kernel(const double2* __restrict__ part, float2* __re
     double2 v = part[(bz * nblk + b) * MN + e];
     x += v.x, y += v.y;
   }
-  C[bz * MN + e] = make_float2((float)x, (float)y);
+  C[om.row(bz, e / N, M, N) + om.col(e % N)] = make_float2((float)x, (float)y);
 }
 
 // ------------------------------------------------------------------ accum
@@ -307,14 +319,16 @@ __global__ void accum_kernel(const float2* __restrict__ root, double2* __restric
 }
 
 __global__ void splitk_reduce_kernel(const float2* __restrict__ part, float2* __restrict__ C, int splits,
-                                     int64_t n) {
+                                     int64_t n, int64_t M, int64_t N,
+                                     const __grid_constant__ OutMap om) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double x = 0, y = 0;
     for (int s = 0; s < splits; ++s) {
       float2 v = part[(int64_t)s * n + i];
       x += v.x, y += v.y;
     }
-    C[i] = make_float2((float)x, (float)y);
+    const int64_t nn = i % N, bm = i / N;
+    C[om.row(bm / M, bm % M, M, N) + om.col(nn)] = make_float2((float)x, (float)y);
   }
 }
 
@@ -328,18 +342,21 @@ int run_simt(const GemmDesc& d, const float2* A, const float2* B, float2* C, flo
   float2* dst = C;
   if (splits > 1) {
     if ((uint64_t)splits * nout > d.scratch_elems) return (int)cudaErrorInvalidValue;
-    dst = ws + d.scratch;
+    dst = ws;
   }
   const int64_t kchunk = (d.K + splits - 1) / splits;
+  const OutMap om = out_map(d);
+  OutMap ident = om;
+  ident.ident = 1;
   for (int64_t b0 = 0; b0 < d.batch; b0 += 65535) {
     int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
     dim3 grid((unsigned)(mt * nt), (unsigned)splits, (unsigned)nb);
     cgemm_simt_kernel<BM, BN, BK, TM, TN><<<grid, NT, 0, st>>>(A, B, dst, d.M, d.N, d.K, d.transA, d.transB, b0,
-                                                                kchunk, nout);
+                                                                kchunk, nout, splits > 1 ? ident : om);
   }
   if (splits > 1) {
     unsigned blocks = (unsigned)((nout + 255) / 256 < 152 * 16 ? (nout + 255) / 256 : 152 * 16);
-    splitk_reduce_kernel<<<blocks, 256, 0, st>>>(dst, C, splits, nout);
+    splitk_reduce_kernel<<<blocks, 256, 0, st>>>(dst, C, splits, nout, d.M, d.N, om);
   }
   return (int)cudaGetLastError();
 }
@@ -370,11 +387,15 @@ int launch_gather(const GatherDesc* d_descs, int n_descs, int max_out_rank, cons
 }
 
 int launch_permute(const PermDesc& d, void* ws, void* stream) {
+  return launch_permute_ptr(d, (const float2*)ws + d.src, (float2*)ws + d.dst, stream);
+}
+
+int launch_permute_ptr(const PermDesc& d, const void* in, void* out, void* stream) {
   const int r = d.rank;
   PermArgs p;
   memset(&p, 0, sizeof(p));
-  p.src = d.src;
-  p.dst = d.dst;
+  p.src = 0;
+  p.dst = 0;
   int dst_of[kMaxRank];
   for (int j = 0; j < r; ++j) dst_of[(int)d.src_bit[j]] = j;
   int a = r < 5 ? r : 5, b = r < 5 ? r : 5;
@@ -417,17 +438,25 @@ int launch_permute(const PermDesc& d, void* ws, void* stream) {
   unsigned gy = (unsigned)(nblocks / gx);
   dim3 grid(gx, gy);
   size_t smem = ((size_t)1 << nU) * sizeof(float2);
-  permute_kernel<<<grid, kPermThreads, smem, (cudaStream_t)stream>>>((const float2*)ws, (float2*)ws, p);
+  permute_kernel<<<grid, kPermThreads, smem, (cudaStream_t)stream>>>((const float2*)in, (float2*)out, p);
   return (int)cudaGetLastError();
 }
 
-int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* C, void* ws, cudaStream_t st);
+int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* C, void* scratch, cudaStream_t st);
 
 int launch_gemm(const GemmDesc& d, const void* base, void* ws, void* stream) {
-  cudaStream_t st = (cudaStream_t)stream;
   const float2* A = (const float2*)(d.a_buf ? base : ws) + d.a;
   const float2* B = (const float2*)(d.b_buf ? base : ws) + d.b;
   float2* C = (float2*)ws + d.c;
+  return launch_gemm_ptr(d, A, B, C, d.scratch_elems ? (float2*)ws + d.scratch : nullptr, stream);
+}
+
+int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp, void* scratch, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const float2* A = (const float2*)Ap;
+  const float2* B = (const float2*)Bp;
+  float2* C = (float2*)Cp;
+  float2* ws = (float2*)scratch;  // per-node scratch (d.scratch_elems complex64 slots)
   switch (d.kernel) {
     case KG_SIMT_128x64:
       return run_simt<128, 64, 8, 8, 4>(d, A, B, C, (float2*)ws, st);
@@ -442,13 +471,14 @@ int launch_gemm(const GemmDesc& d, const void* base, void* ws, void* stream) {
       for (int64_t b0 = 0; b0 < d.batch; b0 += 65535) {
         int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
         dim3 grid((unsigned)blocks, (unsigned)nb);
-        cgemm_narrow_kernel<<<grid, 256, 0, st>>>(A, B, C, d.M, (int)d.N, (int)d.K, d.transA, d.transB, b0);
+        cgemm_narrow_kernel<<<grid, 256, 0, st>>>(A, B, C, d.M, (int)d.N, (int)d.K, d.transA, d.transB, b0,
+                                                   out_map(d));
       }
       return (int)cudaGetLastError();
     }
     case KG_DOT: {
       if (d.M * d.N > 16 || d.M > 4 || d.N > 4) return run_simt<64, 32, 8, 4, 4>(d, A, B, C, (float2*)ws, st);
-      double2* part = (double2*)((float2*)ws + d.scratch);
+      double2* part = (double2*)ws;
       const int MN = (int)(d.M * d.N);
       int64_t nblk = (d.K + kDotThreads * 32 - 1) / (kDotThreads * 32);
       if (nblk > 1024) nblk = 1024;
@@ -461,11 +491,12 @@ int launch_gemm(const GemmDesc& d, const void* base, void* ws, void* stream) {
                                                         b0);
       }
       int64_t tot = d.batch * MN;
-      dot_finish_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, C, (int)nblk, MN, d.batch);
+      dot_finish_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, C, (int)nblk, (int)d.M, (int)d.N,
+                                                                          d.batch, out_map(d));
       return (int)cudaGetLastError();
     }
     case KG_TC:
-      return launch_tc_gemm(d, A, B, C, ws, st);
+      return launch_tc_gemm(d, A, B, C, scratch, st);
     default:
       return (int)cudaErrorInvalidValue;
   }

@@ -180,6 +180,15 @@ class Builder {
   }
 
   Tree tree;
+  // classification (0 inside, 1 outside, 2 intersected) of the separator
+  // kept by the last call of separate(), whether it met Eqs. (1)-(2), and k
+  std::vector<int> last_cls;
+  bool last_valid = false;
+  int last_k = 0;
+
+  void separate_public(const std::vector<int>& set, std::vector<int>& s0, std::vector<int>& s1) {
+    separate(set, s0, s1);
+  }
 
  private:
   const PlanNet& pn_;
@@ -377,7 +386,7 @@ class Builder {
     // step 4: dilation parameter
     const double alpha = std::sqrt((1 - nc) / (1 + nc));
 
-    std::vector<int> cls(n), best_cls;
+    std::vector<int> cls(n), best_cls, best_raw, eq2_raw;
     int best_cut = 1 << 30, best_imb = 1 << 30;
     bool best_valid = false;
     std::vector<int> eq2_cls;
@@ -440,20 +449,27 @@ class Builder {
           best_cut = cut;
           best_imb = imb;
           best_cls = sides;
+          best_raw = cls;
         }
       } else if (ok2 && cut < eq2_cut) {
         eq2_cut = cut;
         eq2_cls = sides;
+        eq2_raw = cls;
       }
     }
     std::vector<int> sides;
+    last_k = kmax;
+    last_valid = best_valid;
+    last_cls.clear();
     if (best_valid) {
       if (st_) st_->ssa_valid++;
       sides = best_cls;
+      last_cls = best_raw;
     } else {
       if (st_) st_->ssa_fallback++;
       if (!eq2_cls.empty()) {
         sides = eq2_cls;
+        last_cls = eq2_raw;
       } else {
         // median split along the axis of largest spread
         int ax = 0;
@@ -478,6 +494,45 @@ class Builder {
 };
 
 }  // namespace
+
+// Algorithm 1 on a bare set of spheres (no bonds): the classification of the
+// separator kept, whether it satisfies Eqs. (1)-(2), and the overlap number k.
+int ssa_separate_points(const double* pos, const double* rad, int n, int dim, uint64_t seed, int trials,
+                        int* cls_out, int* valid, int* k_out) {
+  PlanNet pn;
+  pn.dim = dim;
+  pn.n_leaves = n;
+  pn.leaf_labels.assign(n, {});
+  pn.pos.resize(n);
+  pn.radius.resize(n);
+  for (int i = 0; i < n; ++i) {
+    for (int k = 0; k < 3; ++k) pn.pos[i][k] = k < dim ? pos[(size_t)i * dim + k] : 0.0;
+    pn.radius[i] = rad[i];
+  }
+  PlannerOpts o;
+  o.seed = seed;
+  o.trials = trials;
+  Builder b(pn, o, nullptr);
+  std::vector<int> all(n), s0, s1;
+  std::iota(all.begin(), all.end(), 0);
+  b.separate_public(all, s0, s1);
+  for (int i = 0; i < n; ++i) cls_out[i] = b.last_cls.empty() ? -1 : b.last_cls[i];
+  *valid = b.last_valid ? 1 : 0;
+  *k_out = b.last_k;
+  return 0;
+}
+
+int centerpoint_points(const double* pts, int n, int D, uint64_t seed, double* c) {
+  std::vector<P4> v(n);
+  for (int i = 0; i < n; ++i) {
+    v[i] = P4{};
+    for (int k = 0; k < D; ++k) v[i][k] = pts[(size_t)i * D + k];
+  }
+  Rng rng(seed);
+  P4 r = centerpoint(v, D, rng);
+  for (int k = 0; k < D; ++k) c[k] = r[k];
+  return 0;
+}
 
 Tree plan_tree(const PlanNet& pn, const PlannerOpts& o, PlannerStats* st) {
   Builder b(pn, o, st);

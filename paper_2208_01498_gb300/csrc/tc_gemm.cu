@@ -28,6 +28,7 @@
 #include <cstring>
 
 #include "../../include/tnc.h"
+#include "outmap.cuh"
 #include "tnc_kernels.h"
 
 namespace tnc {
@@ -172,7 +173,7 @@ template <bool kTF32, int BN, int STAGES>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
                    const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
-                   float* __restrict__ C, int M, int N2, int K2, int b0) {
+                   float* __restrict__ C, int M, int N2, int K2, int b0, const __grid_constant__ OutMap om) {
   constexpr int ES = kTF32 ? 4 : 2;
   constexpr int BK = 128 / ES;            // elements per 128-byte row
   constexpr int KSTEP = kTF32 ? 8 : 16;   // K of one MMA instruction
@@ -190,6 +191,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t* done = acc_empty + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   int* abort_flag = (int*)(tmem_slot + 1);
+  uint64_t* coltab = (uint64_t*)(tmem_slot + 4);  // [BN/2] column offsets of this tile (8-aligned)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles_m = M / BM;
@@ -284,6 +286,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else {
     // accumulation warps: row 32 (warp % 4) + lane of the tile
     const int quarter = warp & 3;
+    const int et = threadIdx.x - 64;  // 0..127
+    if (!om.ident && et < BN / 2) coltab[et] = om.col(n0 / 2 + et);
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // the four accumulation warps only
     float acc[BN];
 #pragma unroll
     for (int i = 0; i < BN; ++i) acc[i] = 0.f;
@@ -310,9 +315,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (ok && !*(volatile int*)abort_flag) {
       const int row = m0 + quarter * 32 + lane;
-      float4* dst = (float4*)(C + ((int64_t)bz * M + row) * N2 + n0);
+      if (om.ident) {
+        float4* dst = (float4*)(C + ((int64_t)bz * M + row) * N2 + n0);
 #pragma unroll
-      for (int i = 0; i < BN / 4; ++i) dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+        for (int i = 0; i < BN / 4; ++i)
+          dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+      } else {
+        // complex column n0/2 + i of row `row`, placed in the consumer's layout
+        float2* C2 = (float2*)C;
+        const uint64_t roff = om.row(bz, row, M, N2 / 2);
+#pragma unroll
+        for (int i = 0; i < BN / 2; ++i) C2[roff + coltab[i]] = make_float2(acc[2 * i], acc[2 * i + 1]);
+      }
     }
   }
   // all MMAs retired before TMEM is freed
@@ -432,7 +446,7 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
   if ((r = make_map(&mBh, b_hi, kTF32, K2, N2, nb, BN))) return r;
   if ((r = make_map(&mBl, b_lo, kTF32, K2, N2, nb, BN))) return r;
   constexpr uint32_t STAGE_BYTES = 2 * BM * 128 + 2 * BN * 128;
-  const size_t smem = 1024 + STAGES * STAGE_BYTES + (2 * STAGES + 5) * 8 + 16;
+  const size_t smem = 1024 + STAGES * STAGE_BYTES + (2 * STAGES + 5) * 8 + 16 + BN / 2 * 8;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kTF32, BN, STAGES>,
@@ -445,7 +459,7 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
     int64_t cnt = nb - b0 < 65535 ? nb - b0 : 65535;
     dim3 grid((unsigned)tiles, 1, (unsigned)cnt);
     tc_gemm_kernel<kTF32, BN, STAGES><<<grid, kTcThreads, smem, st>>>(mAh, mAl, mBh, mBl, C, (int)M, (int)N2,
-                                                                     (int)K2, (int)b0);
+                                                                     (int)K2, (int)b0, out_map(d));
   }
   return (int)cudaGetLastError();
 }
@@ -454,7 +468,8 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
 
 // Shapes reaching here are powers of two with M >= 128, N >= 32, K >= 32
 // (checked again below); the scratch holds the four planes.
-int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* C, void* ws, cudaStream_t st) {
+int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* C, void* scratch_ptr,
+                   cudaStream_t st) {
   if (d.M < BM || d.N < 32 || d.K < 32 || (d.M % BM) || (d.N % 32) || (d.K % 32) || d.M > (1 << 30) ||
       2 * d.N > (1 << 30) || 2 * d.K > (1 << 30))
     return (int)cudaErrorInvalidValue;
@@ -462,7 +477,8 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   const uint64_t es = tf32 ? 4 : 2;
   const uint64_t need = (uint64_t)d.batch * (d.M * 2 * d.K * 2 + 2 * d.N * 2 * d.K * 2) * es;
   if (need > d.scratch_elems * 8) return (int)cudaErrorInvalidValue;
-  uint8_t* scratch = (uint8_t*)((float2*)ws + d.scratch);
+  uint8_t* scratch = (uint8_t*)scratch_ptr;
+  if (!scratch) return (int)cudaErrorInvalidValue;
   if (tf32) {
     if (d.N >= 64) return run_tc<true, 128, 3>(d, A, B, (float*)C, scratch, st);
     return run_tc<true, 64, 4>(d, A, B, (float*)C, scratch, st);

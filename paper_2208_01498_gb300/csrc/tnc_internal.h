@@ -82,6 +82,9 @@ struct PlannerStats {
   int ssa_calls = 0, ssa_valid = 0, ssa_fallback = 0, greedy_clusters = 0;
 };
 Tree plan_tree(const PlanNet& pn, const PlannerOpts& o, PlannerStats* st);
+int ssa_separate_points(const double* pos, const double* rad, int n, int dim, uint64_t seed, int trials,
+                        int* cls_out, int* valid, int* k_out);
+int centerpoint_points(const double* pts, int n, int D, uint64_t seed, double* c);
 
 // Node output labels recomputed for a given set of labels that are kept to
 // the root; cost and size in log2.

@@ -54,7 +54,13 @@ struct GemmDesc {
   uint64_t scratch;      // workspace element offset of per-node scratch (0 if none)
   uint64_t scratch_elems;
   int splitk;            // CUDA-core kernels: K split into this many FP32 chunks summed in FP64
-  int pad_;
+  // Output layout.  c_ident: C stored [b][M][N].  Otherwise element (b, m, n)
+  // is stored at sum_i bit_i(n) << c_pos[i] + sum_i bit_i(m) << c_pos[nN + i]
+  // + sum_i bit_i(b) << c_pos[nN + nM + i] (M, N, batch powers of two with
+  // nN = log2 N, nM = log2 M, nB = log2 batch): the layout the consumer reads.
+  int c_ident;
+  int nN, nM, nB;
+  int8_t c_pos[kMaxRank];
 };
 
 // Final accumulation: out[beta][j] += sum over the bits of the grouped
@@ -74,7 +80,14 @@ int launch_gather(const GatherDesc* d_descs, int n_descs, int max_out_rank, cons
                   void* ws, const uint8_t* d_bits, int n_qubits, const uint64_t* d_slice_ctr,
                   void* stream);
 int launch_permute(const PermDesc& d, void* ws, void* stream);
+int launch_permute_ptr(const PermDesc& d, const void* in, void* out, void* stream);
 int launch_gemm(const GemmDesc& d, const void* base, void* ws, void* stream);
+int launch_gemm_ptr(const GemmDesc& d, const void* A, const void* B, void* C, void* scratch, void* stream);
+
+// kernel variant, split-K and scratch size of a GEMM node (shared by the
+// plan compiler and the kernel-level entry points)
+void choose_gemm_kernel(GemmDesc& g);
+uint64_t gemm_scratch_bytes(const GemmDesc& g);
 int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, void* stream);
 int launch_zero(void* ptr, size_t bytes, void* stream);
 int launch_set_counter(uint64_t* d_ctr, uint64_t value, void* stream);

@@ -63,7 +63,8 @@ EXPORTED = [
     "tnc_contract_amplitudes_dbits", "tnc_contract_partial", "tnc_server_create",
     "tnc_server_submit", "tnc_server_poll", "tnc_server_wait", "tnc_server_cancel",
     "tnc_server_destroy", "tnc_plan_set_profiling", "tnc_plan_get_profile", "tnc_device_error",
-    "tnc_contract_amplitudes_static",
+    "tnc_contract_amplitudes_static", "tnc_permute", "tnc_cgemm_scratch_bytes", "tnc_cgemm",
+    "tnc_ssa_separate", "tnc_centerpoint",
 ]
 
 
@@ -95,6 +96,12 @@ def _load():
         "tnc_plan_set_profiling": (i, [vp, i]),
         "tnc_device_error": (i, [C.POINTER(i)]),
         "tnc_contract_amplitudes_static": (i, [vp, vp, i, vp, vp]),
+        "tnc_permute": (i, [vp, vp, i, C.POINTER(i), vp]),
+        "tnc_ssa_separate": (i, [C.POINTER(C.c_double), C.POINTER(C.c_double), i, i, u64, i, C.POINTER(i),
+                                 C.POINTER(i), C.POINTER(i)]),
+        "tnc_centerpoint": (i, [C.POINTER(C.c_double), i, i, u64, C.POINTER(C.c_double)]),
+        "tnc_cgemm_scratch_bytes": (sz, [C.c_int64] * 4 + [i]),
+        "tnc_cgemm": (i, [vp, vp, vp] + [C.c_int64] * 4 + [i, i, i, vp, sz, vp]),
         "tnc_plan_get_profile": (i, [vp, C.POINTER(i), i, C.POINTER(C.c_double), C.POINTER(i),
                                      C.POINTER(i), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     }
@@ -300,3 +307,52 @@ def contract_amplitudes_static(p: Plan, bits, out, stream=None):
                                               C.c_void_p(out.data_ptr()), _stream_ptr(stream)),
            "tnc_contract_amplitudes_static")
     return out
+
+
+def permute(x, src_bit, out=None, stream=None):
+    """``tnc_permute`` on a complex64 CUDA tensor of 2^rank elements."""
+    import torch
+    rank = len(src_bit)
+    if out is None:
+        out = torch.empty_like(x)
+    sb = np.ascontiguousarray(src_bit, np.int32)
+    _check(lib.tnc_permute(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), rank,
+                           sb.ctypes.data_as(C.POINTER(C.c_int)), _stream_ptr(stream)), "tnc_permute")
+    return out
+
+
+def cgemm(A, B, batch, M, N, K, transA=0, transB=0, form="fp32", out=None, scratch=None, stream=None):
+    """``tnc_cgemm``: batched complex GEMM of one tree node on complex64 CUDA tensors."""
+    import torch
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    need = lib.tnc_cgemm_scratch_bytes(batch, M, N, K, f)
+    if out is None:
+        out = torch.empty((batch, M, N), dtype=torch.complex64, device=A.device)
+    if scratch is None and need:
+        scratch = torch.empty(need, dtype=torch.uint8, device=A.device)
+    _check(lib.tnc_cgemm(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()), C.c_void_p(out.data_ptr()),
+                         batch, M, N, K, int(transA), int(transB), f,
+                         C.c_void_p(scratch.data_ptr() if scratch is not None else 0),
+                         scratch.numel() if scratch is not None else 0, _stream_ptr(stream)), "tnc_cgemm")
+    return out
+
+
+def ssa_separate(pos, rad, seed: int = 1, trials: int = 32):
+    """Algorithm 1 on spheres (centres ``pos`` [n][dim], radii ``rad``):
+    returns (side array: 0 inside, 1 outside, 2 intersected; valid; k)."""
+    pos = np.ascontiguousarray(pos, np.float64)
+    rad = np.ascontiguousarray(rad, np.float64)
+    n, dim = pos.shape
+    side = np.zeros(n, np.int32)
+    valid, k = C.c_int(), C.c_int()
+    _check(lib.tnc_ssa_separate(_ptr(pos, C.c_double), _ptr(rad, C.c_double), n, dim, seed, trials,
+                                _ptr(side, C.c_int), C.byref(valid), C.byref(k)), "tnc_ssa_separate")
+    return side, bool(valid.value), k.value
+
+
+def centerpoint(pts, seed: int = 1):
+    pts = np.ascontiguousarray(pts, np.float64)
+    c = np.zeros(pts.shape[1], np.float64)
+    _check(lib.tnc_centerpoint(_ptr(pts, C.c_double), pts.shape[0], pts.shape[1], seed, _ptr(c, C.c_double)),
+           "tnc_centerpoint")
+    return c

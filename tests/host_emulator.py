@@ -122,7 +122,23 @@ def emulate_program(e: dict, bits: np.ndarray, groups=None) -> np.ndarray:
                 Bm = Bb[st["b"]: st["b"] + Bn * K * N].astype(np.complex128)
                 Bm = Bm.reshape(Bn, N, K).transpose(0, 2, 1) if st["tB"] else Bm.reshape(Bn, K, N)
                 assert np.isfinite(A).all() and np.isfinite(Bm).all(), "read of an unwritten workspace slot"
-                ws[st["c"]: st["c"] + Bn * M * N] = (A @ Bm).astype(np.complex64).reshape(-1)
+                Cv = (A @ Bm).astype(np.complex64).reshape(-1)
+                if st.get("c_ident", 1):
+                    ws[st["c"]: st["c"] + Bn * M * N] = Cv
+                else:
+                    # element (b, m, n) at the bit positions c_pos: n bits, m bits, batch bits
+                    idx = np.arange(Bn * M * N, dtype=np.int64)
+                    nN, nM = int(np.log2(N)), int(np.log2(M))
+                    n_, m_, b_ = idx % N, (idx // N) % M, idx // (N * M)
+                    off = np.zeros_like(idx)
+                    pos = st["c_pos"]
+                    for i in range(nN):
+                        off |= ((n_ >> i) & 1) << pos[i]
+                    for i in range(nM):
+                        off |= ((m_ >> i) & 1) << pos[nN + i]
+                    for i in range(len(pos) - nN - nM):
+                        off |= ((b_ >> i) & 1) << pos[nN + nM + i]
+                    ws[st["c"] + off] = Cv
         rank = len(acc["role"])
         root = ws[acc["src"]: acc["src"] + (1 << rank)].astype(np.complex128)
         for beta in range(batch):

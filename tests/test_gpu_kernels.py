@@ -1,0 +1,90 @@
+"""Kernel-level parity (GPU): the permute and the complex GEMM of one tree
+node, called through tnc_permute / tnc_cgemm, against NumPy complex128."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# relative Frobenius error bound per form (random normal operands)
+TOL = {"fp32": 2e-6, "3xtf32": 4e-6, "split_bf16": 4e-5}
+
+
+@pytest.fixture(scope="module")
+def tnc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_01498_gb300 import tnc as t
+    return t
+
+
+def _crand(shape, rng):
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+
+
+@pytest.mark.parametrize("rank", [0, 1, 3, 5, 8, 11, 16, 21])
+@pytest.mark.parametrize("kind", ["random", "identity", "reverse"])
+def test_permute_matches_numpy(tnc, rank, kind):
+    rng = np.random.default_rng(rank)
+    src_bit = {"random": rng.permutation(rank), "identity": np.arange(rank),
+               "reverse": np.arange(rank)[::-1]}[kind].astype(np.int32)
+    x = _crand(1 << rank, rng)
+    got = tnc.permute(torch.from_numpy(x).cuda(), src_bit).cpu().numpy()
+    # out bit k = in bit src_bit[k]; numpy axis a <-> bit rank-1-a
+    perm = [rank - 1 - src_bit[rank - 1 - a] for a in range(rank)]
+    ref = np.transpose(x.reshape((2,) * rank), perm).reshape(-1) if rank else x
+    assert np.array_equal(got, ref)
+
+
+def test_permute_rejects_non_permutation(tnc):
+    x = torch.zeros(8, dtype=torch.complex64, device="cuda")
+    with pytest.raises(tnc.TncError) as ei:
+        tnc.permute(x, [0, 0, 1])
+    assert ei.value.status == tnc.TNC_EINVAL
+
+
+SHAPES = [  # batch, M, N, K, transA, transB
+    (1, 1, 1, 1, 0, 0), (3, 5, 7, 9, 0, 0), (2, 64, 48, 100, 1, 0), (2, 33, 65, 17, 0, 1),
+    (1, 1000, 4, 2, 0, 1), (4, 513, 16, 16, 1, 1), (1, 2, 2, 100000, 0, 1), (2, 8, 8, 20000, 1, 0),
+    (1, 4, 4, 3000, 0, 0), (8, 16, 256, 8, 0, 1),
+]
+TC_SHAPES = [(4, 128, 64, 64, 0, 1), (2, 256, 128, 512, 0, 1), (1, 512, 256, 4096, 0, 1),
+             (3, 128, 32, 32, 1, 0), (2, 128, 128, 1024, 0, 0)]
+
+
+def _ref(A, B, batch, M, N, K, tA, tB):
+    a = A.reshape(batch, K, M).transpose(0, 2, 1) if tA else A.reshape(batch, M, K)
+    b = B.reshape(batch, N, K).transpose(0, 2, 1) if tB else B.reshape(batch, K, N)
+    return a.astype(np.complex128) @ b.astype(np.complex128)
+
+
+def _check_gemm(tnc, shape, form):
+    batch, M, N, K, tA, tB = shape
+    rng = np.random.default_rng(batch * 7 + M + N + K)
+    A = _crand(batch * M * K, rng)
+    B = _crand(batch * K * N, rng)
+    got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, tA, tB, form)
+    torch.cuda.synchronize()
+    ref = _ref(A, B, batch, M, N, K, tA, tB)
+    err = np.linalg.norm(got.cpu().numpy().astype(np.complex128) - ref) / np.linalg.norm(ref)
+    assert err <= TOL[form], f"{shape} {form}: {err:.3g}"
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_cgemm_cuda_cores(tnc, shape):
+    _check_gemm(tnc, shape, "fp32")
+
+
+@pytest.mark.parametrize("shape", TC_SHAPES)
+@pytest.mark.parametrize("form", ["split_bf16", "3xtf32", "fp32"])
+def test_cgemm_tensor_cores(tnc, shape, form):
+    _check_gemm(tnc, shape, form)
+
+
+def test_cgemm_scratch_too_small(tnc):
+    A = torch.zeros(128 * 64, dtype=torch.complex64, device="cuda")
+    B = torch.zeros(64 * 64, dtype=torch.complex64, device="cuda")
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(tnc.TncError) as ei:
+        tnc.cgemm(A, B, 1, 128, 64, 64, 0, 1, "split_bf16", scratch=small)
+    assert ei.value.status == tnc.TNC_ENOMEM
