@@ -152,6 +152,73 @@ def run_reference(args):
     return 0
 
 
+def serving_measure(tnc, torch, form: str, seed: int = 0, n_req: int = 240, cost_cap_log2: float = 36.0,
+                    ws_cap_bytes: int = 8 << 30):
+    """Poisson-arriving amplitude requests over the mixed pool (2D L x L
+    random circuits and (2+1)D layered circuits), 1-256 bitstrings each
+    (log-uniform), served by the continuous-batching loop; p50/p99 latency and
+    amplitudes/s at two arrival rates relative to the measured single-stream
+    capacity.  Instances planned above 2^cost_cap_log2 paper ops are excluded
+    and listed, as are those whose workspace exceeds ws_cap_bytes."""
+    rng = np.random.default_rng(seed + 17)
+    buckets = [1, 16, 256]
+    pool, excluded = [], []
+    for gl in C.serving_pool(seed):
+        net = tnc.Network(gl)
+        big = tnc.Plan(net, max_batch=buckets[-1], form=form)
+        if big.report["tree_cost_log2"] > cost_cap_log2 or big.ws_bytes > ws_cap_bytes:
+            excluded.append({"circuit": gl.name, "paper_ops_log2": round(big.report["tree_cost_log2"], 1),
+                             "ws_GB": round(big.ws_bytes / 1e9, 1)})
+            continue
+        pool.append((gl, {b: (big if b == buckets[-1] else tnc.Plan(net, max_batch=b, form=form))
+                          for b in buckets}))
+    if not pool:
+        return {"excluded": excluded}
+    reqs = []
+    for i in range(n_req):
+        gl, plans = pool[int(rng.integers(len(pool)))]
+        nb = int(round(float(np.exp(rng.uniform(0.0, np.log(256.0))))))
+        bucket = next(b for b in buckets if b >= nb)
+        reqs.append((gl, plans[bucket], C.random_bitstrings(gl.n_qubits, nb, 5000 + i)))
+    # single-stream service time of the mix (alone, warm)
+    ws = {id(p): tnc.alloc_workspace(p) for _, plans in pool for p in plans.values()}
+    for gl, p, bits in reqs[:len(pool) * 3]:
+        tnc.contract_amplitudes(p, bits, ws=ws[id(p)])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for gl, p, bits in reqs[:60]:
+        tnc.contract_amplitudes(p, bits, ws=ws[id(p)])
+        torch.cuda.synchronize()
+    service = (time.perf_counter() - t0) / 60
+    del ws
+    arena_bytes = (2 * max(p.ws_bytes for _, pl in pool for p in pl.values()) + (64 << 20)) // 256 * 256
+    arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
+    result = {"pool": len(pool), "excluded": excluded, "requests": n_req, "streams": 4,
+              "single_stream_ms_per_request": 1e3 * service, "rates": []}
+    for factor in (0.5, 0.9):
+        rate = factor / service
+        gaps = rng.exponential(1.0 / rate, size=n_req)
+        srv = tnc.Server(arena, n_streams=4)
+        outs, tickets = [], []
+        start = time.perf_counter()
+        due = start
+        for (gl, p, bits), gap in zip(reqs, gaps):
+            due += gap
+            while time.perf_counter() < due:
+                pass
+            out = torch.empty((bits.shape[0], 1 << p.n_open), dtype=torch.complex128, device="cuda")
+            outs.append(out)
+            tickets.append(srv.submit(p, bits, out))
+        lat = [srv.wait(t, 120000) for t in tickets]
+        span = time.perf_counter() - start
+        srv.close()
+        amps = sum(b.shape[0] for _, _, b in reqs)
+        result["rates"].append({"rate_factor": factor, "requests_per_s": rate,
+                                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                "amplitudes_per_s": amps / span})
+    return result
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -308,6 +375,8 @@ def run_ours(args):
         "clocks": ck,
         "gpu_launches": int(args.steps * rep["n_launches"]),
     }
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_measure(tnc, torch, args.form, args.seed)
     if rank == 0 and not args.no_cpu_baseline:
         v, n_done, dt = _cpu_oracle(gl, bits[args.warmup:args.warmup + 1])
         line["cpu_baseline"] = {"value": v, "unit": "amplitudes/s", "cores": 1, "kind": "oracle",
@@ -330,6 +399,7 @@ def main():
     ap.add_argument("--form", choices=["fp32", "3xtf32", "split_bf16"], default="split_bf16")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-mix latency measurement")
     ap.add_argument("--rows", type=int, default=5, help="IQP lattice rows (the benchmark uses 5 x 8)")
     ap.add_argument("--cols", type=int, default=8)
     args = ap.parse_args()

@@ -83,6 +83,7 @@ typedef struct {
   int ssa_trials;           /* great circles tried per separator (Alg. 1 step 7) */
   int leaf_size;            /* clusters of at most this many tensors are contracted greedily */
   int max_group_log2;       /* at most 2^k slices run together in one launch per node */
+  int use_graph;            /* 1: replay each slice group as a captured CUDA graph */
 } tnc_plan_opts;
 
 typedef struct {
@@ -116,7 +117,7 @@ int tnc_load_network(const tnc_network_desc* desc, tnc_network_t** out);
 void tnc_free_network(tnc_network_t* net);
 
 /* Fill *opts with defaults (no open qubits, batch 1, no cap, FP32, 32
- * trials, leaf size 8, group log2 6). */
+ * trials, leaf size 8, group log2 6, CUDA graphs on). */
 void tnc_plan_opts_default(tnc_plan_opts* opts);
 
 /* ------------------------------------------------- planner primitives (host)
@@ -172,6 +173,7 @@ int tnc_plan_set_profiling(tnc_plan_t* plan, int enable);
  * (8 M real flops per node, Eq. 3; 8 (|A|+|B|+|C|) bytes; a permutation
  * moves 16 bytes per element).  Arrays may be NULL to query n. */
 #define TNC_STEP_PERMUTE 100
+#define TNC_STEP_GROUPED 101
 int tnc_plan_get_profile(tnc_plan_t* plan, int* n_steps, int cap, double* ms, int* runs, int* kind,
                          double* flops, double* bytes);
 

@@ -87,7 +87,7 @@ static void fill_report(Plan& p, double plan_ms) {
   r.n_slices = std::exp2((double)r.n_sliced);
   r.n_slice_groups = (int)groups;
   int nodes = 0;
-  for (auto& s : p.prog.steps) nodes += s.kind == ST_GEMM;
+  for (auto& s : p.prog.steps) nodes += s.kind == ST_GEMM ? 1 : s.kind == ST_GROUPED ? s.g_count : 0;
   r.n_nodes = nodes;
   r.n_leaves = (int)p.net.leaves.size();
   r.max_rank = p.prog.max_rank;
@@ -95,7 +95,7 @@ static void fill_report(Plan& p, double plan_ms) {
   // counter, the gather and the accumulation, plus every step's launches
   int per_group = 2 + (p.prog.gathers.empty() ? 0 : 1);
   for (auto& s : p.prog.steps) {
-    if (s.kind == ST_PERMUTE) {
+    if (s.kind == ST_PERMUTE || s.kind == ST_GROUPED) {
       per_group += 1;
       continue;
     }
@@ -180,6 +180,7 @@ void tnc_plan_opts_default(tnc_plan_opts* o) {
   o->ssa_trials = 32;
   o->leaf_size = 8;
   o->max_group_log2 = 6;
+  o->use_graph = 1;
 }
 
 int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** out, tnc_plan_report* rep) {
@@ -255,12 +256,15 @@ void tnc_free_plan(tnc_plan_t* plan) {
   Plan& p = plan->p;
   for (auto& r : p.prof) cudaEventDestroy((cudaEvent_t)r.ev);
   p.prof.clear();
+  for (auto& ge : p.graphs) cudaGraphExecDestroy((cudaGraphExec_t)ge.exec);
+  p.graphs.clear();
   if (p.d_base || p.d_gathers) {
     int prev = -1;
     cudaGetDevice(&prev);
     if (p.device >= 0) cudaSetDevice(p.device);
     if (p.d_base) cudaFree(p.d_base);
     if (p.d_gathers) cudaFree(p.d_gathers);
+    if (p.d_grouped) cudaFree(p.d_grouped);
     if (prev >= 0) cudaSetDevice(prev);
   }
   delete plan;
@@ -342,7 +346,19 @@ int tnc_plan_export_json(const tnc_plan_t* plan, char* buf, size_t cap, size_t* 
   for (size_t i = 0; i < p.prog.steps.size(); ++i) {
     const Step& s = p.prog.steps[i];
     o << (i ? "," : "") << "{\"kind\":" << s.kind << ",\"node\":" << s.node;
-    if (s.kind == ST_GEMM) {
+    if (s.kind == ST_GROUPED) {
+      o << ",\"problems\":[";
+      for (int q = 0; q < s.g_count; ++q) {
+        const GroupedDesc& gd = p.prog.grouped[s.g_first + q];
+        o << (q ? "," : "") << "{\"batch\":" << gd.batch << ",\"M\":" << gd.M << ",\"N\":" << gd.N
+          << ",\"K\":" << gd.K << ",\"tA\":0,\"tB\":1,\"kernel\":2,\"a\":" << gd.a << ",\"b\":" << gd.b
+          << ",\"c\":" << gd.c << ",\"a_buf\":" << gd.a_buf << ",\"b_buf\":" << gd.b_buf
+          << ",\"c_ident\":" << gd.c_ident << ",\"c_pos\":[";
+        for (int j = 0; j < gd.nN + gd.nM + gd.nB; ++j) o << (j ? "," : "") << (int)gd.c_pos[j];
+        o << "]}";
+      }
+      o << "]";
+    } else if (s.kind == ST_GEMM) {
       o << ",\"batch\":" << s.gemm.batch << ",\"M\":" << s.gemm.M << ",\"N\":" << s.gemm.N
         << ",\"K\":" << s.gemm.K << ",\"kernel\":" << s.gemm.kernel << ",\"tA\":" << s.gemm.transA
         << ",\"tB\":" << s.gemm.transB << ",\"a\":" << s.gemm.a << ",\"b\":" << s.gemm.b
@@ -407,6 +423,14 @@ int tnc_plan_upload(tnc_plan_t* plan, void* stream) {
                         cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: copy descriptors");
   }
+  size_t grb = std::max<size_t>(p.prog.grouped.size() * sizeof(GroupedDesc), 256);
+  e = cudaMalloc(&p.d_grouped, grb);
+  if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: cudaMalloc");
+  if (!p.prog.grouped.empty()) {
+    e = cudaMemcpyAsync(p.d_grouped, p.prog.grouped.data(), p.prog.grouped.size() * sizeof(GroupedDesc),
+                        cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: copy grouped descriptors");
+  }
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: sync");
   p.device = dev;
@@ -416,7 +440,7 @@ int tnc_plan_upload(tnc_plan_t* plan, void* stream) {
 // The executor: per serial slice group set the counter, gather the derived
 // leaves, run the node program, accumulate the root in FP64.
 static int run(tnc_plan_t* tp, const uint8_t* bits, bool bits_on_device, int batch, int g0, int g1, void* d_out,
-               void* d_ws, size_t ws_bytes, void* stream) {
+               void* d_ws, size_t ws_bytes, void* stream, bool allow_graph = true) {
   Plan& p = tp->p;
   if (!d_out || !d_ws || !bits) {
     set_error("tnc_contract: NULL pointer argument");
@@ -467,8 +491,9 @@ static int run(tnc_plan_t* tp, const uint8_t* bits, bool bits_on_device, int bat
                       bits_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "tnc_contract: copy bits");
   const size_t out_bytes = (size_t)batch * ((size_t)16 << p.open_qubits.size());
-  e = cudaMemsetAsync(d_out, 0, out_bytes, st);
-  if (e != cudaSuccess) return cuda_fail(e, "tnc_contract: memset out");
+  double2* acc = (double2*)(ws + p.prog.off_acc);
+  e = cudaMemsetAsync(acc, 0, out_bytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "tnc_contract: memset accumulator");
   uint64_t* d_ctr = (uint64_t*)(ws + p.prog.off_ctr);
   auto mark = [&](int step) -> int {
     if (!p.profiling) return TNC_OK;
@@ -480,37 +505,91 @@ static int run(tnc_plan_t* tp, const uint8_t* bits, bool bits_on_device, int bat
     p.prof.push_back({step, (void*)ev});
     return TNC_OK;
   };
+  // one slice group's program: gather, node steps, FP64 accumulation
+  auto program = [&](cudaStream_t s, bool marks) -> int {
+    int r;
+    if (!p.prog.gathers.empty()) {
+      r = launch_gather((const GatherDesc*)p.d_gathers, (int)p.prog.gathers.size(), p.prog.max_gather_rank,
+                        p.d_base, ws, (const uint8_t*)(ws + p.prog.off_bits), nq, d_ctr, s);
+      if (r) return cuda_fail((cudaError_t)r, "gather");
+    }
+    if (marks && (r = mark(-2)) != TNC_OK) return r;
+    for (size_t si = 0; si < p.prog.steps.size(); ++si) {
+      const Step& sp = p.prog.steps[si];
+      if (sp.kind == ST_PERMUTE)
+        r = launch_permute(sp.perm, ws, s);
+      else if (sp.kind == ST_GROUPED)
+        r = launch_grouped_narrow((const GroupedDesc*)p.d_grouped + sp.g_first, sp.g_count, sp.g_blocks,
+                                  p.d_base, ws, s);
+      else
+        r = launch_gemm(sp.gemm, p.d_base, ws, s);
+      if (r)
+        return cuda_fail((cudaError_t)r,
+                         sp.kind == ST_PERMUTE ? "permute" : sp.kind == ST_GROUPED ? "grouped" : "gemm");
+      if (marks && (r = mark((int)si)) != TNC_OK) return r;
+    }
+    r = launch_accum(p.prog.accum, ws, acc, batch, s);
+    if (r) return cuda_fail((cudaError_t)r, "accum");
+    return TNC_OK;
+  };
+  cudaGraphExec_t gexec = nullptr;
+  if (allow_graph && p.opts.use_graph && !p.profiling && g1 > g0) {
+    for (auto& ge : p.graphs)
+      if (ge.ws == d_ws && ge.batch == batch) gexec = (cudaGraphExec_t)ge.exec;
+    if (!gexec) {
+      // capture on a private stream (the caller's may be the legacy stream)
+      cudaStream_t cs;
+      e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "graph: cudaStreamCreate");
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+      if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_fail(e, "graph: cudaStreamBeginCapture");
+      }
+      int rc2 = program(cs, false);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+      cudaStreamDestroy(cs);
+      if (rc2 != TNC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc2;
+      }
+      if (e2 != cudaSuccess) return cuda_fail(e2, "graph: cudaStreamEndCapture");
+      e2 = cudaGraphInstantiate(&gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e2 != cudaSuccess) return cuda_fail(e2, "graph: cudaGraphInstantiate");
+      if (p.graphs.size() >= 4) {
+        cudaGraphExecDestroy((cudaGraphExec_t)p.graphs.front().exec);
+        p.graphs.erase(p.graphs.begin());
+      }
+      p.graphs.push_back({d_ws, batch, (void*)gexec});
+    }
+  }
   for (int g = g0; g < g1; ++g) {
     int r;
     if ((r = mark(-1)) != TNC_OK) return r;
     if ((r = launch_set_counter(d_ctr, (uint64_t)g, st))) return cuda_fail((cudaError_t)r, "set counter");
-    if (!p.prog.gathers.empty()) {
-      r = launch_gather((const GatherDesc*)p.d_gathers, (int)p.prog.gathers.size(), p.prog.max_gather_rank,
-                        p.d_base, ws, (const uint8_t*)(ws + p.prog.off_bits), nq, d_ctr, st);
-      if (r) return cuda_fail((cudaError_t)r, "gather");
+    if (gexec) {
+      e = cudaGraphLaunch(gexec, st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    } else if ((r = program(st, true)) != TNC_OK) {
+      return r;
     }
-    if ((r = mark(-2)) != TNC_OK) return r;
-    for (size_t si = 0; si < p.prog.steps.size(); ++si) {
-      const Step& s = p.prog.steps[si];
-      if (s.kind == ST_PERMUTE)
-        r = launch_permute(s.perm, ws, st);
-      else
-        r = launch_gemm(s.gemm, p.d_base, ws, st);
-      if (r) return cuda_fail((cudaError_t)r, s.kind == ST_PERMUTE ? "permute" : "gemm");
-      if ((r = mark((int)si)) != TNC_OK) return r;
-    }
-    r = launch_accum(p.prog.accum, ws, d_out, batch, st);
-    if (r) return cuda_fail((cudaError_t)r, "accum");
   }
+  e = cudaMemcpyAsync(d_out, acc, out_bytes, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "tnc_contract: copy out");
   return TNC_OK;
 }
 
 }  // extern "C"
 
 namespace tnc {
+// Host-bitstring contraction without CUDA-graph capture (used by the server,
+// whose workspace differs per request, and by the static-workspace entry
+// point, which must not take driver resources).
 int run_request(tnc_plan_t* plan, const uint8_t* host_bits, int batch, void* d_out, void* d_ws, size_t ws_bytes,
                 void* stream) {
-  return run(plan, host_bits, false, batch, 0, plan->p.rep.n_slice_groups, d_out, d_ws, ws_bytes, stream);
+  return run(plan, host_bits, false, batch, 0, plan->p.rep.n_slice_groups, d_out, d_ws, ws_bytes, stream, false);
 }
 }  // namespace tnc
 
@@ -651,9 +730,16 @@ int tnc_plan_get_profile(tnc_plan_t* plan, int* n_steps, int cap, double* ms, in
     const Step& s = p.prog.steps[i];
     if (ms) ms[i] = p.prof_ms[i];
     if (runs) runs[i] = p.prof_runs[i];
-    if (kind) kind[i] = s.kind == ST_PERMUTE ? TNC_STEP_PERMUTE : s.gemm.kernel;
+    if (kind)
+      kind[i] = s.kind == ST_PERMUTE ? TNC_STEP_PERMUTE : s.kind == ST_GROUPED ? TNC_STEP_GROUPED : s.gemm.kernel;
     double f = 0, b = 0;
-    if (s.kind == ST_GEMM) {
+    if (s.kind == ST_GROUPED) {
+      for (int q = 0; q < s.g_count; ++q) {
+        const GroupedDesc& gd = p.prog.grouped[s.g_first + q];
+        f += 8.0 * gd.batch * gd.M * gd.N * gd.K;
+        b += 8.0 * gd.batch * ((double)gd.M * gd.K + (double)gd.K * gd.N + (double)gd.M * gd.N);
+      }
+    } else if (s.kind == ST_GEMM) {
       const GemmDesc& g = s.gemm;
       f = 8.0 * g.batch * g.M * g.N * g.K;
       b = 8.0 * g.batch * ((double)g.M * g.K + (double)g.K * g.N + (double)g.M * g.N);

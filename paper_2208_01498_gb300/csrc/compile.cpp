@@ -310,6 +310,8 @@ int compile_program(Plan& p) {
   uint64_t off = align_up((uint64_t)batch_pad * net.n_qubits);
   pr.off_ctr = off;
   off += kAlign;
+  pr.off_acc = off;
+  off += align_up((uint64_t)batch_pad * 16 << p.open_qubits.size());
   const uint64_t leaf_area = off;
 
   // execution order: post-order, the child with the larger subtree peak first
@@ -449,11 +451,17 @@ int compile_program(Plan& p) {
 
   constexpr int BUF_ARENA = 2;
   double flops = 0, bytes = 0, pops = 0;
+
+  // shape of every node: batch, M (larger free side), N, K; operands are
+  // [b][free][K], so either child can play A
+  struct Shape {
+    int A, B, nb, nk, nM, nN;
+    GemmDesc g;
+  };
+  std::vector<Shape> shp(t.nodes.size());
   for (int v : order) {
     const TreeNode& nd = t.nodes[v];
     const int x = nd.left, y = nd.right;
-    for (int c : {x, y})
-      if (!placed[c]) place_leaf(c);
     std::set<int> Lx(t.nodes[x].out.begin(), t.nodes[x].out.end());
     std::set<int> Ly(t.nodes[y].out.begin(), t.nodes[y].out.end());
     int nb = 0, nk = 0, nfx = 0, nfy = 0;
@@ -465,45 +473,122 @@ int compile_program(Plan& p) {
     }
     for (int a : Ly)
       if (!Lx.count(a)) ++nfy;
-    // orientation by shape: the larger free side is M
-    const int A = nfx >= nfy ? x : y, B = nfx >= nfy ? y : x;
-    const int nM = nfx >= nfy ? nfx : nfy, nN = nfx >= nfy ? nfy : nfx;
-    // operand layouts are [b][free][K]: A as [b][M][K], B as [b][N][K]
-    const std::vector<int>& LA = want[A];
-    const std::vector<int>& LB = want[B];
+    Shape& s = shp[v];
+    s.A = nfx >= nfy ? x : y;
+    s.B = nfx >= nfy ? y : x;
+    s.nM = nfx >= nfy ? nfx : nfy;
+    s.nN = nfx >= nfy ? nfy : nfx;
+    s.nb = nb;
+    s.nk = nk;
+    GemmDesc& g = s.g;
+    std::memset(&g, 0, sizeof(g));
+    g.batch = (int64_t)1 << nb;
+    g.M = (int64_t)1 << s.nM;
+    g.N = (int64_t)1 << s.nN;
+    g.K = (int64_t)1 << nk;
+    g.transA = 0;
+    g.transB = 1;
+    g.form = form;
+    // output scatter: n bits (B's free labels, least significant first), then
+    // m bits (A's free labels), then batch bits, to their places in want[v]
+    const std::vector<int>& LA = want[s.A];
+    const std::vector<int>& LB = want[s.B];
     const std::vector<int>& LC = want[v];
-    uint64_t cbytes = nsize(v) * 8;
-    uint64_t coff = arena.alloc(cbytes);
+    g.nN = s.nN, g.nM = s.nM, g.nB = nb;
+    int i = 0;
+    for (int j = s.nN - 1; j >= 0; --j) g.c_pos[i++] = (int8_t)bitpos(LC, LB[nb + j]);
+    for (int j = s.nM - 1; j >= 0; --j) g.c_pos[i++] = (int8_t)bitpos(LC, LA[nb + j]);
+    for (int j = nb - 1; j >= 0; --j) g.c_pos[i++] = (int8_t)bitpos(LC, LA[j]);
+    bool ident = true;
+    for (int q = 0; q < i; ++q) ident &= g.c_pos[q] == q;
+    g.c_ident = ident ? 1 : 0;
+    choose_gemm_kernel(g);
+    double work = (double)g.batch * g.M * g.N * g.K;
+    flops += 8 * work;
+    pops += 2 * work;
+    bytes += 8.0 * ((double)g.batch * (g.M * g.K + g.K * g.N + g.M * g.N));
+  }
+
+  // nodes whose whole subtree is made of small narrow contractions run first,
+  // level by level, each level as one grouped launch
+  std::vector<char> small(t.nodes.size(), 0);
+  std::vector<int> lvl(t.nodes.size(), 0);
+  int max_lvl = 0;
+  for (int v : order) {
+    const TreeNode& nd = t.nodes[v];
+    const GemmDesc& g = shp[v].g;
+    bool ok = g.kernel == KG_NARROW && (double)g.batch * g.M * g.N <= (double)(1 << 20);
+    for (int c : {nd.left, nd.right})
+      if (t.nodes[c].left >= 0 && !small[c]) ok = false;
+    small[v] = ok ? 1 : 0;
+    lvl[v] = 1 + std::max(t.nodes[nd.left].left >= 0 ? lvl[nd.left] : 0,
+                          t.nodes[nd.right].left >= 0 ? lvl[nd.right] : 0);
+    if (small[v]) max_lvl = std::max(max_lvl, lvl[v]);
+  }
+  for (int L = 1; L <= max_lvl; ++L) {
+    std::vector<int> members;
+    for (int v : order)
+      if (small[v] && lvl[v] == L) members.push_back(v);
+    if (members.empty()) continue;
+    Step s;
+    std::memset(&s, 0, sizeof(s));
+    s.kind = ST_GROUPED;
+    s.node = -1;
+    s.g_first = (int)pr.grouped.size();
+    s.g_count = (int)members.size();
+    int64_t blocks = 0;
+    std::vector<uint64_t> to_free;
+    for (int v : members) {
+      const Shape& sh = shp[v];
+      for (int c : {sh.A, sh.B})
+        if (!placed[c]) place_leaf(c);
+      uint64_t coff = arena.alloc(nsize(v) * 8);
+      GroupedDesc gd;
+      std::memset(&gd, 0, sizeof(gd));
+      gd.a = loc[sh.A];
+      gd.b = loc[sh.B];
+      gd.a_buf = buf[sh.A];  // tag, fixed below
+      gd.b_buf = buf[sh.B];
+      gd.c = coff / 8;
+      gd.M = sh.g.M;
+      gd.N = (int)sh.g.N;
+      gd.K = (int)sh.g.K;
+      gd.batch = (int)sh.g.batch;
+      gd.c_ident = sh.g.c_ident;
+      gd.nN = sh.g.nN, gd.nM = sh.g.nM, gd.nB = sh.g.nB;
+      for (int q = 0; q < kMaxRank; ++q) gd.c_pos[q] = sh.g.c_pos[q];
+      gd.blocks_per_batch = (int)((sh.g.M + 127) / 128);
+      gd.first_block = blocks;
+      blocks += (int64_t)gd.blocks_per_batch * gd.batch;
+      pr.grouped.push_back(gd);
+      for (int c : {sh.A, sh.B})
+        if (buf[c] == BUF_ARENA) to_free.push_back(loc[c] * 8);
+      buf[v] = BUF_ARENA;
+      loc[v] = coff / 8;
+      placed[v] = 1;
+    }
+    s.g_blocks = blocks;
+    steps.push_back(s);
+    for (uint64_t f : to_free) arena.release(f);
+  }
+
+  for (int v : order) {
+    if (small[v]) continue;
+    const Shape& sh = shp[v];
+    for (int c : {sh.A, sh.B})
+      if (!placed[c]) place_leaf(c);
+    uint64_t coff = arena.alloc(nsize(v) * 8);
     Step s;
     std::memset(&s, 0, sizeof(s));
     s.kind = ST_GEMM;
     s.node = v;
+    s.gemm = sh.g;
     GemmDesc& g = s.gemm;
-    g.batch = (int64_t)1 << nb;
-    g.M = (int64_t)1 << nM;
-    g.N = (int64_t)1 << nN;
-    g.K = (int64_t)1 << nk;
-    g.transA = 0;
-    g.transB = 1;
-    g.a = loc[A];
-    g.b = loc[B];
-    g.a_buf = buf[A];
-    g.b_buf = buf[B];
+    g.a = loc[sh.A];
+    g.b = loc[sh.B];
+    g.a_buf = buf[sh.A];
+    g.b_buf = buf[sh.B];
     g.c = coff / 8;
-    g.form = form;
-    // output scatter: n bits (B's free labels, least significant first), then
-    // m bits (A's free labels), then batch bits, to their places in LC
-    g.nN = nN, g.nM = nM, g.nB = nb;
-    {
-      int i = 0;
-      for (int j = nN - 1; j >= 0; --j) g.c_pos[i++] = (int8_t)bitpos(LC, LB[nb + j]);
-      for (int j = nM - 1; j >= 0; --j) g.c_pos[i++] = (int8_t)bitpos(LC, LA[nb + j]);
-      for (int j = nb - 1; j >= 0; --j) g.c_pos[i++] = (int8_t)bitpos(LC, LA[j]);
-      bool ident = true;
-      for (int k = 0; k < i; ++k) ident &= g.c_pos[k] == k;
-      g.c_ident = ident ? 1 : 0;
-    }
-    choose_gemm_kernel(g);
     const uint64_t scratch_bytes = gemm_scratch_bytes(g);
     uint64_t soff = scratch_bytes ? arena.alloc(scratch_bytes) : 0;
     g.scratch = soff / 8;
@@ -511,15 +596,11 @@ int compile_program(Plan& p) {
     steps.push_back(s);
     fix_b.push_back({steps.size() - 1, 0});
     if (scratch_bytes) arena.release(soff);
-    for (int c : {A, B})
+    for (int c : {sh.A, sh.B})
       if (buf[c] == BUF_ARENA) arena.release(loc[c] * 8);
     buf[v] = BUF_ARENA;
     loc[v] = coff / 8;
     placed[v] = 1;
-    double work = (double)g.batch * g.M * g.N * g.K;
-    flops += 8 * work;
-    pops += 2 * work;
-    bytes += 8.0 * ((double)g.batch * (g.M * g.K + g.K * g.N + g.M * g.N));
   }
   if (!placed[t.root]) place_leaf(t.root);  // single-leaf network
   const std::vector<std::vector<int>>& layout = want;
@@ -533,6 +614,13 @@ int compile_program(Plan& p) {
     if (b == 0) return leaf_area / 8 + rel;
     return rel;
   };
+  for (auto& gd : pr.grouped) {
+    gd.a = abs_off(gd.a_buf, gd.a);
+    gd.b = abs_off(gd.b_buf, gd.b);
+    gd.c = abs_off(BUF_ARENA, gd.c);
+    gd.a_buf = gd.a_buf == 1 ? 1 : 0;
+    gd.b_buf = gd.b_buf == 1 ? 1 : 0;
+  }
   for (auto& f : fix_b) {
     Step& s = steps[f.first];
     s.gemm.a = abs_off(s.gemm.a_buf, s.gemm.a);

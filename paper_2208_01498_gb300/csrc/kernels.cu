@@ -217,6 +217,58 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ------------------------------------------------------------------ grouped narrow
+// Many independent narrow nodes in one launch: block -> (problem, batch,
+// row chunk) by binary search over the problems' first blocks.
+constexpr int kGroupThreads = 128;
+
+__global__ void __launch_bounds__(kGroupThreads)
+    grouped_narrow_kernel(const GroupedDesc* __restrict__ descs, int n, const float2* __restrict__ base,
+                          float2* __restrict__ ws) {
+  __shared__ float2 Bs[16 * 16];
+  __shared__ uint64_t coff[16];
+  int lo = 0, hi = n - 1;
+  const int64_t blk = blockIdx.x;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (descs[mid].first_block <= blk)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const GroupedDesc& d = descs[lo];
+  const int64_t local = blk - d.first_block;
+  const int64_t bz = local / d.blocks_per_batch;
+  const int64_t chunk = local % d.blocks_per_batch;
+  const int N = d.N, K = d.K;
+  const float2* A = (d.a_buf ? base : ws) + d.a + bz * d.M * K;
+  const float2* B = (d.b_buf ? base : ws) + d.b + bz * (int64_t)K * N;
+  float2* C = ws + d.c;
+  for (int e = threadIdx.x; e < K * N; e += blockDim.x) {
+    int kk = e / N, nn = e % N;
+    Bs[e] = B[(int64_t)nn * K + kk];  // B stored [N][K]
+  }
+  OutMap om;
+  om.ident = d.c_ident, om.nN = d.nN, om.nM = d.nM, om.nB = d.nB;
+  for (int i = 0; i < kMaxRank; ++i) om.pos[i] = d.c_pos[i];
+  if (threadIdx.x < N) coff[threadIdx.x] = om.col(threadIdx.x);
+  __syncthreads();
+  const int64_t m = chunk * kGroupThreads + threadIdx.x;
+  if (m >= d.M) return;
+  float2 a[16];
+#pragma unroll
+  for (int kk = 0; kk < 16; ++kk)
+    if (kk < K) a[kk] = A[m * K + kk];
+  const uint64_t roff = om.row(bz, m, d.M, N);
+  for (int nn = 0; nn < N; ++nn) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk)
+      if (kk < K) acc = cmul_add(acc, a[kk], Bs[kk * N + nn]);
+    C[roff + coff[nn]] = acc;
+  }
+}
+
 // ------------------------------------------------------------------ dot
 // split-K for M*N <= 16: FP32 products summed in runs of 32, runs summed in
 // FP64; per-block partials reduced by a second pass.
@@ -500,6 +552,15 @@ int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp,
     default:
       return (int)cudaErrorInvalidValue;
   }
+}
+
+int launch_grouped_narrow(const GroupedDesc* d_descs, int n, int64_t total_blocks, const void* base, void* ws,
+                          void* stream) {
+  if (n <= 0 || total_blocks <= 0) return 0;
+  if (total_blocks > 0x7fffffff) return (int)cudaErrorInvalidConfiguration;
+  grouped_narrow_kernel<<<(unsigned)total_blocks, kGroupThreads, 0, (cudaStream_t)stream>>>(
+      d_descs, n, (const float2*)base, (float2*)ws);
+  return (int)cudaGetLastError();
 }
 
 int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, void* stream) {

@@ -93,22 +93,27 @@ double tree_cost_log2(const Tree& t);       // log2 sum_nodes 2 M
 int tree_max_rank(const Tree& t);
 
 // ------------------------------------------------------------------ program
-enum StepKind { ST_PERMUTE = 0, ST_GEMM = 1 };
+enum StepKind { ST_PERMUTE = 0, ST_GEMM = 1, ST_GROUPED = 2 };
 
 struct Step {
   int kind;
   PermDesc perm;
   GemmDesc gemm;
-  int node;  // tree node this step belongs to
+  int node;  // tree node this step belongs to (-1 for a grouped step)
+  // grouped step: problems [g_first, g_first + g_count) of Program::grouped
+  int g_first, g_count;
+  int64_t g_blocks;
 };
 
 struct Program {
   std::vector<GatherDesc> gathers;
+  std::vector<GroupedDesc> grouped;
   int max_gather_rank = 0;
   std::vector<Step> steps;
   AccumDesc accum;
   uint64_t ws_bytes = 0;
   uint64_t off_bits = 0, off_ctr = 0;   // byte offsets in the workspace
+  uint64_t off_acc = 0;                 // FP64 accumulator of the amplitudes
   uint64_t base_elems = 0;              // complex64 elements of the leaf buffer
   std::vector<std::complex<float>> base_host;
   double flops_per_group = 0, bytes_per_group = 0, paper_ops_per_group = 0;
@@ -137,10 +142,18 @@ struct Plan {
   std::vector<void*> ev_pool;
   std::vector<double> prof_ms;
   std::vector<int> prof_runs;
+  // captured CUDA graphs of one slice group, per (workspace, batch)
+  struct GraphEntry {
+    void* ws;
+    int batch;
+    void* exec;
+  };
+  std::vector<GraphEntry> graphs;
   // device state
   int device = -1;
   void* d_base = nullptr;        // leaf buffer (complex64)
   void* d_gathers = nullptr;
+  void* d_grouped = nullptr;
   std::mutex mu;
 };
 

@@ -63,6 +63,20 @@ struct GemmDesc {
   int8_t c_pos[kMaxRank];
 };
 
+// One problem of a grouped launch of narrow nodes (N, K <= 16): the same
+// contraction as a GemmDesc with the narrow kernel, A [b][M][K], B [b][N][K].
+// first_block: prefix sum of the blocks of the earlier problems.
+struct GroupedDesc {
+  uint64_t a, b, c;      // element offsets (a_buf/b_buf: 0 workspace, 1 leaf buffer)
+  int64_t M;
+  int N, K, batch;
+  int a_buf, b_buf;
+  int c_ident, nN, nM, nB;
+  int blocks_per_batch;
+  int8_t c_pos[kMaxRank];
+  int64_t first_block;
+};
+
 // Final accumulation: out[beta][j] += sum over the bits of the grouped
 // slices of root[...]; root bit k is beta bit (role 0, idx), open bit (role
 // 1, idx) or a grouped-slice bit (role 2, idx).
@@ -89,6 +103,8 @@ int launch_gemm_ptr(const GemmDesc& d, const void* A, const void* B, void* C, vo
 void choose_gemm_kernel(GemmDesc& g);
 uint64_t gemm_scratch_bytes(const GemmDesc& g);
 int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, void* stream);
+int launch_grouped_narrow(const GroupedDesc* d_descs, int n, int64_t total_blocks, const void* base, void* ws,
+                          void* stream);
 int launch_zero(void* ptr, size_t bytes, void* stream);
 int launch_set_counter(uint64_t* d_ctr, uint64_t value, void* stream);
 

@@ -42,7 +42,8 @@ class NetworkDesc(C.Structure):
 class PlanOpts(C.Structure):
     _fields_ = [("n_open", C.c_int), ("open_qubits", C.POINTER(C.c_int)), ("max_batch", C.c_int),
                 ("mem_cap_bytes", C.c_size_t), ("form", C.c_int), ("seed", C.c_uint64),
-                ("ssa_trials", C.c_int), ("leaf_size", C.c_int), ("max_group_log2", C.c_int)]
+                ("ssa_trials", C.c_int), ("leaf_size", C.c_int), ("max_group_log2", C.c_int),
+                ("use_graph", C.c_int)]
 
 
 class PlanReport(C.Structure):
@@ -168,7 +169,7 @@ class Plan:
 
     def __init__(self, net: Network, open_qubits=(), max_batch: int = 1, mem_cap_bytes: int = 0,
                  form: str = "fp32", seed: int = 1, ssa_trials: int = 32, leaf_size: int = 8,
-                 max_group_log2: int = 6):
+                 max_group_log2: int = 6, use_graph: bool = True):
         o = PlanOpts()
         lib.tnc_plan_opts_default(C.byref(o))
         self._open = np.ascontiguousarray(sorted(int(q) for q in open_qubits), np.int32)
@@ -181,6 +182,7 @@ class Plan:
         o.ssa_trials = int(ssa_trials)
         o.leaf_size = int(leaf_size)
         o.max_group_log2 = int(max_group_log2)
+        o.use_graph = int(bool(use_graph))
         rep = PlanReport()
         h = C.c_void_p()
         _check(lib.tnc_plan(net.handle, C.byref(o), C.byref(h), C.byref(rep)), "tnc_plan")
@@ -356,3 +358,49 @@ def centerpoint(pts, seed: int = 1):
     _check(lib.tnc_centerpoint(_ptr(pts, C.c_double), pts.shape[0], pts.shape[1], seed, _ptr(c, C.c_double)),
            "tnc_centerpoint")
     return c
+
+
+class Server:
+    """``tnc_server_*``: continuous batching of amplitude requests over a
+    device arena (a uint8 CUDA tensor owned by the caller)."""
+
+    def __init__(self, arena, n_streams: int = 4):
+        self.arena = arena
+        h = C.c_void_p()
+        _check(lib.tnc_server_create(C.c_void_p(arena.data_ptr()), arena.numel(), n_streams, C.byref(h)),
+               "tnc_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, plan: Plan, bits, out) -> int:
+        bits = np.ascontiguousarray(np.atleast_2d(bits), dtype=np.uint8)
+        t = C.c_uint64()
+        _check(lib.tnc_server_submit(self.handle, plan.handle, bits.ctypes.data_as(C.c_void_p), bits.shape[0],
+                                     C.c_void_p(out.data_ptr()), C.byref(t)), "tnc_server_submit")
+        self._keep[t.value] = out
+        return t.value
+
+    def poll(self, ticket: int):
+        done = C.c_int()
+        st = lib.tnc_server_poll(self.handle, ticket, C.byref(done))
+        return bool(done.value), st
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> float:
+        lat = C.c_double()
+        _check(lib.tnc_server_wait(self.handle, ticket, timeout_ms, C.byref(lat)), "tnc_server_wait")
+        self._keep.pop(ticket, None)
+        return lat.value
+
+    def cancel(self, ticket: int) -> int:
+        return lib.tnc_server_cancel(self.handle, ticket)
+
+    def close(self):
+        if self.handle:
+            lib.tnc_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

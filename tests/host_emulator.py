@@ -105,8 +105,11 @@ def emulate_program(e: dict, bits: np.ndarray, groups=None) -> np.ndarray:
             for pos, k in zip(gd["sliced_pos"], gd["sliced_bit"]):
                 src |= ((g >> k) & 1) << pos
             ws[gd["dst"] + o] = base[gd["src"] + src]
+        flat = []
         for st in e["steps"]:
-            if st["kind"] == 0:
+            flat += st["problems"] if st["kind"] == 2 else [st]
+        for st in flat:
+            if st.get("kind", 1) == 0:
                 r = st["rank"]
                 j = np.arange(1 << r, dtype=np.int64)
                 i = np.zeros_like(j)
