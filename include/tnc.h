@@ -209,6 +209,15 @@ int tnc_cgemm(const void* d_A, const void* d_B, void* d_C, int64_t batch, int64_
  * value.  A set flag means the affected contraction results are invalid. */
 int tnc_device_error(int* flag);
 
+/* Autotuner: for every contraction step of the plan, time each kernel
+ * variant that can run it on this GPU (tile shapes of the CUDA-core cGEMM,
+ * the narrow and split-K kernels, the tensor-core tile widths of the 3xTF32
+ * and split-BF16 forms), keep the fastest, and drop captured graphs.  Runs one
+ * slice group on d_ws (contents are scratch; ws_bytes >= report.ws_bytes);
+ * reps timed launches per variant (>= 1); synchronous.  *n_changed (may be
+ * NULL) receives the number of steps whose kernel changed. */
+int tnc_plan_autotune(tnc_plan_t* plan, void* d_ws, size_t ws_bytes, void* cuda_stream, int reps, int* n_changed);
+
 /* Amplitudes for `batch` bitstrings (1 <= batch <= max_batch).
  * bits: HOST uint8 [batch][n_qubits]; entries of open qubits are ignored.
  * d_out: DEVICE complex128 [batch][2^n_open], caller-owned, overwritten.

@@ -75,24 +75,9 @@ static void make_plan_net(const Network& net, const std::vector<int>& open_q, in
   for (int q : open_q) pn.global_out[net.final_label[q]] = 1;
 }
 
-static void fill_report(Plan& p, double plan_ms) {
-  tnc_plan_report& r = p.rep;
-  const double groups = std::exp2((double)p.sliced_serial.size());
-  r.paper_ops = p.prog.paper_ops_per_group * groups;
-  r.real_flops = p.prog.flops_per_group * groups;
-  r.bytes = p.prog.bytes_per_group * groups;
-  r.peak_bytes = p.prog.peak_bytes;
-  r.ws_bytes = p.prog.ws_bytes;
-  r.n_sliced = (int)(p.sliced_serial.size() + p.sliced_par.size());
-  r.n_slices = std::exp2((double)r.n_sliced);
-  r.n_slice_groups = (int)groups;
-  int nodes = 0;
-  for (auto& s : p.prog.steps) nodes += s.kind == ST_GEMM ? 1 : s.kind == ST_GROUPED ? s.g_count : 0;
-  r.n_nodes = nodes;
-  r.n_leaves = (int)p.net.leaves.size();
-  r.max_rank = p.prog.max_rank;
-  // kernels of this library launched per request: per slice group the
-  // counter, the gather and the accumulation, plus every step's launches
+// kernels of this library launched per slice group: the counter, the
+// gather and the accumulation, plus every step's launches
+static int launches_per_group(const Plan& p) {
   int per_group = 2 + (p.prog.gathers.empty() ? 0 : 1);
   for (auto& s : p.prog.steps) {
     if (s.kind == ST_PERMUTE || s.kind == ST_GROUPED) {
@@ -110,6 +95,26 @@ static void fill_report(Plan& p, double plan_ms) {
     else
       per_group += chunks;
   }
+  return per_group;
+}
+
+static void fill_report(Plan& p, double plan_ms) {
+  tnc_plan_report& r = p.rep;
+  const double groups = std::exp2((double)p.sliced_serial.size());
+  r.paper_ops = p.prog.paper_ops_per_group * groups;
+  r.real_flops = p.prog.flops_per_group * groups;
+  r.bytes = p.prog.bytes_per_group * groups;
+  r.peak_bytes = p.prog.peak_bytes;
+  r.ws_bytes = p.prog.ws_bytes;
+  r.n_sliced = (int)(p.sliced_serial.size() + p.sliced_par.size());
+  r.n_slices = std::exp2((double)r.n_sliced);
+  r.n_slice_groups = (int)groups;
+  int nodes = 0;
+  for (auto& s : p.prog.steps) nodes += s.kind == ST_GEMM ? 1 : s.kind == ST_GROUPED ? s.g_count : 0;
+  r.n_nodes = nodes;
+  r.n_leaves = (int)p.net.leaves.size();
+  r.max_rank = p.prog.max_rank;
+  const int per_group = launches_per_group(p);
   r.n_launches = (int)(per_group * groups);
   r.plan_ms = plan_ms;
 }
@@ -666,6 +671,87 @@ int tnc_cgemm(const void* A, const void* B, void* Cp, int64_t batch, int64_t M, 
   if (rc != TNC_OK) return rc;
   int r = launch_gemm_ptr(g, A, B, Cp, scratch, stream);
   return r ? cuda_fail((cudaError_t)r, "tnc_cgemm") : TNC_OK;
+}
+
+int tnc_plan_autotune(tnc_plan_t* plan, void* d_ws, size_t ws_bytes, void* stream, int reps, int* n_changed) {
+  if (!plan || !d_ws || reps < 1) {
+    set_error("tnc_plan_autotune: invalid argument");
+    return TNC_EINVAL;
+  }
+  Plan& p = plan->p;
+  if (ws_bytes < p.prog.ws_bytes || ((uintptr_t)d_ws & 255)) {
+    set_error("tnc_plan_autotune: workspace too small or not 256-byte aligned");
+    return ws_bytes < p.prog.ws_bytes ? TNC_ENOMEM : TNC_EINVAL;
+  }
+  int rc = device_of(d_ws, "tnc_plan_autotune");
+  if (rc != TNC_OK) return rc;
+  if ((rc = tnc_plan_upload(plan, stream)) != TNC_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)d_ws;
+  const int nq = p.net.n_qubits;
+  cudaError_t e = cudaMemsetAsync(ws + p.prog.off_bits, 0, ((size_t)1 << p.beta_bits) * nq, st);
+  if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_autotune: memset");
+  uint64_t* d_ctr = (uint64_t*)(ws + p.prog.off_ctr);
+  int r = launch_set_counter(d_ctr, 0, st);
+  if (!r && !p.prog.gathers.empty())
+    r = launch_gather((const GatherDesc*)p.d_gathers, (int)p.prog.gathers.size(), p.prog.max_gather_rank, p.d_base,
+                      ws, (const uint8_t*)(ws + p.prog.off_bits), nq, d_ctr, st);
+  if (r) return cuda_fail((cudaError_t)r, "tnc_plan_autotune: gather");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int changed = 0;
+  for (Step& s : p.prog.steps) {
+    if (s.kind == ST_GROUPED) {
+      r = launch_grouped_narrow((const GroupedDesc*)p.d_grouped + s.g_first, s.g_count, s.g_blocks, p.d_base, ws, st);
+      if (r) break;
+      continue;
+    }
+    if (s.kind != ST_GEMM) continue;
+    GemmDesc cand[kMaxCandidates];
+    int nc = 0;
+    gemm_candidates(s.gemm, cand, &nc);
+    int best = 0;
+    float best_ms = 3.4e38f;
+    for (int q = 0; q < nc; ++q) {
+      GemmDesc g = cand[q];
+      g.scratch = s.gemm.scratch;
+      g.scratch_elems = s.gemm.scratch_elems;
+      if (gemm_scratch_bytes(g) > g.scratch_elems * 8) continue;
+      if (launch_gemm(g, p.d_base, ws, st)) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaEventRecord(e0, st);
+      for (int i = 0; i < reps; ++i) launch_gemm(g, p.d_base, ws, st);
+      cudaEventRecord(e1, st);
+      e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(e, "tnc_plan_autotune: timing");
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) best_ms = ms, best = q;
+    }
+    GemmDesc g = cand[best];
+    g.scratch = s.gemm.scratch;
+    g.scratch_elems = s.gemm.scratch_elems;
+    if (g.kernel != s.gemm.kernel || g.tile != s.gemm.tile) ++changed;
+    s.gemm = g;
+    if ((r = launch_gemm(s.gemm, p.d_base, ws, st))) break;  // leave real data for the next steps
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (r) return cuda_fail((cudaError_t)r, "tnc_plan_autotune: launch");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_autotune: sync");
+  for (auto& ge : p.graphs) cudaGraphExecDestroy((cudaGraphExec_t)ge.exec);
+  p.graphs.clear();
+  p.rep.n_launches = launches_per_group(p) * p.rep.n_slice_groups;
+  if (n_changed) *n_changed = changed;
+  return TNC_OK;
 }
 
 int tnc_device_error(int* flag) {

@@ -87,6 +87,8 @@ int bitpos(const std::vector<int>& L, int x) {
 
 }  // namespace
 
+static void set_splitk(GemmDesc& g);
+
 // Kernel variant by shape: tiny outputs with long K -> split-K dot; narrow
 // N and K -> one row per thread; dense enough nodes of the tensor-core forms
 // -> tcgen05; otherwise the register-tiled CUDA-core kernel.  Long FP32 sums
@@ -105,6 +107,10 @@ void choose_gemm_kernel(GemmDesc& g) {
     g.kernel = KG_SIMT_64x32;
   else
     g.kernel = KG_SIMT_128x64;
+  set_splitk(g);
+}
+
+static void set_splitk(GemmDesc& g) {
   g.splitk = 1;
   const bool simt = g.kernel == KG_SIMT_128x64 || g.kernel == KG_SIMT_64x32 || g.kernel == KG_SIMT_32x128 ||
                     (g.kernel == KG_DOT && (g.M > 4 || g.N > 4));
@@ -113,6 +119,31 @@ void choose_gemm_kernel(GemmDesc& g) {
     while (s > 1 && (double)s * g.batch * g.M * g.N * 8 > (double)(256u << 20)) s >>= 1;
     g.splitk = (int)std::min<int64_t>(s, 4096);
   }
+}
+
+void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
+  int k = 0;
+  out[k++] = g0;
+  auto add = [&](int kernel, int tile) {
+    GemmDesc g = g0;
+    g.kernel = kernel;
+    g.tile = tile;
+    set_splitk(g);
+    for (int i = 0; i < k; ++i)
+      if (out[i].kernel == g.kernel && out[i].tile == g.tile) return;
+    if (k < kMaxCandidates) out[k++] = g;
+  };
+  add(KG_SIMT_128x64, 0);
+  add(KG_SIMT_64x32, 0);
+  add(KG_SIMT_32x128, 0);
+  if (g0.N <= 16 && g0.K <= 16) add(KG_NARROW, 0);
+  if (g0.M <= 4 && g0.N <= 4 && g0.K >= 512) add(KG_DOT, 0);
+  const bool pow2 = !(g0.M & (g0.M - 1)) && !(g0.N & (g0.N - 1)) && !(g0.K & (g0.K - 1));
+  if (g0.form != TNC_FP32 && pow2 && g0.M >= 128 && g0.N >= 32 && g0.K >= 32) {
+    add(KG_TC, 1);
+    if (g0.N >= 64) add(KG_TC, 2);
+  }
+  *n = k;
 }
 
 uint64_t gemm_scratch_bytes(const GemmDesc& g) {
@@ -589,7 +620,13 @@ int compile_program(Plan& p) {
     g.a_buf = buf[sh.A];
     g.b_buf = buf[sh.B];
     g.c = coff / 8;
-    const uint64_t scratch_bytes = gemm_scratch_bytes(g);
+    uint64_t scratch_bytes = 0;  // room for any candidate the autotuner may pick
+    {
+      GemmDesc cand[kMaxCandidates];
+      int nc = 0;
+      gemm_candidates(g, cand, &nc);
+      for (int q = 0; q < nc; ++q) scratch_bytes = std::max(scratch_bytes, gemm_scratch_bytes(cand[q]));
+    }
     uint64_t soff = scratch_bytes ? arena.alloc(scratch_bytes) : 0;
     g.scratch = soff / 8;
     g.scratch_elems = scratch_bytes / 8;

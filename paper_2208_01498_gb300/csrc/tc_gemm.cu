@@ -479,11 +479,13 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   if (need > d.scratch_elems * 8) return (int)cudaErrorInvalidValue;
   uint8_t* scratch = (uint8_t*)scratch_ptr;
   if (!scratch) return (int)cudaErrorInvalidValue;
+  const bool wide = d.tile == 2 || (d.tile == 0 && d.N >= 64);
+  if (wide && d.N < 64) return (int)cudaErrorInvalidValue;
   if (tf32) {
-    if (d.N >= 64) return run_tc<true, 128, 3>(d, A, B, (float*)C, scratch, st);
+    if (wide) return run_tc<true, 128, 3>(d, A, B, (float*)C, scratch, st);
     return run_tc<true, 64, 4>(d, A, B, (float*)C, scratch, st);
   }
-  if (d.N >= 64) return run_tc<false, 128, 3>(d, A, B, (float*)C, scratch, st);
+  if (wide) return run_tc<false, 128, 3>(d, A, B, (float*)C, scratch, st);
   return run_tc<false, 64, 4>(d, A, B, (float*)C, scratch, st);
 }
 

@@ -61,6 +61,7 @@ struct GemmDesc {
   int c_ident;
   int nN, nM, nB;
   int8_t c_pos[kMaxRank];
+  int tile;              // tensor-core tile width: 0 auto, 1 N = 64 real columns, 2 N = 128
 };
 
 // One problem of a grouped launch of narrow nodes (N, K <= 16): the same
@@ -102,6 +103,9 @@ int launch_gemm_ptr(const GemmDesc& d, const void* A, const void* B, void* C, vo
 // plan compiler and the kernel-level entry points)
 void choose_gemm_kernel(GemmDesc& g);
 uint64_t gemm_scratch_bytes(const GemmDesc& g);
+// every kernel variant that can run this node (the default choice first)
+void gemm_candidates(const GemmDesc& g, GemmDesc* out, int* n);
+constexpr int kMaxCandidates = 8;
 int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, void* stream);
 int launch_grouped_narrow(const GroupedDesc* d_descs, int n, int64_t total_blocks, const void* base, void* ws,
                           void* stream);

@@ -65,7 +65,7 @@ EXPORTED = [
     "tnc_server_submit", "tnc_server_poll", "tnc_server_wait", "tnc_server_cancel",
     "tnc_server_destroy", "tnc_plan_set_profiling", "tnc_plan_get_profile", "tnc_device_error",
     "tnc_contract_amplitudes_static", "tnc_permute", "tnc_cgemm_scratch_bytes", "tnc_cgemm",
-    "tnc_ssa_separate", "tnc_centerpoint",
+    "tnc_ssa_separate", "tnc_centerpoint", "tnc_plan_autotune",
 ]
 
 
@@ -101,6 +101,7 @@ def _load():
         "tnc_ssa_separate": (i, [C.POINTER(C.c_double), C.POINTER(C.c_double), i, i, u64, i, C.POINTER(i),
                                  C.POINTER(i), C.POINTER(i)]),
         "tnc_centerpoint": (i, [C.POINTER(C.c_double), i, i, u64, C.POINTER(C.c_double)]),
+        "tnc_plan_autotune": (i, [vp, vp, sz, vp, i, C.POINTER(i)]),
         "tnc_cgemm_scratch_bytes": (sz, [C.c_int64] * 4 + [i]),
         "tnc_cgemm": (i, [vp, vp, vp] + [C.c_int64] * 4 + [i, i, i, vp, sz, vp]),
         "tnc_plan_get_profile": (i, [vp, C.POINTER(i), i, C.POINTER(C.c_double), C.POINTER(i),
@@ -207,6 +208,19 @@ class Plan:
 
     def upload(self, stream=None):
         _check(lib.tnc_plan_upload(self.handle, _stream_ptr(stream)), "tnc_plan_upload")
+
+    def autotune(self, ws=None, stream=None, reps: int = 3) -> int:
+        """``tnc_plan_autotune``: pick the fastest kernel variant per step on
+        this GPU; returns the number of steps that changed."""
+        if ws is None:
+            ws = alloc_workspace(self)
+        n = C.c_int()
+        _check(lib.tnc_plan_autotune(self.handle, C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream),
+                                     int(reps), C.byref(n)), "tnc_plan_autotune")
+        rep = PlanReport()
+        _check(lib.tnc_plan_get_report(self.handle, C.byref(rep)), "tnc_plan_get_report")
+        self.report = rep.as_dict()
+        return n.value
 
     def set_profiling(self, enable: bool):
         _check(lib.tnc_plan_set_profiling(self.handle, int(bool(enable))), "tnc_plan_set_profiling")

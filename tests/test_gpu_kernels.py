@@ -49,6 +49,7 @@ SHAPES = [  # batch, M, N, K, transA, transB
     (1, 4, 4, 3000, 0, 0), (8, 16, 256, 8, 0, 1),
 ]
 TC_SHAPES = [(4, 128, 64, 64, 0, 1), (2, 256, 128, 512, 0, 1), (1, 512, 256, 4096, 0, 1),
+             (2, 128, 32, 64, 0, 1), (1, 1024, 512, 8192, 0, 1),
              (3, 128, 32, 32, 1, 0), (2, 128, 128, 1024, 0, 0)]
 
 

@@ -214,3 +214,15 @@ def test_profiling_counts_every_step(tnc):
     assert (prof["runs"] == 3).all()
     assert (prof["ms"] > 0).all()
     assert abs(prof["flops"].sum() - p.report["real_flops"]) / p.report["real_flops"] < 1e-12
+
+
+def test_autotuned_plan_stays_correct(tnc):
+    gl = C.random_2d(4, 5, 10, 6)
+    bits = C.random_bitstrings(20, 8, 5)
+    ref = O.statevector_amplitudes(gl, bits)
+    for form in ("fp32", "split_bf16"):
+        p = tnc.Plan(tnc.Network(gl), max_batch=8, form=form)
+        ws = tnc.alloc_workspace(p)
+        p.autotune(ws, reps=2)
+        got = tnc.contract_amplitudes(p, bits, ws=ws).cpu().numpy()
+        _check(got, ref, 20, form)
