@@ -358,8 +358,7 @@ int tnc_plan_export_json(const tnc_plan_t* plan, char* buf, size_t cap, size_t* 
         o << (q ? "," : "") << "{\"batch\":" << gd.batch << ",\"M\":" << gd.M << ",\"N\":" << gd.N
           << ",\"K\":" << gd.K << ",\"tA\":0,\"tB\":1,\"kernel\":2,\"a\":" << gd.a << ",\"b\":" << gd.b
           << ",\"c\":" << gd.c << ",\"a_buf\":" << gd.a_buf << ",\"b_buf\":" << gd.b_buf
-          << ",\"c_ident\":" << gd.c_ident << ",\"c_fmt\":" << gd.c_fmt << ",\"c_kbits\":" << gd.c_kbits
-          << ",\"c_pos\":[";
+          << ",\"c_ident\":" << gd.c_ident << ",\"c_pos\":[";
         for (int j = 0; j < gd.nN + gd.nM + gd.nB; ++j) o << (j ? "," : "") << (int)gd.c_pos[j];
         o << "]}";
       }
@@ -369,9 +368,7 @@ int tnc_plan_export_json(const tnc_plan_t* plan, char* buf, size_t cap, size_t* 
         << ",\"K\":" << s.gemm.K << ",\"kernel\":" << s.gemm.kernel << ",\"tA\":" << s.gemm.transA
         << ",\"tB\":" << s.gemm.transB << ",\"a\":" << s.gemm.a << ",\"b\":" << s.gemm.b
         << ",\"c\":" << s.gemm.c << ",\"a_buf\":" << s.gemm.a_buf << ",\"b_buf\":" << s.gemm.b_buf
-        << ",\"c_ident\":" << s.gemm.c_ident << ",\"c_fmt\":" << s.gemm.c_fmt
-        << ",\"c_kbits\":" << s.gemm.c_kbits << ",\"a_split\":" << s.gemm.a_split
-        << ",\"b_split\":" << s.gemm.b_split << ",\"c_pos\":[";
+        << ",\"c_ident\":" << s.gemm.c_ident << ",\"c_pos\":[";
       for (int j = 0; j < s.gemm.nN + s.gemm.nM + s.gemm.nB; ++j) o << (j ? "," : "") << (int)s.gemm.c_pos[j];
       o << "]";
     } else {

@@ -124,17 +124,6 @@ static void set_splitk(GemmDesc& g) {
 void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
   int k = 0;
   out[k++] = g0;
-  if (g0.a_split || g0.b_split) {
-    // operands already in tensor-core plane form: only the tile width varies
-    for (int tile = 1; tile <= 2; ++tile) {
-      if (tile == 2 && g0.N < 64) continue;
-      GemmDesc g = g0;
-      g.tile = tile;
-      if (g.tile != g0.tile) out[k++] = g;
-    }
-    *n = k;
-    return;
-  }
   auto add = [&](int kernel, int tile) {
     GemmDesc g = g0;
     g.kernel = kernel;
@@ -567,29 +556,6 @@ int compile_program(Plan& p) {
                           t.nodes[nd.right].left >= 0 ? lvl[nd.right] : 0);
     if (small[v]) max_lvl = std::max(max_lvl, lvl[v]);
   }
-  // operand formats: a node consumed by a tensor-core node writes its output
-  // directly as that consumer's hi/lo planes (A' or B'^T), so the consumer
-  // needs no split pass for it; leaves are split by the consumer's prep
-  std::vector<int> fmt(t.nodes.size(), 0), fkbits(t.nodes.size(), 0);
-  const int tf32 = form == TNC_3XTF32 ? 1 : 0;
-  const uint64_t es = tf32 ? 4 : 2;
-  for (int v : order) {
-    Shape& sh = shp[v];
-    if (small[v] || sh.g.kernel != KG_TC) continue;
-    for (int c : {sh.A, sh.B}) {
-      if (t.nodes[c].left < 0) continue;
-      fmt[c] = c == sh.A ? 1 : 2;
-      fkbits[c] = sh.nk;
-    }
-    sh.g.a_split = fmt[sh.A] != 0 ? 1 : 0;
-    sh.g.b_split = fmt[sh.B] != 0 ? 1 : 0;
-  }
-  auto out_bytes = [&](int v) -> uint64_t {
-    const uint64_t E = nsize(v);
-    return fmt[v] == 0 ? 8 * E : fmt[v] == 1 ? 4 * E * es : 8 * E * es;
-  };
-  auto out_plane = [&](int v) -> uint64_t { return fmt[v] == 1 ? 2 * nsize(v) : 4 * nsize(v); };
-
   for (int L = 1; L <= max_lvl; ++L) {
     std::vector<int> members;
     for (int v : order)
@@ -607,13 +573,9 @@ int compile_program(Plan& p) {
       const Shape& sh = shp[v];
       for (int c : {sh.A, sh.B})
         if (!placed[c]) place_leaf(c);
-      uint64_t coff = arena.alloc(out_bytes(v));
+      uint64_t coff = arena.alloc(nsize(v) * 8);
       GroupedDesc gd;
       std::memset(&gd, 0, sizeof(gd));
-      gd.c_fmt = fmt[v];
-      gd.c_kbits = fkbits[v];
-      gd.c_tf32 = tf32;
-      gd.c_plane = fmt[v] ? out_plane(v) : 0;
       gd.a = loc[sh.A];
       gd.b = loc[sh.B];
       gd.a_buf = buf[sh.A];  // tag, fixed below
@@ -646,7 +608,7 @@ int compile_program(Plan& p) {
     const Shape& sh = shp[v];
     for (int c : {sh.A, sh.B})
       if (!placed[c]) place_leaf(c);
-    uint64_t coff = arena.alloc(out_bytes(v));
+    uint64_t coff = arena.alloc(nsize(v) * 8);
     Step s;
     std::memset(&s, 0, sizeof(s));
     s.kind = ST_GEMM;
@@ -658,10 +620,6 @@ int compile_program(Plan& p) {
     g.a_buf = buf[sh.A];
     g.b_buf = buf[sh.B];
     g.c = coff / 8;
-    g.c_fmt = fmt[v];
-    g.c_kbits = fkbits[v];
-    g.c_tf32 = tf32;
-    g.c_plane = fmt[v] ? out_plane(v) : 0;
     uint64_t scratch_bytes = 0;  // room for any candidate the autotuner may pick
     {
       GemmDesc cand[kMaxCandidates];

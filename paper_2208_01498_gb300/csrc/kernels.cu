@@ -179,7 +179,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       int64_t n = n0 + tx * TN + j;
-      if (n < N) om.store(C, roff + coff[j], acc[i][j]);
+      if (n < N) C[roff + coff[j]] = acc[i][j];
     }
   }
 }
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int k = 0; k < 16; ++k)
         if (k < K) acc = cmul_add(acc, a[k], Bs[k * N + n]);
-      om.store(C, roff + coff[n], acc);
+      C[roff + coff[n]] = acc;
     }
   }
 }
@@ -250,7 +250,6 @@ __global__ void __launch_bounds__(kGroupThreads)
   }
   OutMap om;
   om.ident = d.c_ident, om.nN = d.nN, om.nM = d.nM, om.nB = d.nB;
-  om.fmt = d.c_fmt, om.kbits = d.c_kbits, om.tf32 = d.c_tf32, om.plane = d.c_plane;
   for (int i = 0; i < kMaxRank; ++i) om.pos[i] = d.c_pos[i];
   if (threadIdx.x < N) coff[threadIdx.x] = om.col(threadIdx.x);
   __syncthreads();
@@ -266,7 +265,7 @@ __global__ void __launch_bounds__(kGroupThreads)
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk)
       if (kk < K) acc = cmul_add(acc, a[kk], Bs[kk * N + nn]);
-    om.store(C, roff + coff[nn], acc);
+    C[roff + coff[nn]] = acc;
   }
 }
 
@@ -339,7 +338,7 @@ __global__ void dot_finish_kernel(const double2* __restrict__ part, float2* __re
     double2 v = part[(bz * nblk + b) * MN + e];
     x += v.x, y += v.y;
   }
-  om.store(C, om.row(bz, e / N, M, N) + om.col(e % N), make_float2((float)x, (float)y));
+  C[om.row(bz, e / N, M, N) + om.col(e % N)] = make_float2((float)x, (float)y);
 }
 
 // ------------------------------------------------------------------ accum
@@ -381,7 +380,7 @@ __global__ void splitk_reduce_kernel(const float2* __restrict__ part, float2* __
       x += v.x, y += v.y;
     }
     const int64_t nn = i % N, bm = i / N;
-    om.store(C, om.row(bm / M, bm % M, M, N) + om.col(nn), make_float2((float)x, (float)y));
+    C[om.row(bm / M, bm % M, M, N) + om.col(nn)] = make_float2((float)x, (float)y);
   }
 }
 

@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // accumulation warps: row 32 (warp % 4) + lane of the tile
     const int quarter = warp & 3;
     const int et = threadIdx.x - 64;  // 0..127
-    if (et < BN / 2) coltab[et] = om.col(n0 / 2 + et);
+    if (!om.ident && et < BN / 2) coltab[et] = om.col(n0 / 2 + et);
     asm volatile("bar.sync 1, 128;" ::: "memory");  // the four accumulation warps only
     float acc[BN];
 #pragma unroll
@@ -315,16 +315,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (ok && !*(volatile int*)abort_flag) {
       const int row = m0 + quarter * 32 + lane;
-      if (om.ident && om.fmt == 0) {
+      if (om.ident) {
         float4* dst = (float4*)(C + ((int64_t)bz * M + row) * N2 + n0);
 #pragma unroll
         for (int i = 0; i < BN / 4; ++i)
           dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
       } else {
         // complex column n0/2 + i of row `row`, placed in the consumer's layout
+        float2* C2 = (float2*)C;
         const uint64_t roff = om.row(bz, row, M, N2 / 2);
 #pragma unroll
-        for (int i = 0; i < BN / 2; ++i) om.store(C, roff + coltab[i], make_float2(acc[2 * i], acc[2 * i + 1]));
+        for (int i = 0; i < BN / 2; ++i) C2[roff + coltab[i]] = make_float2(acc[2 * i], acc[2 * i + 1]);
       }
     }
   }
@@ -436,19 +437,8 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
   uint8_t* b_lo = b_hi + nb * N2 * K2 * es;
   const int64_t na = nb * M * d.K, nbb = nb * d.N * d.K;
   auto blocks = [](int64_t n) { return (unsigned)(n / 256 + 1 < 152 * 32 ? n / 256 + 1 : 152 * 32); };
-  // operands a producer already wrote as hi/lo planes are used in place
-  if (d.a_split) {
-    a_hi = (uint8_t*)A;
-    a_lo = a_hi + nb * M * K2 * es;
-  } else {
-    prep_a_kernel<kTF32><<<blocks(na), 256, 0, st>>>(A, a_hi, a_lo, M, d.K, na, d.transA);
-  }
-  if (d.b_split) {
-    b_hi = (uint8_t*)B;
-    b_lo = b_hi + nb * N2 * K2 * es;
-  } else {
-    prep_b_kernel<kTF32><<<blocks(nbb), 256, 0, st>>>(B, b_hi, b_lo, d.N, d.K, nbb, d.transB);
-  }
+  prep_a_kernel<kTF32><<<blocks(na), 256, 0, st>>>(A, a_hi, a_lo, M, d.K, na, d.transA);
+  prep_b_kernel<kTF32><<<blocks(nbb), 256, 0, st>>>(B, b_hi, b_lo, d.N, d.K, nbb, d.transB);
   CUtensorMap mAh, mAl, mBh, mBl;
   int r;
   if ((r = make_map(&mAh, a_hi, kTF32, K2, M, nb, BM))) return r;

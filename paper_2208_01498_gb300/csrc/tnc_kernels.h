@@ -62,14 +62,6 @@ struct GemmDesc {
   int nN, nM, nB;
   int8_t c_pos[kMaxRank];
   int tile;              // tensor-core tile width: 0 auto, 1 N = 64 real columns, 2 N = 128
-  // Output format (the consumer's operand form): 0 complex64; 1 hi/lo planes
-  // of A' = [b][M'][2K'] (re, im interleaved); 2 hi/lo planes of B'^T =
-  // [b][2N'][2K'] (rows (re, -im) and (im, re)); c_kbits = log2 K' of the
-  // consumer; c_tf32: planes hold tf32 (else bf16); c_plane: values per plane.
-  int c_fmt, c_kbits, c_tf32;
-  uint64_t c_plane;
-  // tensor-core nodes: operand already stored as hi/lo planes by its producer
-  int a_split, b_split;
 };
 
 // One problem of a grouped launch of narrow nodes (N, K <= 16): the same
@@ -84,8 +76,6 @@ struct GroupedDesc {
   int blocks_per_batch;
   int8_t c_pos[kMaxRank];
   int64_t first_block;
-  int c_fmt, c_kbits, c_tf32;
-  uint64_t c_plane;
 };
 
 // Final accumulation: out[beta][j] += sum over the bits of the grouped

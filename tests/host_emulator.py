@@ -105,7 +105,6 @@ def emulate_program(e: dict, bits: np.ndarray, groups=None) -> np.ndarray:
             for pos, k in zip(gd["sliced_pos"], gd["sliced_bit"]):
                 src |= ((g >> k) & 1) << pos
             ws[gd["dst"] + o] = base[gd["src"] + src]
-        planes = {}  # outputs stored as tensor-core operand planes: offset -> complex values
         flat = []
         for st in e["steps"]:
             flat += st["problems"] if st["kind"] == 2 else [st]
@@ -121,28 +120,14 @@ def emulate_program(e: dict, bits: np.ndarray, groups=None) -> np.ndarray:
                 Bn, M, N, K = st["batch"], st["M"], st["N"], st["K"]
                 Ab = base if st["a_buf"] else ws
                 Bb = base if st["b_buf"] else ws
-                if st.get("a_split"):
-                    A = planes[st["a"]].astype(np.complex128)
-                else:
-                    A = Ab[st["a"]: st["a"] + Bn * M * K].astype(np.complex128)
+                A = Ab[st["a"]: st["a"] + Bn * M * K].astype(np.complex128)
                 A = A.reshape(Bn, K, M).transpose(0, 2, 1) if st["tA"] else A.reshape(Bn, M, K)
-                if st.get("b_split"):
-                    Bm = planes[st["b"]].astype(np.complex128)
-                else:
-                    Bm = Bb[st["b"]: st["b"] + Bn * K * N].astype(np.complex128)
+                Bm = Bb[st["b"]: st["b"] + Bn * K * N].astype(np.complex128)
                 Bm = Bm.reshape(Bn, N, K).transpose(0, 2, 1) if st["tB"] else Bm.reshape(Bn, K, N)
                 assert np.isfinite(A).all() and np.isfinite(Bm).all(), "read of an unwritten workspace slot"
                 Cv = (A @ Bm).astype(np.complex64).reshape(-1)
-                if st.get("c_fmt", 0):
-                    # logical values in the consumer's layout (planes are opaque here)
-                    logical = np.empty(Bn * M * N, np.complex64)
-                    target = logical
-                    cbase = 0
-                else:
-                    target = ws
-                    cbase = st["c"]
                 if st.get("c_ident", 1):
-                    target[cbase: cbase + Bn * M * N] = Cv
+                    ws[st["c"]: st["c"] + Bn * M * N] = Cv
                 else:
                     # element (b, m, n) at the bit positions c_pos: n bits, m bits, batch bits
                     idx = np.arange(Bn * M * N, dtype=np.int64)
@@ -156,9 +141,7 @@ def emulate_program(e: dict, bits: np.ndarray, groups=None) -> np.ndarray:
                         off |= ((m_ >> i) & 1) << pos[nN + i]
                     for i in range(len(pos) - nN - nM):
                         off |= ((b_ >> i) & 1) << pos[nN + nM + i]
-                    target[cbase + off] = Cv
-                if st.get("c_fmt", 0):
-                    planes[st["c"]] = logical
+                    ws[st["c"] + off] = Cv
         rank = len(acc["role"])
         root = ws[acc["src"]: acc["src"] + (1 << rank)].astype(np.complex128)
         for beta in range(batch):
