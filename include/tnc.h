@@ -218,6 +218,15 @@ int tnc_device_error(int* flag);
  * NULL) receives the number of steps whose kernel changed. */
 int tnc_plan_autotune(tnc_plan_t* plan, void* d_ws, size_t ws_bytes, void* cuda_stream, int reps, int* n_changed);
 
+/* Kernel choice of every step (for saving and restoring autotuner results):
+ * choices[2 i] = kernel variant, choices[2 i + 1] = tensor-core tile width
+ * of step i (grouped and permute steps report -1).  get: cap >= 2 * n_steps,
+ * *n_steps receives the step count.  set: exactly the array get returns for
+ * the same plan; TNC_EINVAL if a choice cannot run its step.  Setting drops
+ * captured graphs. */
+int tnc_plan_get_kernels(const tnc_plan_t* plan, int* choices, int cap, int* n_steps);
+int tnc_plan_set_kernels(tnc_plan_t* plan, const int* choices, int n_steps);
+
 /* Amplitudes for `batch` bitstrings (1 <= batch <= max_batch).
  * bits: HOST uint8 [batch][n_qubits]; entries of open qubits are ignored.
  * d_out: DEVICE complex128 [batch][2^n_open], caller-owned, overwritten.

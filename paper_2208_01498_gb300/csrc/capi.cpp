@@ -754,6 +754,66 @@ int tnc_plan_autotune(tnc_plan_t* plan, void* d_ws, size_t ws_bytes, void* strea
   return TNC_OK;
 }
 
+int tnc_plan_get_kernels(const tnc_plan_t* plan, int* choices, int cap, int* n_steps) {
+  if (!plan || !n_steps) {
+    set_error("tnc_plan_get_kernels: NULL argument");
+    return TNC_EINVAL;
+  }
+  const Plan& p = plan->p;
+  const int n = (int)p.prog.steps.size();
+  *n_steps = n;
+  if (!choices) return TNC_OK;
+  if (cap < 2 * n) {
+    set_error("tnc_plan_get_kernels: cap %d < %d", cap, 2 * n);
+    return TNC_EINVAL;
+  }
+  for (int i = 0; i < n; ++i) {
+    const Step& s = p.prog.steps[i];
+    choices[2 * i] = s.kind == ST_GEMM ? s.gemm.kernel : -1;
+    choices[2 * i + 1] = s.kind == ST_GEMM ? s.gemm.tile : -1;
+  }
+  return TNC_OK;
+}
+
+int tnc_plan_set_kernels(tnc_plan_t* plan, const int* choices, int n_steps) {
+  if (!plan || !choices) {
+    set_error("tnc_plan_set_kernels: NULL argument");
+    return TNC_EINVAL;
+  }
+  Plan& p = plan->p;
+  if (n_steps != (int)p.prog.steps.size()) {
+    set_error("tnc_plan_set_kernels: %d choices for %zu steps", n_steps, p.prog.steps.size());
+    return TNC_EINVAL;
+  }
+  std::vector<GemmDesc> chosen(n_steps);
+  for (int i = 0; i < n_steps; ++i) {
+    const Step& s = p.prog.steps[i];
+    if (s.kind != ST_GEMM) continue;
+    GemmDesc cand[kMaxCandidates];
+    int nc = 0, hit = -1;
+    gemm_candidates(s.gemm, cand, &nc);
+    for (int q = 0; q < nc; ++q)
+      if (cand[q].kernel == choices[2 * i] && cand[q].tile == choices[2 * i + 1]) hit = q;
+    if (hit < 0) {
+      set_error("tnc_plan_set_kernels: step %d cannot run kernel %d tile %d", i, choices[2 * i], choices[2 * i + 1]);
+      return TNC_EINVAL;
+    }
+    chosen[i] = cand[hit];
+    chosen[i].scratch = s.gemm.scratch;
+    chosen[i].scratch_elems = s.gemm.scratch_elems;
+    if (gemm_scratch_bytes(chosen[i]) > chosen[i].scratch_elems * 8) {
+      set_error("tnc_plan_set_kernels: step %d: scratch too small for kernel %d", i, choices[2 * i]);
+      return TNC_EINVAL;
+    }
+  }
+  for (int i = 0; i < n_steps; ++i)
+    if (p.prog.steps[i].kind == ST_GEMM) p.prog.steps[i].gemm = chosen[i];
+  for (auto& ge : p.graphs) cudaGraphExecDestroy((cudaGraphExec_t)ge.exec);
+  p.graphs.clear();
+  p.rep.n_launches = launches_per_group(p) * p.rep.n_slice_groups;
+  return TNC_OK;
+}
+
 int tnc_device_error(int* flag) {
   if (!flag) {
     set_error("tnc_device_error: NULL argument");

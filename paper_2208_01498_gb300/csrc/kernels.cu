@@ -100,14 +100,15 @@ __global__ void __launch_bounds__(kPermThreads) permute_kernel(const float2* __r
 
 // ------------------------------------------------------------------ SIMT GEMM
 template <int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+__global__ void __launch_bounds__((BM / TM) * (BN / TN), (BM * BN >= 8192) ? 1 : 2)
     cgemm_simt_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
                       int64_t M, int64_t N, int64_t K, int transA, int transB, int64_t b0, int64_t kchunk,
                       int64_t part_stride, const __grid_constant__ OutMap om) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
-  __shared__ __align__(16) float2 As[BK][BM];
-  __shared__ __align__(16) float2 Bs[BK][BN];
+  // rows padded by 16 bytes: the transposing tile stores spread over banks
+  __shared__ __align__(16) float2 As[BK][BM + 2];
+  __shared__ __align__(16) float2 Bs[BK][BN + 2];
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   const int64_t bz = b0 + blockIdx.z;

@@ -65,7 +65,8 @@ EXPORTED = [
     "tnc_server_submit", "tnc_server_poll", "tnc_server_wait", "tnc_server_cancel",
     "tnc_server_destroy", "tnc_plan_set_profiling", "tnc_plan_get_profile", "tnc_device_error",
     "tnc_contract_amplitudes_static", "tnc_permute", "tnc_cgemm_scratch_bytes", "tnc_cgemm",
-    "tnc_ssa_separate", "tnc_centerpoint", "tnc_plan_autotune",
+    "tnc_ssa_separate", "tnc_centerpoint", "tnc_plan_autotune", "tnc_plan_get_kernels",
+    "tnc_plan_set_kernels",
 ]
 
 
@@ -102,6 +103,8 @@ def _load():
                                  C.POINTER(i), C.POINTER(i)]),
         "tnc_centerpoint": (i, [C.POINTER(C.c_double), i, i, u64, C.POINTER(C.c_double)]),
         "tnc_plan_autotune": (i, [vp, vp, sz, vp, i, C.POINTER(i)]),
+        "tnc_plan_get_kernels": (i, [vp, C.POINTER(i), i, C.POINTER(i)]),
+        "tnc_plan_set_kernels": (i, [vp, C.POINTER(i), i]),
         "tnc_cgemm_scratch_bytes": (sz, [C.c_int64] * 4 + [i]),
         "tnc_cgemm": (i, [vp, vp, vp] + [C.c_int64] * 4 + [i, i, i, vp, sz, vp]),
         "tnc_plan_get_profile": (i, [vp, C.POINTER(i), i, C.POINTER(C.c_double), C.POINTER(i),
@@ -221,6 +224,21 @@ class Plan:
         _check(lib.tnc_plan_get_report(self.handle, C.byref(rep)), "tnc_plan_get_report")
         self.report = rep.as_dict()
         return n.value
+
+    def get_kernels(self):
+        """Kernel choice per step ([kernel, tile] pairs; -1 for non-GEMM steps)."""
+        n = C.c_int()
+        _check(lib.tnc_plan_get_kernels(self.handle, None, 0, C.byref(n)), "tnc_plan_get_kernels")
+        arr = np.zeros(2 * n.value, np.int32)
+        _check(lib.tnc_plan_get_kernels(self.handle, _ptr(arr, C.c_int), arr.size, C.byref(n)), "tnc_plan_get_kernels")
+        return arr.reshape(-1, 2).tolist()
+
+    def set_kernels(self, choices):
+        arr = np.ascontiguousarray(np.asarray(choices, np.int32).reshape(-1))
+        _check(lib.tnc_plan_set_kernels(self.handle, _ptr(arr, C.c_int), arr.size // 2), "tnc_plan_set_kernels")
+        rep = PlanReport()
+        _check(lib.tnc_plan_get_report(self.handle, C.byref(rep)), "tnc_plan_get_report")
+        self.report = rep.as_dict()
 
     def set_profiling(self, enable: bool):
         _check(lib.tnc_plan_set_profiling(self.handle, int(bool(enable))), "tnc_plan_set_profiling")
