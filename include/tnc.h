@@ -189,7 +189,8 @@ int tnc_plan_get_profile(tnc_plan_t* plan, int* n_steps, int cap, double* ms, in
  * not overlap.  TNC_EINVAL for a bad permutation. */
 int tnc_permute(const void* d_in, void* d_out, int rank, const int* src_bit, void* cuda_stream);
 
-/* Scratch bytes tnc_cgemm needs for this shape and form (0 if none). */
+/* Scratch bytes tnc_cgemm (and tnc_cgemm_variant, any variant) needs for
+ * this shape and form (0 if none). */
 size_t tnc_cgemm_scratch_bytes(int64_t batch, int64_t M, int64_t N, int64_t K, int form);
 
 /* tnc_cgemm: one pairwise contraction (Eq. 3: M_paper = batch*M*N*K
@@ -202,6 +203,21 @@ size_t tnc_cgemm_scratch_bytes(int64_t batch, int64_t M, int64_t N, int64_t K, i
  * tnc_cgemm_scratch_bytes(), 256-byte aligned (may be NULL if that is 0). */
 int tnc_cgemm(const void* d_A, const void* d_B, void* d_C, int64_t batch, int64_t M, int64_t N, int64_t K,
               int transA, int transB, int form, void* d_scratch, size_t scratch_bytes, void* cuda_stream);
+
+/* tnc_cgemm with the kernel variant named: kernel = TNC_KG_* below (-1: by
+ * shape, as tnc_cgemm), tile = tensor-core tile width (1: 128 x 64 real
+ * outputs per CTA, 2: 128 x 128, 3: 128 x 256; -1: any; 0 for the other
+ * kernels).  The variants are those a plan's autotuner may pick for the
+ * shape; TNC_EINVAL for one that cannot run it. */
+#define TNC_KG_SIMT_128x64 0
+#define TNC_KG_SIMT_64x32 1
+#define TNC_KG_NARROW 2
+#define TNC_KG_DOT 3
+#define TNC_KG_TC 4
+#define TNC_KG_SIMT_32x128 5
+int tnc_cgemm_variant(const void* d_A, const void* d_B, void* d_C, int64_t batch, int64_t M, int64_t N, int64_t K,
+                      int transA, int transB, int form, int kernel, int tile, void* d_scratch, size_t scratch_bytes,
+                      void* cuda_stream);
 
 /* Device-side error flag of the kernels with bounded waits (the tcgen05
  * pipeline): 0 if no wait has timed out on the current device since load,

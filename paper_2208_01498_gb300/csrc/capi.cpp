@@ -646,17 +646,36 @@ static GemmDesc make_gemm(int64_t batch, int64_t M, int64_t N, int64_t K, int tA
 
 size_t tnc_cgemm_scratch_bytes(int64_t batch, int64_t M, int64_t N, int64_t K, int form) {
   if (batch < 1 || M < 1 || N < 1 || K < 1 || form < 0 || form > 2) return 0;
-  return (size_t)gemm_scratch_bytes(make_gemm(batch, M, N, K, 0, 0, form));
+  // enough for every variant tnc_cgemm_variant accepts for this shape
+  GemmDesc cand[kMaxCandidates];
+  int n = 0;
+  gemm_candidates(make_gemm(batch, M, N, K, 0, 0, form), cand, &n);
+  uint64_t need = 0;
+  for (int i = 0; i < n; ++i) need = std::max<uint64_t>(need, gemm_scratch_bytes(cand[i]));
+  return (size_t)need;
 }
 
-int tnc_cgemm(const void* A, const void* B, void* Cp, int64_t batch, int64_t M, int64_t N, int64_t K, int tA,
-              int tB, int form, void* scratch, size_t scratch_bytes, void* stream) {
+int tnc_cgemm_variant(const void* A, const void* B, void* Cp, int64_t batch, int64_t M, int64_t N, int64_t K,
+                      int tA, int tB, int form, int kernel, int tile, void* scratch, size_t scratch_bytes,
+                      void* stream) {
   if (!A || !B || !Cp || batch < 1 || M < 1 || N < 1 || K < 1 || form < 0 || form > 2 || (tA & ~1) ||
       (tB & ~1)) {
     set_error("tnc_cgemm: invalid argument");
     return TNC_EINVAL;
   }
   GemmDesc g = make_gemm(batch, M, N, K, tA, tB, form);
+  if (kernel >= 0) {
+    GemmDesc cand[kMaxCandidates];
+    int n = 0, hit = -1;
+    gemm_candidates(g, cand, &n);
+    for (int i = 0; i < n && hit < 0; ++i)
+      if (cand[i].kernel == kernel && (tile < 0 || cand[i].tile == tile)) hit = i;
+    if (hit < 0) {
+      set_error("tnc_cgemm_variant: kernel %d tile %d cannot run this shape", kernel, tile);
+      return TNC_EINVAL;
+    }
+    g = cand[hit];
+  }
   const uint64_t need = gemm_scratch_bytes(g);
   if (need > scratch_bytes || (need && !scratch)) {
     set_error("tnc_cgemm: scratch of %zu bytes < required %llu", scratch_bytes, (unsigned long long)need);
@@ -671,6 +690,11 @@ int tnc_cgemm(const void* A, const void* B, void* Cp, int64_t batch, int64_t M, 
   if (rc != TNC_OK) return rc;
   int r = launch_gemm_ptr(g, A, B, Cp, scratch, stream);
   return r ? cuda_fail((cudaError_t)r, "tnc_cgemm") : TNC_OK;
+}
+
+int tnc_cgemm(const void* A, const void* B, void* Cp, int64_t batch, int64_t M, int64_t N, int64_t K, int tA,
+              int tB, int form, void* scratch, size_t scratch_bytes, void* stream) {
+  return tnc_cgemm_variant(A, B, Cp, batch, M, N, K, tA, tB, form, -1, -1, scratch, scratch_bytes, stream);
 }
 
 int tnc_plan_autotune(tnc_plan_t* plan, void* d_ws, size_t ws_bytes, void* stream, int reps, int* n_changed) {

@@ -142,6 +142,8 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
   if (g0.form != TNC_FP32 && pow2 && g0.M >= 128 && g0.N >= 32 && g0.K >= 32) {
     add(KG_TC, 1);
     if (g0.N >= 64) add(KG_TC, 2);
+    if (g0.N >= 128) add(KG_TC, 3);
+    if (g0.form == TNC_SPLIT_BF16 && g0.N >= 64 && !g0.transA && g0.transB) add(KG_TC, 4);
   }
   *n = k;
 }

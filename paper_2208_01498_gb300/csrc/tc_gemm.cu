@@ -161,16 +161,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 // ------------------------------------------------------------ GEMM kernel
 // D[b][m][n'] = sum_k' A'[b][m][k'] B'^T[b][n'][k'], 3 products per k-step.
-// Warp 0: TMA producer; warp 1: MMA issuer; warps 2..5: accumulation and
-// epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31).  The K range is cut
+// Warp 0: TMA producer; warp 1: MMA issuer; the remaining warps: accumulation
+// and epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31; with BN = 256 two
+// warps share each lane quarter, one per half of the columns, so that a
+// thread keeps at most 128 FP32 partial sums in registers).  The K range is cut
 // into chunks of CHUNK k-blocks; chunk c accumulates in TMEM slot c % 2 and
 // the epilogue warps add each finished slot into FP32 registers while the
 // other slot fills, so no tensor-core accumulation chain is longer than one
 // chunk.
-constexpr int kTcThreads = 192;
+template <int BN>
+struct TcShape {
+  static constexpr int kEpiCols = BN > 128 ? 128 : BN;      // columns per accumulation thread
+  static constexpr int kEpiWarps = 4 * BN / kEpiCols;        // 4 or 8
+  static constexpr int kThreads = 64 + 32 * kEpiWarps;
+};
 
 template <bool kTF32, int BN, int STAGES>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
                    const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
                    float* __restrict__ C, int M, int N2, int K2, int b0, const __grid_constant__ OutMap om) {
@@ -208,7 +215,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&acc_full[s], 1);
-      mbar_init(&acc_empty[s], 128);
+      mbar_init(&acc_empty[s], 32 * TcShape<BN>::kEpiWarps);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -284,14 +291,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mma_commit(done);
     }
   } else {
-    // accumulation warps: row 32 (warp % 4) + lane of the tile
+    // accumulation warps: row 32 (warp % 4) + lane of the tile, columns
+    // [half * EC, half * EC + EC)
+    constexpr int EC = TcShape<BN>::kEpiCols;
     const int quarter = warp & 3;
-    const int et = threadIdx.x - 64;  // 0..127
+    const int half = (warp - 2) >> 2;
+    const int et = threadIdx.x - 64;
     if (!om.ident && et < BN / 2) coltab[et] = om.col(n0 / 2 + et);
-    asm volatile("bar.sync 1, 128;" ::: "memory");  // the four accumulation warps only
-    float acc[BN];
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * TcShape<BN>::kEpiWarps) : "memory");  // accumulation warps only
+    float acc[EC];
 #pragma unroll
-    for (int i = 0; i < BN; ++i) acc[i] = 0.f;
+    for (int i = 0; i < EC; ++i) acc[i] = 0.f;
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const int slot = c & 1;
@@ -302,9 +312,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         break;
       }
       tc_fence_after();
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + slot * BN;
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + slot * BN + half * EC;
 #pragma unroll
-      for (int col = 0; col < BN; col += 16) {
+      for (int col = 0; col < EC; col += 16) {
         float v[16];
         tmem_ld16(taddr + col, v);
 #pragma unroll
@@ -316,16 +326,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (ok && !*(volatile int*)abort_flag) {
       const int row = m0 + quarter * 32 + lane;
       if (om.ident) {
-        float4* dst = (float4*)(C + ((int64_t)bz * M + row) * N2 + n0);
+        float4* dst = (float4*)(C + ((int64_t)bz * M + row) * N2 + n0 + half * EC);
 #pragma unroll
-        for (int i = 0; i < BN / 4; ++i)
+        for (int i = 0; i < EC / 4; ++i)
           dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
       } else {
         // complex column n0/2 + i of row `row`, placed in the consumer's layout
         float2* C2 = (float2*)C;
         const uint64_t roff = om.row(bz, row, M, N2 / 2);
+        const uint64_t* ct = coltab + half * (EC / 2);
 #pragma unroll
-        for (int i = 0; i < BN / 2; ++i) C2[roff + coltab[i]] = make_float2(acc[2 * i], acc[2 * i + 1]);
+        for (int i = 0; i < EC / 2; ++i) C2[roff + ct[i]] = make_float2(acc[2 * i], acc[2 * i + 1]);
       }
     }
   }
@@ -343,6 +354,303 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     tmem_dealloc(tmem, 2 * BN);
   }
+}
+
+// ------------------------------------------------------------ fused split-BF16 kernel
+// The same 4M product, but without hi/lo planes in global memory: converter
+// warps read the complex64 operands (A [b][M][K], B [b][N][K]) straight from
+// global memory, split each value into bf16 hi + lo in registers and store
+// the A' and B'^T tiles into shared memory in the 128-byte-swizzled layout
+// the MMA descriptors read (16-byte chunk c of tile row r at
+// r * 128 + ((c ^ (r % 8)) * 16) within each 1024-byte group of 8 rows).
+// Each operand byte then crosses HBM once instead of three times (read,
+// planes written, planes read back).
+//
+// Warps 0..3: accumulation and epilogue (TMEM lane quarter = warp); warp 4:
+// TMEM allocation and the MMA issuer (one lane); warps 5..12: converters.
+// Finished accumulation chunks are added into a third TMEM region (the
+// running sum) instead of registers, so no thread holds a whole row.
+// Every wait is bounded as in tc_gemm_kernel; no asynchronous copies are in
+// flight at teardown (the converters' stores are synchronous).
+constexpr int kFzBN = 128;            // real output columns per CTA (64 complex)
+constexpr int kFzStages = 3;
+constexpr int kFzConvWarps = 8;
+constexpr int kFzThreads = 32 * (5 + kFzConvWarps);
+constexpr uint32_t kFzTileBytes = BM * 128;                    // one plane tile: 128 rows x 64 bf16
+constexpr uint32_t kFzStageBytes = 4 * kFzTileBytes;            // A hi, A lo, B' hi, B' lo
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t swz128(int row, int chunk) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+// bf16 hi/lo words of 8 consecutive reals: word j packs elements 2j (low
+// half) and 2j + 1 (high half)
+__device__ __forceinline__ void split_words(const float4& p, const float4& q, uint32_t* h, uint32_t* l) {
+  const float x[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+    const float2 hf = __bfloat1622float2(hb);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * j] - hf.x, x[2 * j + 1] - hf.y);
+    h[j] = *(const uint32_t*)&hb;
+    l[j] = *(const uint32_t*)&lb;
+  }
+}
+
+__device__ __forceinline__ void sts128(uint32_t addr, const uint32_t* w) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kFzThreads, 1)
+    tc_fused_bf16_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float* __restrict__ C, int M,
+                         int N2, int K, int b0, const __grid_constant__ OutMap om) {
+  constexpr int CHUNK = 512 / 64;  // k-blocks (64 k') per accumulation chunk
+  constexpr uint32_t IDESC = instr_desc<false, kFzBN>();
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + kFzStages * kFzStageBytes);
+  uint64_t* empty = full + kFzStages;
+  uint64_t* acc_full = empty + kFzStages;  // [2]
+  uint64_t* acc_empty = acc_full + 2;      // [2]
+  uint64_t* done = acc_empty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  int* abort_flag = (int*)(tmem_slot + 1);
+  uint64_t* coltab = (uint64_t*)(tmem_slot + 4);  // [kFzBN / 2]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_m = M / BM;
+  const int m0 = (blockIdx.x % tiles_m) * BM;
+  const int n0 = (blockIdx.x / tiles_m) * kFzBN;  // real column
+  const int bz = b0 + blockIdx.z;
+  const int N = N2 / 2;
+  const int nk = K / 32;  // k-blocks: 32 complex k = 64 k'
+  const int nchunks = (nk + CHUNK - 1) / CHUNK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kFzStages; ++s) {
+      mbar_init(&full[s], 32 * kFzConvWarps);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&acc_full[s], 1);
+      mbar_init(&acc_empty[s], 128);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < kFzBN / 2 && !om.ident) coltab[threadIdx.x] = om.col(n0 / 2 + threadIdx.x);
+  if (warp == 4) tmem_alloc(tmem_slot, 512);  // slot 0, slot 1, running sum (128 columns each)
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp >= 5) {
+    // converters: thread ct handles tile rows ct/8 + 32 i (A, i < 4) and
+    // complex columns ct/8 + 32 i (B, i < 2), 16-byte chunk ct % 8 of each
+    const int ct = threadIdx.x - 160;
+    const int cr = ct >> 3, cc = ct & 7;
+    const float4* pa[4];
+    const float4* pb[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      pa[i] = (const float4*)(A + ((int64_t)bz * M + m0 + cr + 32 * i) * K + 4 * cc);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      pb[i] = (const float4*)(B + ((int64_t)bz * N + n0 / 2 + cr + 32 * i) * K + 4 * cc);
+    float4 ra[4][2], rb[2][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      ra[i][0] = __ldg(pa[i]);
+      ra[i][1] = __ldg(pa[i] + 1);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      rb[i][0] = __ldg(pb[i]);
+      rb[i][1] = __ldg(pb[i] + 1);
+    }
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kFzStages;
+      if (kb >= kFzStages && !mbar_wait(&empty[s], ((kb / kFzStages) + 1) & 1)) {
+        atomicExch(&tc_error_flag, 6);
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)abort_flag) break;
+      const uint32_t st = smem_u32(smem + s * kFzStageBytes);
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        split_words(ra[i][0], ra[i][1], h, l);
+        const uint32_t o = swz128(cr + 32 * i, cc);
+        sts128(st + o, h);
+        sts128(st + kFzTileBytes + o, l);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        // words (br, bi) -> row 2n: (br, -bi), row 2n + 1: (bi, br)
+        split_words(rb[i][0], rb[i][1], h, l);
+        uint32_t h0[4], l0[4], h1[4], l1[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          h0[j] = h[j] ^ 0x80000000u;
+          l0[j] = l[j] ^ 0x80000000u;
+          h1[j] = __byte_perm(h[j], 0, 0x1032);
+          l1[j] = __byte_perm(l[j], 0, 0x1032);
+        }
+        const int r0 = 2 * (cr + 32 * i);
+        sts128(st + 2 * kFzTileBytes + swz128(r0, cc), h0);
+        sts128(st + 3 * kFzTileBytes + swz128(r0, cc), l0);
+        sts128(st + 2 * kFzTileBytes + swz128(r0 + 1, cc), h1);
+        sts128(st + 3 * kFzTileBytes + swz128(r0 + 1, cc), l1);
+      }
+      // make the generic-proxy stores visible to the tensor core, then signal
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[s])) : "memory");
+      if (kb + 1 < nk) {
+        const int adv = (kb + 1) * 16;  // float4 per k-block
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          ra[i][0] = __ldg(pa[i] + adv);
+          ra[i][1] = __ldg(pa[i] + adv + 1);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          rb[i][0] = __ldg(pb[i] + adv);
+          rb[i][1] = __ldg(pb[i] + adv + 1);
+        }
+      }
+    }
+  } else if (warp == 4) {
+    if (lane == 0) {
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int slot = c & 1;
+        if (c >= 2 && !mbar_wait(&acc_empty[slot], ((c >> 1) + 1) & 1)) {
+          atomicExch(&tc_error_flag, 4);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        const uint32_t dtm = tmem + slot * kFzBN;
+        const int kb_end = (c + 1) * CHUNK < nk ? (c + 1) * CHUNK : nk;
+        for (int kb = c * CHUNK; kb < kb_end; ++kb) {
+          const int s = kb % kFzStages;
+          if (!mbar_wait(&full[s], (kb / kFzStages) & 1)) {
+            atomicExch(&tc_error_flag, 2);
+            *(volatile int*)abort_flag = 1;
+            ok = false;
+            break;
+          }
+          if (*(volatile int*)abort_flag) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * kFzStageBytes);
+          const uint64_t dAh = sw128_desc(sa), dAl = sw128_desc(sa + kFzTileBytes);
+          const uint64_t dBh = sw128_desc(sa + 2 * kFzTileBytes), dBl = sw128_desc(sa + 3 * kFzTileBytes);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t adv = (uint64_t)((kk * 16 * 2) >> 4);
+            const uint32_t first = (kb == c * CHUNK && kk == 0) ? 0u : 1u;
+            mma<false>(dtm, dAh + adv, dBh + adv, IDESC, first);
+            mma<false>(dtm, dAh + adv, dBl + adv, IDESC, 1u);
+            mma<false>(dtm, dAl + adv, dBh + adv, IDESC, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&acc_full[slot]);
+      }
+      mma_commit(done);
+    }
+  } else {
+    // accumulation: row 32 warp + lane of the tile
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t tsum = tmem + lane_base + 2 * kFzBN;
+    const int row = m0 + warp * 32 + lane;
+    const uint64_t roff = om.ident ? 0 : om.row(bz, row, M, N);
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int slot = c & 1;
+      if (!mbar_wait(&acc_full[slot], (c >> 1) & 1)) {
+        atomicExch(&tc_error_flag, 3);
+        *(volatile int*)abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const bool last = c == nchunks - 1;
+      const uint32_t tslot = tmem + lane_base + slot * kFzBN;
+      const bool write_out = last && !*(volatile int*)abort_flag;
+#pragma unroll 1
+      for (int col = 0; col < kFzBN; col += 16) {
+        float v[16];
+        tmem_ld16(tslot + col, v);
+        if (c > 0) {
+          float w[16];
+          tmem_ld16(tsum + col, w);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += w[i];
+        }
+        if (!last) {
+          tmem_st16(tsum + col, v);
+        } else if (write_out) {
+          if (om.ident) {
+            float4* dst = (float4*)(C + ((int64_t)bz * M + row) * N2 + n0 + col);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          } else {
+            float2* C2 = (float2*)C;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) C2[roff + coltab[col / 2 + i]] = make_float2(v[2 * i], v[2 * i + 1]);
+          }
+        }
+      }
+      if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      tc_fence_before();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[slot])) : "memory");
+    }
+    (void)ok;
+  }
+  if (threadIdx.x == 0 && !mbar_wait(done, 0)) atomicExch(&tc_error_flag, 5);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 4) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+int run_tc_fused(const GemmDesc& d, const float2* A, const float2* B, float* C, cudaStream_t st) {
+  const int64_t M = d.M, N2 = 2 * d.N, nb = d.batch;
+  const size_t smem = 1024 + kFzStages * kFzStageBytes + (2 * kFzStages + 5) * 8 + 16 + kFzBN / 2 * 8;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tc_fused_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    attr_set = true;
+  }
+  const int64_t tiles = (M / BM) * (N2 / kFzBN);
+  for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
+    int64_t cnt = nb - b0 < 65535 ? nb - b0 : 65535;
+    dim3 grid((unsigned)tiles, 1, (unsigned)cnt);
+    tc_fused_bf16_kernel<<<grid, kFzThreads, smem, st>>>(A, B, C, (int)M, (int)N2, (int)d.K, (int)b0, out_map(d));
+  }
+  return (int)cudaGetLastError();
 }
 
 // ------------------------------------------------------------ prep kernels
@@ -395,6 +703,82 @@ __global__ void prep_b_kernel(const float2* __restrict__ B, void* hi, void* lo, 
   }
 }
 
+// Vectorised forms for the K-major operands every compiled program passes
+// (A as [b][M][K], B as [b][N][K]).  A thread splits 4 consecutive complex
+// values (two 16-byte loads) and writes 8 consecutive elements of each plane
+// row it touches (16-byte stores for bf16, 32 bytes for tf32).
+template <bool kTF32>
+__device__ __forceinline__ void store8(void* plane, int64_t off, const float* v) {
+  if constexpr (kTF32) {
+    uint4* p = (uint4*)((uint32_t*)plane + off);
+    p[0] = make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3]));
+    p[1] = make_uint4(__float_as_uint(v[4]), __float_as_uint(v[5]), __float_as_uint(v[6]), __float_as_uint(v[7]));
+  } else {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      w[j] = *(uint32_t*)&h2;
+    }
+    *(uint4*)((__nv_bfloat16*)plane + off) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// hi = x rounded to the plane format, lo = (x - hi) rounded (values already
+// representable in the format come out of store8's rounding unchanged)
+template <bool kTF32>
+__device__ __forceinline__ void split8(const float* x, float* hi, float* lo) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float h;
+    if constexpr (kTF32) {
+      uint32_t u;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x[j]));
+      h = __uint_as_float(u);
+      uint32_t l;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x[j] - h));
+      lo[j] = __uint_as_float(l);
+    } else {
+      h = __bfloat162float(__float2bfloat16_rn(x[j]));
+      lo[j] = x[j] - h;
+    }
+    hi[j] = h;
+  }
+}
+
+// A [b][M][K] complex is already A' [b][M][2K] real: a plain split
+template <bool kTF32>
+__global__ void prep_a_vec_kernel(const float4* __restrict__ A, void* hi, void* lo, int64_t n8) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n8; t += (int64_t)gridDim.x * blockDim.x) {
+    const float4 p = A[2 * t], q = A[2 * t + 1];
+    const float x[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
+    float h[8], l[8];
+    split8<kTF32>(x, h, l);
+    store8<kTF32>(hi, 8 * t, h);
+    store8<kTF32>(lo, 8 * t, l);
+  }
+}
+
+// B [b][N][K] complex -> B'^T [b][2N][2K]; log2k = log2(K)
+template <bool kTF32>
+__global__ void prep_b_vec_kernel(const float4* __restrict__ B, void* hi, void* lo, int64_t n4, int log2k) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n4; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = 4 * t;  // first complex element (b, n, k..k+3)
+    const int64_t bn = i >> log2k, k = i & ((1ll << log2k) - 1);
+    const int64_t r0 = (bn << (log2k + 2)) + 2 * k, r1 = r0 + (2ll << log2k);
+    const float4 p = B[2 * t], q = B[2 * t + 1];
+    const float x0[8] = {p.x, -p.y, p.z, -p.w, q.x, -q.y, q.z, -q.w};
+    const float x1[8] = {p.y, p.x, p.w, p.z, q.y, q.x, q.w, q.z};
+    float h[8], l[8];
+    split8<kTF32>(x0, h, l);
+    store8<kTF32>(hi, r0, h);
+    store8<kTF32>(lo, r0, l);
+    split8<kTF32>(x1, h, l);
+    store8<kTF32>(hi, r1, h);
+    store8<kTF32>(lo, r1, l);
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -437,8 +821,16 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
   uint8_t* b_lo = b_hi + nb * N2 * K2 * es;
   const int64_t na = nb * M * d.K, nbb = nb * d.N * d.K;
   auto blocks = [](int64_t n) { return (unsigned)(n / 256 + 1 < 152 * 32 ? n / 256 + 1 : 152 * 32); };
-  prep_a_kernel<kTF32><<<blocks(na), 256, 0, st>>>(A, a_hi, a_lo, M, d.K, na, d.transA);
-  prep_b_kernel<kTF32><<<blocks(nbb), 256, 0, st>>>(B, b_hi, b_lo, d.N, d.K, nbb, d.transB);
+  const bool kpow2 = (d.K & (d.K - 1)) == 0;
+  if (!d.transA && ((uintptr_t)A & 15) == 0)
+    prep_a_vec_kernel<kTF32><<<blocks(na / 4), 256, 0, st>>>((const float4*)A, a_hi, a_lo, na / 4);
+  else
+    prep_a_kernel<kTF32><<<blocks(na), 256, 0, st>>>(A, a_hi, a_lo, M, d.K, na, d.transA);
+  if (d.transB && kpow2 && ((uintptr_t)B & 15) == 0)
+    prep_b_vec_kernel<kTF32><<<blocks(nbb / 4), 256, 0, st>>>((const float4*)B, b_hi, b_lo, nbb / 4,
+                                                             __builtin_ctzll((unsigned long long)d.K));
+  else
+    prep_b_kernel<kTF32><<<blocks(nbb), 256, 0, st>>>(B, b_hi, b_lo, d.N, d.K, nbb, d.transB);
   CUtensorMap mAh, mAl, mBh, mBl;
   int r;
   if ((r = make_map(&mAh, a_hi, kTF32, K2, M, nb, BM))) return r;
@@ -458,7 +850,7 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
   for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
     int64_t cnt = nb - b0 < 65535 ? nb - b0 : 65535;
     dim3 grid((unsigned)tiles, 1, (unsigned)cnt);
-    tc_gemm_kernel<kTF32, BN, STAGES><<<grid, kTcThreads, smem, st>>>(mAh, mAl, mBh, mBl, C, (int)M, (int)N2,
+    tc_gemm_kernel<kTF32, BN, STAGES><<<grid, TcShape<BN>::kThreads, smem, st>>>(mAh, mAl, mBh, mBl, C, (int)M, (int)N2,
                                                                      (int)K2, (int)b0, out_map(d));
   }
   return (int)cudaGetLastError();
@@ -479,13 +871,23 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   if (need > d.scratch_elems * 8) return (int)cudaErrorInvalidValue;
   uint8_t* scratch = (uint8_t*)scratch_ptr;
   if (!scratch) return (int)cudaErrorInvalidValue;
-  const bool wide = d.tile == 2 || (d.tile == 0 && d.N >= 64);
-  if (wide && d.N < 64) return (int)cudaErrorInvalidValue;
+  // tile 1: 128 x 64 real outputs per CTA, 2: 128 x 128, 3: 128 x 256;
+  // 4: 128 x 128 with the split done on chip (split-BF16, K-major operands)
+  const int tile = d.tile ? d.tile : (d.N >= 64 ? 2 : 1);
+  if (tile < 1 || tile > 4 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
+      (tile == 4 && (d.N < 64 || tf32 || d.transA || !d.transB)))
+    return (int)cudaErrorInvalidValue;
+  if (tile == 4) {
+    if (((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0) return run_tc_fused(d, A, B, (float*)C, st);
+    return run_tc<false, 128, 3>(d, A, B, (float*)C, scratch, st);  // unaligned operands: through the planes
+  }
   if (tf32) {
-    if (wide) return run_tc<true, 128, 3>(d, A, B, (float*)C, scratch, st);
+    if (tile == 3) return run_tc<true, 256, 2>(d, A, B, (float*)C, scratch, st);
+    if (tile == 2) return run_tc<true, 128, 3>(d, A, B, (float*)C, scratch, st);
     return run_tc<true, 64, 4>(d, A, B, (float*)C, scratch, st);
   }
-  if (wide) return run_tc<false, 128, 3>(d, A, B, (float*)C, scratch, st);
+  if (tile == 3) return run_tc<false, 256, 2>(d, A, B, (float*)C, scratch, st);
+  if (tile == 2) return run_tc<false, 128, 3>(d, A, B, (float*)C, scratch, st);
   return run_tc<false, 64, 4>(d, A, B, (float*)C, scratch, st);
 }
 

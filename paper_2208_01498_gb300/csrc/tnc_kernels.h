@@ -61,7 +61,8 @@ struct GemmDesc {
   int c_ident;
   int nN, nM, nB;
   int8_t c_pos[kMaxRank];
-  int tile;              // tensor-core tile width: 0 auto, 1 N = 64 real columns, 2 N = 128
+  int tile;              // tensor-core tile width: 0 auto, 1 N = 64 real columns, 2 N = 128, 3 N = 256,
+                        // 4 N = 128 with the split-BF16 split on chip
 };
 
 // One problem of a grouped launch of narrow nodes (N, K <= 16): the same

@@ -3,6 +3,7 @@ GPU), for roofline checks and for profiler captures of a single kernel:
 
     python -m paper_2208_01498_gb300.kbench permute --rank 26
     python -m paper_2208_01498_gb300.kbench gemm --batch 256 --M 256 --N 256 --K 4096 --form split_bf16
+    python -m paper_2208_01498_gb300.kbench gemm ... --kernel tc --tile 3
 
 Prints one JSON line: the kernel's average time and its algorithmic GB/s
 (permute: 16 bytes per element) or useful TFLOP/s (8 flops per complex
@@ -44,6 +45,8 @@ def main():
     ap.add_argument("--tA", type=int, default=0)
     ap.add_argument("--tB", type=int, default=1)
     ap.add_argument("--form", default="split_bf16")
+    ap.add_argument("--kernel", default=None, help="variant name of tnc.KG (default: chosen by shape)")
+    ap.add_argument("--tile", type=int, default=None, help="tensor-core tile width 1, 2 or 3")
     ap.add_argument("--iters", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     a = ap.parse_args()
@@ -62,11 +65,12 @@ def main():
     f = tnc.FORMS[a.form]
     need = tnc.lib.tnc_cgemm_scratch_bytes(a.batch, a.M, a.N, a.K, f)
     scr = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
-    ms = _time(lambda: tnc.cgemm(A, B, a.batch, a.M, a.N, a.K, a.tA, a.tB, a.form, out=C, scratch=scr),
+    ms = _time(lambda: tnc.cgemm(A, B, a.batch, a.M, a.N, a.K, a.tA, a.tB, a.form, out=C, scratch=scr,
+                                   kernel=a.kernel, tile=a.tile),
                a.iters, a.warmup)
     flops = 8.0 * a.batch * a.M * a.N * a.K
     byts = 8.0 * a.batch * (a.M * a.K + a.K * a.N + a.M * a.N)
-    print(json.dumps({"kernel": "cgemm", "form": a.form, "batch": a.batch, "M": a.M, "N": a.N, "K": a.K,
+    print(json.dumps({"kernel": "cgemm", "variant": a.kernel, "tile": a.tile, "form": a.form, "batch": a.batch, "M": a.M, "N": a.N, "K": a.K,
                       "ms": ms, "useful_TFLOP/s": flops / (ms / 1e3) / 1e12, "GB/s": byts / (ms / 1e3) / 1e9}))
 
 

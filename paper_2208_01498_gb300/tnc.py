@@ -66,8 +66,11 @@ EXPORTED = [
     "tnc_server_destroy", "tnc_plan_set_profiling", "tnc_plan_get_profile", "tnc_device_error",
     "tnc_contract_amplitudes_static", "tnc_permute", "tnc_cgemm_scratch_bytes", "tnc_cgemm",
     "tnc_ssa_separate", "tnc_centerpoint", "tnc_plan_autotune", "tnc_plan_get_kernels",
-    "tnc_plan_set_kernels",
+    "tnc_plan_set_kernels", "tnc_cgemm_variant",
 ]
+
+# kernel variants of a contraction step (TNC_KG_* in tnc.h)
+KG = {"simt_128x64": 0, "simt_64x32": 1, "narrow": 2, "dot": 3, "tc": 4, "simt_32x128": 5}
 
 
 def _load():
@@ -107,6 +110,7 @@ def _load():
         "tnc_plan_set_kernels": (i, [vp, C.POINTER(i), i]),
         "tnc_cgemm_scratch_bytes": (sz, [C.c_int64] * 4 + [i]),
         "tnc_cgemm": (i, [vp, vp, vp] + [C.c_int64] * 4 + [i, i, i, vp, sz, vp]),
+        "tnc_cgemm_variant": (i, [vp, vp, vp] + [C.c_int64] * 4 + [i, i, i, i, i, vp, sz, vp]),
         "tnc_plan_get_profile": (i, [vp, C.POINTER(i), i, C.POINTER(C.c_double), C.POINTER(i),
                                      C.POINTER(i), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     }
@@ -355,8 +359,11 @@ def permute(x, src_bit, out=None, stream=None):
     return out
 
 
-def cgemm(A, B, batch, M, N, K, transA=0, transB=0, form="fp32", out=None, scratch=None, stream=None):
-    """``tnc_cgemm``: batched complex GEMM of one tree node on complex64 CUDA tensors."""
+def cgemm(A, B, batch, M, N, K, transA=0, transB=0, form="fp32", out=None, scratch=None, stream=None,
+          kernel=None, tile=None):
+    """``tnc_cgemm`` (``tnc_cgemm_variant`` when ``kernel`` is given, a name
+    of ``KG`` or its number): batched complex GEMM of one tree node on
+    complex64 CUDA tensors."""
     import torch
     f = FORMS[form] if isinstance(form, str) else int(form)
     need = lib.tnc_cgemm_scratch_bytes(batch, M, N, K, f)
@@ -364,10 +371,11 @@ def cgemm(A, B, batch, M, N, K, transA=0, transB=0, form="fp32", out=None, scrat
         out = torch.empty((batch, M, N), dtype=torch.complex64, device=A.device)
     if scratch is None and need:
         scratch = torch.empty(need, dtype=torch.uint8, device=A.device)
-    _check(lib.tnc_cgemm(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()), C.c_void_p(out.data_ptr()),
-                         batch, M, N, K, int(transA), int(transB), f,
-                         C.c_void_p(scratch.data_ptr() if scratch is not None else 0),
-                         scratch.numel() if scratch is not None else 0, _stream_ptr(stream)), "tnc_cgemm")
+    kg = -1 if kernel is None else (KG[kernel] if isinstance(kernel, str) else int(kernel))
+    _check(lib.tnc_cgemm_variant(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()), C.c_void_p(out.data_ptr()),
+                                 batch, M, N, K, int(transA), int(transB), f, kg, -1 if tile is None else int(tile),
+                                 C.c_void_p(scratch.data_ptr() if scratch is not None else 0),
+                                 scratch.numel() if scratch is not None else 0, _stream_ptr(stream)), "tnc_cgemm")
     return out
 
 

@@ -89,3 +89,52 @@ def test_cgemm_scratch_too_small(tnc):
     with pytest.raises(tnc.TncError) as ei:
         tnc.cgemm(A, B, 1, 128, 64, 64, 0, 1, "split_bf16", scratch=small)
     assert ei.value.status == tnc.TNC_ENOMEM
+
+
+TILE_SHAPES = [(2, 128, 128, 64, 0, 1), (1, 256, 256, 4096, 0, 1), (3, 512, 128, 128, 0, 1), (1, 256, 512, 1024, 1, 0)]
+
+
+@pytest.mark.parametrize("shape", TILE_SHAPES)
+@pytest.mark.parametrize("tile", [1, 2, 3, 4])
+@pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
+def test_cgemm_tensor_core_tile_widths(tnc, shape, tile, form):
+    """Every tcgen05 tile width (128 x 64, 128 x 128, 128 x 256 real outputs
+    per CTA; 128 x 128 with the split on chip) on the same shapes, through
+    tnc_cgemm_variant."""
+    batch, M, N, K, tA, tB = shape
+    if tile == 4 and (form != "split_bf16" or tA or not tB):
+        pytest.skip("the on-chip split takes split-BF16 with K-major operands only")
+    rng = np.random.default_rng(batch + M + N + K + tile)
+    A = _crand(batch * M * K, rng)
+    B = _crand(batch * K * N, rng)
+    got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, tA, tB, form,
+                    kernel="tc", tile=tile)
+    torch.cuda.synchronize()
+    ref = _ref(A, B, batch, M, N, K, tA, tB)
+    err = np.linalg.norm(got.cpu().numpy().astype(np.complex128) - ref) / np.linalg.norm(ref)
+    assert err <= TOL[form], f"{shape} tile {tile} {form}: {err:.3g}"
+
+
+def test_cgemm_variant_rejects_impossible_choice(tnc):
+    A = torch.zeros(128 * 64, dtype=torch.complex64, device="cuda")
+    B = torch.zeros(64 * 64, dtype=torch.complex64, device="cuda")
+    with pytest.raises(tnc.TncError) as ei:  # N = 64 complex is too narrow for 256 real columns
+        tnc.cgemm(A, B, 1, 128, 64, 64, 0, 1, "split_bf16", kernel="tc", tile=3)
+    assert ei.value.status == tnc.TNC_EINVAL
+    with pytest.raises(tnc.TncError) as ei:  # no tensor cores in the FP32 form
+        tnc.cgemm(A, B, 1, 128, 64, 64, 0, 1, "fp32", kernel="tc", tile=2)
+    assert ei.value.status == tnc.TNC_EINVAL
+
+
+def test_cgemm_on_chip_split_unaligned_operands(tnc):
+    """Operands that are not 16-byte aligned go through the hi/lo planes
+    instead of the on-chip split, with the same result."""
+    batch, M, N, K = 2, 128, 64, 256
+    rng = np.random.default_rng(5)
+    A = _crand(batch * M * K + 1, rng)
+    B = _crand(batch * K * N + 1, rng)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    got = tnc.cgemm(dA[1:], dB[1:], batch, M, N, K, 0, 1, "split_bf16", kernel="tc", tile=4)
+    ref = _ref(A[1:], B[1:], batch, M, N, K, 0, 1)
+    err = np.linalg.norm(got.cpu().numpy().astype(np.complex128) - ref) / np.linalg.norm(ref)
+    assert err <= TOL["split_bf16"]
