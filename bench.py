@@ -219,16 +219,17 @@ def serving_measure(tnc, torch, form: str, seed: int = 0, n_req: int = 240, cost
     return result
 
 
-def _traffic(step, kernel, form):
+def _traffic(step, kernel, form, tile=0):
     """DRAM bytes per launch of this step from the committed ncu summary
-    (profiles/traffic.json), scaled by batch; None if that shape was not
-    captured."""
+    (profiles/traffic.json), scaled by batch; None if that shape and kernel
+    variant were not captured."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p) or not step.get("batch"):
         return None
     with open(p) as f:
         for e in json.load(f)["entries"]:
-            if e["kernel"] == kernel and e["form"] == form and all(e[k] == step.get(k) for k in ("M", "N", "K")):
+            if e["kernel"] == kernel and e["form"] == form and e.get("tile", 0) == tile and \
+                    all(e[k] == step.get(k) for k in ("M", "N", "K")):
                 return e["dram_bytes_captured"] * step["batch"] / e["captured_batch"]
     return None
 
@@ -367,30 +368,53 @@ def run_ours(args):
         d["launches"] += int(runs)
     total_ms = sum(d["ms"] for d in kinds.values())
     di = int(np.argmax(prof["ms"]))
-    step = plan.export()["steps"][di]
+    steps_all = plan.export()["steps"]
+    step = steps_all[di]
     dkind, druns = int(prof["kind"][di]), int(prof["runs"][di])
     avg_s = float(prof["ms"][di]) / druns / 1e3
     fl, by = float(prof["flops"][di]), float(prof["bytes"][di])
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    if dkind in (100, 101, 2):
-        roof = {"bound": "hbm", "achieved": by / avg_s / 1e9, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}
+    # three bf16 (tf32) products per useful product; tf32 peak = half the bf16 peak
+    tc_peak = float(peaks["bf16_tflops"]) * (1.0 if args.form == "split_bf16" else 0.5)
+    hbm = float(peaks["hbm_gbs"])
+    if dkind in (100, 101, 2) or (dkind == 4 and by / hbm / 1e9 > 3.0 * fl / tc_peak / 1e12):
+        # tensor-core nodes whose algorithmic bytes take longer than their MMAs at peak are HBM-bound
+        roof = {"bound": "hbm", "achieved": by / avg_s / 1e9, "peak": hbm, "unit": "GB/s"}
     elif dkind == 4:
-        # three bf16 (tf32) products per useful product; tf32 peak = half the bf16 peak
-        pk = float(peaks["bf16_tflops"]) * (1.0 if args.form == "split_bf16" else 0.5)
-        roof = {"bound": "tensor", "achieved": 3.0 * fl / avg_s / 1e12, "peak": pk, "unit": "TFLOP/s"}
+        roof = {"bound": "tensor", "achieved": 3.0 * fl / avg_s / 1e12, "peak": tc_peak, "unit": "TFLOP/s"}
     else:
         pk = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock
         roof = {"bound": "alu", "achieved": fl / avg_s / 1e12, "peak": pk, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = _traffic(step, names.get(dkind), args.form)
+    choices = plan.get_kernels()
+    dtile = int(choices[di][1]) if dkind == 4 else 0
+    roof["traffic"] = _traffic(step, names.get(dkind), args.form, dtile)
     roof["kernel"] = names.get(dkind, str(dkind))
     roof["step"] = {k: step.get(k) for k in ("batch", "M", "N", "K")}
+    if dkind == 4:
+        roof["step"]["tile"] = dtile
     roof["launches_timed"] = druns
     roof["avg_launch_ms"] = avg_s * 1e3
     roof["algorithmic_bytes_per_launch"] = by
     roof["algorithmic_flops_per_launch"] = fl
     roof["share_of_device_time"] = float(prof["ms"][di]) / total_ms if total_ms else None
     roof["peak_source"] = src + (" burst" if dkind == 4 else "")
+    if args.steps_detail and rank == 0:
+        rows = []
+        for i, (ms, runs, kind, fl_i, by_i) in enumerate(zip(prof["ms"], prof["runs"], prof["kind"], prof["flops"],
+                                                              prof["bytes"])):
+            if runs == 0:
+                continue
+            st_i = steps_all[i]
+            t_launch = float(ms) / int(runs)
+            mult = 3.0 if int(kind) == 4 else 1.0
+            bound_ms = max(float(by_i) / hbm / 1e6, mult * float(fl_i) / tc_peak / 1e9)
+            rows.append({"step": i, "kernel": names.get(int(kind), str(int(kind))),
+                         "tile": int(choices[i][1]), "shape": {k: st_i.get(k) for k in ("batch", "M", "N", "K")},
+                         "ms": t_launch, "bound_ms": bound_ms, "x_over_bound": t_launch / bound_ms if bound_ms else None})
+        rows.sort(key=lambda r: -r["ms"])
+        with open(args.steps_detail, "w") as f:
+            json.dump(rows, f, indent=1)
     breakdown = {}
     for kd, v in sorted(kinds.items(), key=lambda kv: -kv[1]["ms"]):
         s = v["ms"] / 1e3
@@ -444,6 +468,8 @@ def main():
     ap.add_argument("--tune-cache", default=None, help="JSON file to save / reuse the autotuner's kernel choices")
     ap.add_argument("--rows", type=int, default=5, help="IQP lattice rows (the benchmark uses 5 x 8)")
     ap.add_argument("--cols", type=int, default=8)
+    ap.add_argument("--steps-detail", default=None,
+                    help="write a JSON table of every program step (shape, kernel, ms per launch, roofline ms)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

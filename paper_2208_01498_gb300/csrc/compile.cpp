@@ -101,8 +101,15 @@ void choose_gemm_kernel(GemmDesc& g) {
     g.kernel = KG_DOT;
   else if (g.N <= 16 && g.K <= 16)
     g.kernel = KG_NARROW;
-  else if (g.form != TNC_FP32 && pow2 && g.M >= 128 && g.N >= 32 && g.K >= 32)
+  else if (g.form != TNC_FP32 && pow2 && g.M >= 128 && g.N >= 32 && g.K >= 32) {
     g.kernel = KG_TC;
+    // split-BF16 nodes with K-major operands and moderate M N split on chip
+    // (the operands cross HBM once; long K prefetches the k-block after
+    // next); very large M N re-read the operands from many tiles and run
+    // faster from pre-split planes
+    if (g.form == TNC_SPLIT_BF16 && !g.transA && g.transB && g.N >= 64 && MN <= (double)(1 << 22))
+      g.tile = g.K >= 512 ? 5 : 4;
+  }
   else if (g.N <= 32)
     g.kernel = KG_SIMT_64x32;
   else
@@ -143,7 +150,10 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
     add(KG_TC, 1);
     if (g0.N >= 64) add(KG_TC, 2);
     if (g0.N >= 128) add(KG_TC, 3);
-    if (g0.form == TNC_SPLIT_BF16 && g0.N >= 64 && !g0.transA && g0.transB) add(KG_TC, 4);
+    if (g0.form == TNC_SPLIT_BF16 && g0.N >= 64 && !g0.transA && g0.transB) {
+      add(KG_TC, 4);
+      add(KG_TC, 5);
+    }
   }
   *n = k;
 }

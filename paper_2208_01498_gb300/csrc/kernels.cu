@@ -313,6 +313,7 @@ __global__ void __launch_bounds__(kDotThreads)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
+    if (i >= MN) break;  // uniform over the block
     double x = acc64[i].x + acc[i].x, y = acc64[i].y + acc[i].y;
     for (int off = 16; off; off >>= 1) {
       x += __shfl_xor_sync(0xffffffffu, x, off);
@@ -325,6 +326,59 @@ __global__ void __launch_bounds__(kDotThreads)
     double2 s = make_double2(0, 0);
     for (int w = 0; w < kDotThreads / 32; ++w) s.x += red[w][threadIdx.x].x, s.y += red[w][threadIdx.x].y;
     part[(bz * gridDim.x + blockIdx.x) * MN + threadIdx.x] = s;
+  }
+}
+
+// M = N = 1 (an inner product per batch entry, e.g. the root of a tree):
+// 16-byte loads of two complex values from each operand, four independent
+// loads in flight per thread, FP32 runs of up to 32 products summed in FP64.
+__global__ void __launch_bounds__(kDotThreads)
+    cgemm_dot11_kernel(const float4* __restrict__ A, const float4* __restrict__ B, double2* __restrict__ part,
+                       int64_t K2, int64_t b0) {
+  const int64_t bz = b0 + blockIdx.y;
+  A += bz * K2;
+  B += bz * K2;
+  double2 acc64 = make_double2(0, 0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  while (k < K2) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int r = 0; r < 4 && k < K2; ++r) {
+      float4 a[4], b[4];
+      int cnt = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t kk = k + u * stride;
+        if (kk < K2) {
+          a[u] = A[kk];
+          b[u] = B[kk];
+          cnt = u + 1;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u < cnt) {
+          acc = cmul_add(acc, make_float2(a[u].x, a[u].y), make_float2(b[u].x, b[u].y));
+          acc = cmul_add(acc, make_float2(a[u].z, a[u].w), make_float2(b[u].z, b[u].w));
+        }
+      }
+      k += 4 * stride;
+    }
+    acc64.x += acc.x, acc64.y += acc.y;
+  }
+  __shared__ double2 red[kDotThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double x = acc64.x, y = acc64.y;
+  for (int off = 16; off; off >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, off);
+    y += __shfl_xor_sync(0xffffffffu, y, off);
+  }
+  if (lane == 0) red[wid] = make_double2(x, y);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = make_double2(0, 0);
+    for (int w = 0; w < kDotThreads / 32; ++w) t.x += red[w].x, t.y += red[w].y;
+    part[bz * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -537,7 +591,13 @@ int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp,
       if (nblk > 1024) nblk = 1024;
       if (nblk < 1) nblk = 1;
       if ((uint64_t)d.batch * nblk * MN * 2 > d.scratch_elems) return (int)cudaErrorInvalidValue;
-      for (int64_t b0 = 0; b0 < d.batch; b0 += 65535) {
+      const bool vec11 = MN == 1 && d.K % 2 == 0 && ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0;
+      for (int64_t b0 = 0; b0 < d.batch && vec11; b0 += 65535) {
+        int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
+        dim3 grid((unsigned)nblk, (unsigned)nb);
+        cgemm_dot11_kernel<<<grid, kDotThreads, 0, st>>>((const float4*)A, (const float4*)B, part, d.K / 2, b0);
+      }
+      for (int64_t b0 = 0; b0 < d.batch && !vec11; b0 += 65535) {
         int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
         dim3 grid((unsigned)nblk, (unsigned)nb);
         cgemm_dot_kernel<<<grid, kDotThreads, 0, st>>>(A, B, part, (int)d.M, (int)d.N, d.K, d.transA, d.transB,

@@ -14,7 +14,7 @@
 // 128 x BN output tile per CTA: warp 0 issues TMA loads (128B-swizzled boxes
 // of 128-byte rows) into a STAGES-deep shared-memory ring guarded by
 // mbarriers, warp 1 (one lane) issues tcgen05.mma into one of two 128 x BN FP32
-// accumulators in TMEM (alternating every 512 k' for bf16, 128 k' for tf32),
+// accumulators in TMEM (alternating every 512 k' for bf16, 32 k' for tf32),
 // and warps 2..5 add each finished accumulator into FP32 registers with
 // tcgen05.ld, then store C.
 // Every wait is bounded by a time limit; a timeout sets tc_error_flag and the
@@ -184,7 +184,11 @@ __global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
   constexpr int ES = kTF32 ? 4 : 2;
   constexpr int BK = 128 / ES;            // elements per 128-byte row
   constexpr int KSTEP = kTF32 ? 8 : 16;   // K of one MMA instruction
-  constexpr int CHUNK = (kTF32 ? 128 : 512) / BK;  // k-blocks per accumulation chunk
+  // k-blocks per accumulation chunk: 512 k' for bf16; 32 k' (one k-block)
+  // for tf32, whose three-product error budget leaves less room for the
+  // tensor core's accumulation (on a 36-qubit depth-16 circuit: relative
+  // error 1.4e-5 with 128 k' chunks, 9.7e-6 with 64, 5.2e-6 with 32)
+  constexpr int CHUNK = (kTF32 ? 32 : 512) / BK;
   constexpr uint32_t A_BYTES = BM * 128, B_BYTES = BN * 128;
   constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   constexpr uint32_t IDESC = instr_desc<kTF32, BN>();
@@ -367,14 +371,24 @@ __global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
 // planes written, planes read back).
 //
 // Warps 0..3: accumulation and epilogue (TMEM lane quarter = warp); warp 4:
-// TMEM allocation and the MMA issuer (one lane); warps 5..12: converters.
+// TMEM allocation and the MMA issuer (one lane); warps 5..16: converters.
 // Finished accumulation chunks are added into a third TMEM region (the
-// running sum) instead of registers, so no thread holds a whole row.
+// running sum) instead of registers, so no thread holds a whole row.  The
+// register file is split between the SM's four sub-partitions (16K 32-bit
+// registers each); a 17-warp block puts 5 warps on one of them, which caps a
+// thread at 96 registers, and the converters are sized to fit that (one
+// k-block of loads in registers; the PREFETCH variant also sends the k-block
+// after next towards L2).  Two stages keep the block's shared memory under
+// 196 KB: the SM's unified L1/shared storage then leaves about 90 KB of L1
+// for the converters' loads in flight (with three stages the carve-out rose
+// to 228 KB, L1 fell to 28 KB and the kernel ran 10-25 % slower).
+// The epilogue re-orders each warp's 32 x 8 complex block through shared
+// memory into output order (BlockOrder) before storing.
 // Every wait is bounded as in tc_gemm_kernel; no asynchronous copies are in
 // flight at teardown (the converters' stores are synchronous).
 constexpr int kFzBN = 128;            // real output columns per CTA (64 complex)
-constexpr int kFzStages = 3;
-constexpr int kFzConvWarps = 8;
+constexpr int kFzStages = 2;
+constexpr int kFzConvWarps = 12;   // 384 threads x 4 tasks = 1024 A + 512 B' chunks per k-block
 constexpr int kFzThreads = 32 * (5 + kFzConvWarps);
 constexpr uint32_t kFzTileBytes = BM * 128;                    // one plane tile: 128 rows x 64 bf16
 constexpr uint32_t kFzStageBytes = 4 * kFzTileBytes;            // A hi, A lo, B' hi, B' lo
@@ -414,9 +428,142 @@ __device__ __forceinline__ void sts128(uint32_t addr, const uint32_t* w) {
                : "memory");
 }
 
+// Output order of one warp's epilogue block: 32 rows (m bits 0..4, from the
+// lane) x 8 complex columns (n bits 0..2).  The consumer's layout puts these
+// 8 index bits at 8 output bit positions; ranking the positions gives a
+// staging index whose increasing order is increasing output address, so a
+// block written into shared memory by (row, column) and read back by staging
+// index stores runs of consecutive addresses (a whole 2 KB block when the 8
+// positions are the lowest 8).  Requires nM >= 5 and nN >= 3.
+struct BlockOrder {
+  int pos[8];   // output bit position of block bit b (0..4 rows, 5..7 columns)
+  int rank[8];  // rank of pos[b] among the 8
+  __device__ explicit BlockOrder(const OutMap& om) {
+#pragma unroll
+    for (int b = 0; b < 5; ++b) pos[b] = om.pos[om.nN + b];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) pos[5 + b] = om.pos[b];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      int r = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) r += pos[k] < pos[b];
+      rank[b] = r;
+    }
+  }
+  __device__ uint32_t index_row(uint32_t lane) const {
+    uint32_t x = 0;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) x |= ((lane >> b) & 1u) << rank[b];
+    return x;
+  }
+  __device__ uint32_t index_col(uint32_t j) const {
+    uint32_t x = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) x |= ((j >> b) & 1u) << rank[5 + b];
+    return x;
+  }
+  // output offset (relative to the block's origin) of staging-index bits x
+  __device__ uint64_t offset_of(uint32_t x) const {
+    uint64_t o = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) o |= (uint64_t)((x >> rank[b]) & 1u) << pos[b];
+    return o;
+  }
+};
+
+// bank spread of the staging block (8-byte elements): low 4 index bits XOR
+// the high 4, a bijection on 0..255
+__device__ __forceinline__ uint32_t stage_swz(uint32_t x) { return x ^ ((x >> 4) & 15u); }
+
+// One k-block of a converter thread: its 4 tasks (j = ct + 384 i) of 2 x 16
+// bytes each.  Task j < 1024: A tile row j / 8; otherwise complex column
+// (j - 1024) / 8 of B, giving B' rows 2n and 2n + 1.  Chunk j % 8 = ct % 8
+// in both cases.  1024 is a multiple of 32, so A/B tasks never mix in a warp.
+struct FzRegs {
+  float4 v[4][2];
+};
+
+struct FzGeom {
+  int M, N, K, tiles_m, tiles_n, nk;
+  int64_t tiles;  // tiles_m * tiles_n * batch
+};
+
+// tile t -> (batch, first row, first real column); m-tiles fastest
+__device__ __forceinline__ void fz_tile(const FzGeom& g, int64_t t, int& bz, int& m0, int& n0) {
+  const int64_t per_b = (int64_t)g.tiles_m * g.tiles_n;
+  bz = (int)(t / per_b);
+  const int r = (int)(t - (int64_t)bz * per_b);
+  m0 = (r % g.tiles_m) * BM;
+  n0 = (r / g.tiles_m) * kFzBN;
+}
+
+__device__ __forceinline__ void fz_load(FzRegs& R, const float2* __restrict__ A, const float2* __restrict__ B,
+                                        const FzGeom& g, int bz, int m0, int n0, int kb, int ct) {
+  const int64_t koff = (int64_t)kb * 32 + 4 * (ct & 7);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int j = ct + 384 * i;
+    const float2* p = j < 1024 ? A + ((int64_t)bz * g.M + m0 + (j >> 3)) * g.K + koff
+                               : B + ((int64_t)bz * g.N + n0 / 2 + ((j - 1024) >> 3)) * g.K + koff;
+    R.v[i][0] = __ldg((const float4*)p);
+    R.v[i][1] = __ldg((const float4*)p + 1);
+  }
+}
+
+// L2 prefetch of a k-block's lines (one thread per 128-byte line), so that
+// a second k-block of loads is on its way without holding registers
+__device__ __forceinline__ void fz_prefetch(const float2* __restrict__ A, const float2* __restrict__ B,
+                                            const FzGeom& g, int bz, int m0, int n0, int kb, int ct) {
+  if (ct & 3) return;
+  const int64_t koff = (int64_t)kb * 32 + 4 * (ct & 7);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int j = ct + 384 * i;
+    const float2* p = j < 1024 ? A + ((int64_t)bz * g.M + m0 + (j >> 3)) * g.K + koff
+                               : B + ((int64_t)bz * g.N + n0 / 2 + ((j - 1024) >> 3)) * g.K + koff;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+  }
+}
+
+__device__ __forceinline__ void fz_store(const FzRegs& R, uint32_t st, int ct) {
+  const int cc = ct & 7;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int j = ct + 384 * i;
+    uint32_t h[4], l[4];
+    split_words(R.v[i][0], R.v[i][1], h, l);
+    if (j < 1024) {
+      const uint32_t o = swz128(j >> 3, cc);
+      sts128(st + o, h);
+      sts128(st + kFzTileBytes + o, l);
+    } else {
+      // words (br, bi) -> row 2n: (br, -bi), row 2n + 1: (bi, br)
+      uint32_t h0[4], l0[4], h1[4], l1[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        h0[q] = h[q] ^ 0x80000000u;
+        l0[q] = l[q] ^ 0x80000000u;
+        h1[q] = __byte_perm(h[q], 0, 0x1032);
+        l1[q] = __byte_perm(l[q], 0, 0x1032);
+      }
+      const int r0 = 2 * ((j - 1024) >> 3);
+      sts128(st + 2 * kFzTileBytes + swz128(r0, cc), h0);
+      sts128(st + 3 * kFzTileBytes + swz128(r0, cc), l0);
+      sts128(st + 2 * kFzTileBytes + swz128(r0 + 1, cc), h1);
+      sts128(st + 3 * kFzTileBytes + swz128(r0 + 1, cc), l1);
+    }
+  }
+}
+
+// Persistent: CTA c computes tiles c, c + gridDim.x, ...; the shared-memory
+// ring, the two TMEM accumulator slots and their barriers run on across tile
+// boundaries, so a tile's epilogue overlaps the next tile's MMAs and the
+// converters keep two k-blocks of loads in flight through tile changes.
+template <bool PREFETCH>
 __global__ void __launch_bounds__(kFzThreads, 1)
-    tc_fused_bf16_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float* __restrict__ C, int M,
-                         int N2, int K, int b0, const __grid_constant__ OutMap om) {
+    tc_fused_bf16_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float* __restrict__ C,
+                         const FzGeom geo, const __grid_constant__ OutMap om) {
   constexpr int CHUNK = 512 / 64;  // k-blocks (64 k') per accumulation chunk
   constexpr uint32_t IDESC = instr_desc<false, kFzBN>();
   extern __shared__ uint8_t smem_raw[];
@@ -428,16 +575,16 @@ __global__ void __launch_bounds__(kFzThreads, 1)
   uint64_t* done = acc_empty + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   int* abort_flag = (int*)(tmem_slot + 1);
-  uint64_t* coltab = (uint64_t*)(tmem_slot + 4);  // [kFzBN / 2]
+  uint64_t* coltab = (uint64_t*)(tmem_slot + 4);  // [4 warps][kFzBN / 2]
+  uint32_t* blk_col = (uint32_t*)(coltab + 4 * (kFzBN / 2));  // [8] staging index of block column j
+  uint64_t* blk_dep = (uint64_t*)(blk_col + 8);               // [8] output offset of staging index bits 5..7
+  float2* stage_out = (float2*)(blk_dep + 8);                 // [4 warps][256]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles_m = M / BM;
-  const int m0 = (blockIdx.x % tiles_m) * BM;
-  const int n0 = (blockIdx.x / tiles_m) * kFzBN;  // real column
-  const int bz = b0 + blockIdx.z;
-  const int N = N2 / 2;
-  const int nk = K / 32;  // k-blocks: 32 complex k = 64 k'
-  const int nchunks = (nk + CHUNK - 1) / CHUNK;
+  const int nk = geo.nk;
+  const int nchunks = (nk + CHUNK - 1) / CHUNK;  // per tile
+  const int64_t my_tiles = blockIdx.x < geo.tiles ? (geo.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int N2 = 2 * geo.N;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kFzStages; ++s) {
@@ -452,179 +599,186 @@ __global__ void __launch_bounds__(kFzThreads, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (threadIdx.x < kFzBN / 2 && !om.ident) coltab[threadIdx.x] = om.col(n0 / 2 + threadIdx.x);
   if (warp == 4) tmem_alloc(tmem_slot, 512);  // slot 0, slot 1, running sum (128 columns each)
+  if (!om.ident && threadIdx.x < 8) {
+    const BlockOrder bo(om);
+    blk_col[threadIdx.x] = bo.index_col(threadIdx.x);
+    blk_dep[threadIdx.x] = bo.offset_of((uint32_t)threadIdx.x << 5);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
   if (warp >= 5) {
-    // converters: thread ct handles tile rows ct/8 + 32 i (A, i < 4) and
-    // complex columns ct/8 + 32 i (B, i < 2), 16-byte chunk ct % 8 of each
+    // converters: global k-block q = (local tile) * nk + kb
     const int ct = threadIdx.x - 160;
-    const int cr = ct >> 3, cc = ct & 7;
-    const float4* pa[4];
-    const float4* pb[2];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      pa[i] = (const float4*)(A + ((int64_t)bz * M + m0 + cr + 32 * i) * K + 4 * cc);
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-      pb[i] = (const float4*)(B + ((int64_t)bz * N + n0 / 2 + cr + 32 * i) * K + 4 * cc);
-    float4 ra[4][2], rb[2][2];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      ra[i][0] = __ldg(pa[i]);
-      ra[i][1] = __ldg(pa[i] + 1);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      rb[i][0] = __ldg(pb[i]);
-      rb[i][1] = __ldg(pb[i] + 1);
-    }
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kFzStages;
-      if (kb >= kFzStages && !mbar_wait(&empty[s], ((kb / kFzStages) + 1) & 1)) {
+    const int64_t total = my_tiles * nk;
+    FzRegs R0;
+    // load cursor: local tile lt_ld (coordinates bz, m0, n0), k-block kb_ld
+    int64_t lt_ld = 0;
+    int kb_ld = 0, bz = 0, m0 = 0, n0 = 0;
+    if (my_tiles > 0) fz_tile(geo, blockIdx.x, bz, m0, n0);
+    auto load_next = [&](FzRegs& R) {
+      fz_load(R, A, B, geo, bz, m0, n0, kb_ld, ct);
+      if (++kb_ld == nk) {
+        kb_ld = 0;
+        if (++lt_ld < my_tiles) fz_tile(geo, (int64_t)blockIdx.x + lt_ld * gridDim.x, bz, m0, n0);
+      }
+    };
+    if (total > 0) load_next(R0);
+    int s = 0;         // stage of k-block q
+    uint32_t ph = 0;   // number of ring wraps before q, mod 2
+    // one k-block from registers R into stage s, then the loads of k-block
+    // q + 1 into R; false after a timeout or an abort.  (Two register sets
+    // for two k-blocks in flight need more than the 96 registers a thread
+    // of this 17-warp block can have, and spill.)
+    auto step = [&](FzRegs& R, int64_t q) -> bool {
+      if (q >= kFzStages && !mbar_wait(&empty[s], ph ^ 1u)) {
         atomicExch(&tc_error_flag, 6);
         *(volatile int*)abort_flag = 1;
-        break;
+        return false;
       }
-      if (*(volatile int*)abort_flag) break;
-      const uint32_t st = smem_u32(smem + s * kFzStageBytes);
-      uint32_t h[4], l[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        split_words(ra[i][0], ra[i][1], h, l);
-        const uint32_t o = swz128(cr + 32 * i, cc);
-        sts128(st + o, h);
-        sts128(st + kFzTileBytes + o, l);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        // words (br, bi) -> row 2n: (br, -bi), row 2n + 1: (bi, br)
-        split_words(rb[i][0], rb[i][1], h, l);
-        uint32_t h0[4], l0[4], h1[4], l1[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          h0[j] = h[j] ^ 0x80000000u;
-          l0[j] = l[j] ^ 0x80000000u;
-          h1[j] = __byte_perm(h[j], 0, 0x1032);
-          l1[j] = __byte_perm(l[j], 0, 0x1032);
-        }
-        const int r0 = 2 * (cr + 32 * i);
-        sts128(st + 2 * kFzTileBytes + swz128(r0, cc), h0);
-        sts128(st + 3 * kFzTileBytes + swz128(r0, cc), l0);
-        sts128(st + 2 * kFzTileBytes + swz128(r0 + 1, cc), h1);
-        sts128(st + 3 * kFzTileBytes + swz128(r0 + 1, cc), l1);
-      }
+      if (*(volatile int*)abort_flag) return false;
+      fz_store(R, smem_u32(smem + s * kFzStageBytes), ct);
       // make the generic-proxy stores visible to the tensor core, then signal
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[s])) : "memory");
-      if (kb + 1 < nk) {
-        const int adv = (kb + 1) * 16;  // float4 per k-block
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          ra[i][0] = __ldg(pa[i] + adv);
-          ra[i][1] = __ldg(pa[i] + adv + 1);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          rb[i][0] = __ldg(pb[i] + adv);
-          rb[i][1] = __ldg(pb[i] + adv + 1);
-        }
+      if (++s == kFzStages) {
+        s = 0;
+        ph ^= 1u;
       }
-    }
+      if (q + 1 < total) load_next(R);
+      if (PREFETCH && q + 2 < total) fz_prefetch(A, B, geo, bz, m0, n0, kb_ld, ct);  // cursor is at q + 2
+      return true;
+    };
+    for (int64_t q = 0; q < total; ++q)
+      if (!step(R0, q)) break;
   } else if (warp == 4) {
     if (lane == 0) {
       bool ok = true;
-      for (int c = 0; c < nchunks && ok; ++c) {
-        const int slot = c & 1;
-        if (c >= 2 && !mbar_wait(&acc_empty[slot], ((c >> 1) + 1) & 1)) {
-          atomicExch(&tc_error_flag, 4);
-          *(volatile int*)abort_flag = 1;
-          break;
-        }
-        const uint32_t dtm = tmem + slot * kFzBN;
-        const int kb_end = (c + 1) * CHUNK < nk ? (c + 1) * CHUNK : nk;
-        for (int kb = c * CHUNK; kb < kb_end; ++kb) {
-          const int s = kb % kFzStages;
-          if (!mbar_wait(&full[s], (kb / kFzStages) & 1)) {
-            atomicExch(&tc_error_flag, 2);
+      int64_t gc = 0;       // global chunk counter
+      int s = 0;            // stage of the next k-block
+      uint32_t ph = 0;      // ring wraps before it, mod 2
+      for (int64_t lt = 0; lt < my_tiles && ok; ++lt) {
+        for (int c = 0; c < nchunks && ok; ++c, ++gc) {
+          const int slot = (int)(gc & 1);
+          if (gc >= 2 && !mbar_wait(&acc_empty[slot], (uint32_t)(((gc >> 1) + 1) & 1))) {
+            atomicExch(&tc_error_flag, 4);
             *(volatile int*)abort_flag = 1;
             ok = false;
             break;
           }
-          if (*(volatile int*)abort_flag) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t sa = smem_u32(smem + s * kFzStageBytes);
-          const uint64_t dAh = sw128_desc(sa), dAl = sw128_desc(sa + kFzTileBytes);
-          const uint64_t dBh = sw128_desc(sa + 2 * kFzTileBytes), dBl = sw128_desc(sa + 3 * kFzTileBytes);
+          const uint32_t dtm = tmem + slot * kFzBN;
+          const int kb_end = (c + 1) * CHUNK < nk ? (c + 1) * CHUNK : nk;
+          for (int kb = c * CHUNK; kb < kb_end; ++kb) {
+            if (!mbar_wait(&full[s], ph)) {
+              atomicExch(&tc_error_flag, 2);
+              *(volatile int*)abort_flag = 1;
+              ok = false;
+              break;
+            }
+            if (*(volatile int*)abort_flag) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * kFzStageBytes);
+            const uint64_t dAh = sw128_desc(sa), dAl = sw128_desc(sa + kFzTileBytes);
+            const uint64_t dBh = sw128_desc(sa + 2 * kFzTileBytes), dBl = sw128_desc(sa + 3 * kFzTileBytes);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t adv = (uint64_t)((kk * 16 * 2) >> 4);
-            const uint32_t first = (kb == c * CHUNK && kk == 0) ? 0u : 1u;
-            mma<false>(dtm, dAh + adv, dBh + adv, IDESC, first);
-            mma<false>(dtm, dAh + adv, dBl + adv, IDESC, 1u);
-            mma<false>(dtm, dAl + adv, dBh + adv, IDESC, 1u);
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t adv = (uint64_t)((kk * 16 * 2) >> 4);
+              const uint32_t first = (kb == c * CHUNK && kk == 0) ? 0u : 1u;
+              mma<false>(dtm, dAh + adv, dBh + adv, IDESC, first);
+              mma<false>(dtm, dAh + adv, dBl + adv, IDESC, 1u);
+              mma<false>(dtm, dAl + adv, dBh + adv, IDESC, 1u);
+            }
+            mma_commit(&empty[s]);
+            if (++s == kFzStages) {
+              s = 0;
+              ph ^= 1u;
+            }
           }
-          mma_commit(&empty[s]);
+          if (ok) mma_commit(&acc_full[slot]);
         }
-        if (ok) mma_commit(&acc_full[slot]);
       }
       mma_commit(done);
     }
   } else {
-    // accumulation: row 32 warp + lane of the tile
+    // accumulation: row 32 warp + lane of each tile
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const uint32_t tsum = tmem + lane_base + 2 * kFzBN;
-    const int row = m0 + warp * 32 + lane;
-    const uint64_t roff = om.ident ? 0 : om.row(bz, row, M, N);
+    uint64_t* ct = coltab + warp * (kFzBN / 2);
+    float2* so = stage_out + warp * 256;
+    uint32_t idx_row = 0;
+    uint64_t dep_lane = 0;
+    if (!om.ident) {
+      const BlockOrder bo(om);
+      idx_row = bo.index_row(lane);
+      dep_lane = bo.offset_of((uint32_t)lane);
+    }
+    int64_t gc = 0;
     bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      const int slot = c & 1;
-      if (!mbar_wait(&acc_full[slot], (c >> 1) & 1)) {
-        atomicExch(&tc_error_flag, 3);
-        *(volatile int*)abort_flag = 1;
-        ok = false;
-        break;
+    for (int64_t lt = 0; lt < my_tiles && ok; ++lt) {
+      int bz, m0, n0;
+      fz_tile(geo, (int64_t)blockIdx.x + lt * gridDim.x, bz, m0, n0);
+      const int row = m0 + warp * 32 + lane;
+      const uint64_t roff = om.ident ? 0 : om.row(bz, m0 + warp * 32, geo.M, geo.N);  // lane bits clear
+      if (!om.ident) {
+        ct[lane] = om.col(n0 / 2 + lane);
+        ct[lane + 32] = om.col(n0 / 2 + lane + 32);
       }
-      tc_fence_after();
-      const bool last = c == nchunks - 1;
-      const uint32_t tslot = tmem + lane_base + slot * kFzBN;
-      const bool write_out = last && !*(volatile int*)abort_flag;
-#pragma unroll 1
-      for (int col = 0; col < kFzBN; col += 16) {
-        float v[16];
-        tmem_ld16(tslot + col, v);
-        if (c > 0) {
-          float w[16];
-          tmem_ld16(tsum + col, w);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += w[i];
+      __syncwarp();
+      for (int c = 0; c < nchunks; ++c, ++gc) {
+        const int slot = (int)(gc & 1);
+        if (!mbar_wait(&acc_full[slot], (uint32_t)((gc >> 1) & 1))) {
+          atomicExch(&tc_error_flag, 3);
+          *(volatile int*)abort_flag = 1;
+          ok = false;
+          break;
         }
-        if (!last) {
-          tmem_st16(tsum + col, v);
-        } else if (write_out) {
-          if (om.ident) {
-            float4* dst = (float4*)(C + ((int64_t)bz * M + row) * N2 + n0 + col);
+        tc_fence_after();
+        const bool last = c == nchunks - 1;
+        const uint32_t tslot = tmem + lane_base + slot * kFzBN;
+        const bool write_out = last && !*(volatile int*)abort_flag;
+#pragma unroll 1
+        for (int col = 0; col < kFzBN; col += 16) {
+          float v[16];
+          tmem_ld16(tslot + col, v);
+          if (c > 0) {
+            float w[16];
+            tmem_ld16(tsum + col, w);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-          } else {
-            float2* C2 = (float2*)C;
+            for (int i = 0; i < 16; ++i) v[i] += w[i];
+          }
+          if (!last) {
+            tmem_st16(tsum + col, v);
+          } else if (write_out) {
+            if (om.ident) {
+              float4* dst = (float4*)(C + ((int64_t)bz * geo.M + row) * N2 + n0 + col);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) C2[roff + coltab[col / 2 + i]] = make_float2(v[2 * i], v[2 * i + 1]);
+              for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            } else {
+              // through the warp's staging block: written by (row, column),
+              // read back in output order, so that each store covers the
+              // block's runs of consecutive output addresses
+#pragma unroll
+              for (int j = 0; j < 8; ++j) so[stage_swz(idx_row | blk_col[j])] = make_float2(v[2 * j], v[2 * j + 1]);
+              __syncwarp();
+              float2* C2 = (float2*)C + roff + ct[col / 2] + dep_lane;
+#pragma unroll
+              for (int t = 0; t < 8; ++t) C2[blk_dep[t]] = so[stage_swz((uint32_t)(t * 32 + lane))];
+              __syncwarp();
+            }
           }
         }
+        if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[slot])) : "memory");
       }
-      if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      tc_fence_before();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[slot])) : "memory");
+      __syncwarp();  // coltab entries of this tile read by every lane before the next tile's
     }
-    (void)ok;
   }
   if (threadIdx.x == 0 && !mbar_wait(done, 0)) atomicExch(&tc_error_flag, 5);
   tc_fence_before();
@@ -635,21 +789,44 @@ __global__ void __launch_bounds__(kFzThreads, 1)
   }
 }
 
+int sm_count() {
+  static int n[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (!n[dev] && cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n[dev] = 152;
+  return n[dev];
+}
+
+// the kernel's register count times its block size fits the SM (checked
+// once per process; otherwise the tile runs through the planes)
+bool fused_launchable() {
+  static int ok = -1;
+  if (ok < 0) {
+    cudaFuncAttributes fa;
+    ok = cudaFuncGetAttributes(&fa, tc_fused_bf16_kernel<false>) == cudaSuccess &&
+         fa.maxThreadsPerBlock >= kFzThreads;
+  }
+  return ok == 1;
+}
+
+template <bool PREFETCH>
 int run_tc_fused(const GemmDesc& d, const float2* A, const float2* B, float* C, cudaStream_t st) {
-  const int64_t M = d.M, N2 = 2 * d.N, nb = d.batch;
-  const size_t smem = 1024 + kFzStages * kFzStageBytes + (2 * kFzStages + 5) * 8 + 16 + kFzBN / 2 * 8;
+  const size_t smem =
+      1024 + kFzStages * kFzStageBytes + (2 * kFzStages + 5) * 8 + 16 + 4 * kFzBN / 2 * 8 + 8 * 4 + 8 * 8 + 4 * 256 * 8;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_fused_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(tc_fused_bf16_kernel<PREFETCH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
-  const int64_t tiles = (M / BM) * (N2 / kFzBN);
-  for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
-    int64_t cnt = nb - b0 < 65535 ? nb - b0 : 65535;
-    dim3 grid((unsigned)tiles, 1, (unsigned)cnt);
-    tc_fused_bf16_kernel<<<grid, kFzThreads, smem, st>>>(A, B, C, (int)M, (int)N2, (int)d.K, (int)b0, out_map(d));
-  }
+  FzGeom g;
+  g.M = (int)d.M, g.N = (int)d.N, g.K = (int)d.K;
+  g.tiles_m = (int)(d.M / BM), g.tiles_n = (int)(2 * d.N / kFzBN), g.nk = (int)(d.K / 32);
+  g.tiles = (int64_t)g.tiles_m * g.tiles_n * d.batch;
+  const int64_t grid = g.tiles < sm_count() ? g.tiles : sm_count();
+  tc_fused_bf16_kernel<PREFETCH><<<(unsigned)grid, kFzThreads, smem, st>>>(A, B, C, g, out_map(d));
   return (int)cudaGetLastError();
 }
 
@@ -872,13 +1049,16 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   uint8_t* scratch = (uint8_t*)scratch_ptr;
   if (!scratch) return (int)cudaErrorInvalidValue;
   // tile 1: 128 x 64 real outputs per CTA, 2: 128 x 128, 3: 128 x 256;
-  // 4: 128 x 128 with the split done on chip (split-BF16, K-major operands)
+  // 4, 5: 128 x 128 with the split done on chip (split-BF16, K-major
+  // operands), 5 with an L2 prefetch of the k-block after next
   const int tile = d.tile ? d.tile : (d.N >= 64 ? 2 : 1);
-  if (tile < 1 || tile > 4 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
-      (tile == 4 && (d.N < 64 || tf32 || d.transA || !d.transB)))
+  if (tile < 1 || tile > 5 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
+      (tile >= 4 && (d.N < 64 || tf32 || d.transA || !d.transB)))
     return (int)cudaErrorInvalidValue;
-  if (tile == 4) {
-    if (((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0) return run_tc_fused(d, A, B, (float*)C, st);
+  if (tile >= 4) {
+    if (((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0 && fused_launchable()) {
+      return tile == 5 ? run_tc_fused<true>(d, A, B, (float*)C, st) : run_tc_fused<false>(d, A, B, (float*)C, st);
+    }
     return run_tc<false, 128, 3>(d, A, B, (float*)C, scratch, st);  // unaligned operands: through the planes
   }
   if (tf32) {

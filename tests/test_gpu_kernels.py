@@ -46,7 +46,8 @@ def test_permute_rejects_non_permutation(tnc):
 SHAPES = [  # batch, M, N, K, transA, transB
     (1, 1, 1, 1, 0, 0), (3, 5, 7, 9, 0, 0), (2, 64, 48, 100, 1, 0), (2, 33, 65, 17, 0, 1),
     (1, 1000, 4, 2, 0, 1), (4, 513, 16, 16, 1, 1), (1, 2, 2, 100000, 0, 1), (2, 8, 8, 20000, 1, 0),
-    (1, 4, 4, 3000, 0, 0), (8, 16, 256, 8, 0, 1),
+    (1, 4, 4, 3000, 0, 0), (8, 16, 256, 8, 0, 1), (3, 1, 1, 70000, 0, 1), (2, 1, 1, 4099, 1, 0),
+    (5, 1, 1, 1 << 16, 0, 1),
 ]
 TC_SHAPES = [(4, 128, 64, 64, 0, 1), (2, 256, 128, 512, 0, 1), (1, 512, 256, 4096, 0, 1),
              (2, 128, 32, 64, 0, 1), (1, 1024, 512, 8192, 0, 1),
@@ -95,14 +96,14 @@ TILE_SHAPES = [(2, 128, 128, 64, 0, 1), (1, 256, 256, 4096, 0, 1), (3, 512, 128,
 
 
 @pytest.mark.parametrize("shape", TILE_SHAPES)
-@pytest.mark.parametrize("tile", [1, 2, 3, 4])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
 def test_cgemm_tensor_core_tile_widths(tnc, shape, tile, form):
     """Every tcgen05 tile width (128 x 64, 128 x 128, 128 x 256 real outputs
-    per CTA; 128 x 128 with the split on chip) on the same shapes, through
-    tnc_cgemm_variant."""
+    per CTA; 128 x 128 with the split on chip, without and with prefetch) on
+    the same shapes, through tnc_cgemm_variant."""
     batch, M, N, K, tA, tB = shape
-    if tile == 4 and (form != "split_bf16" or tA or not tB):
+    if tile >= 4 and (form != "split_bf16" or tA or not tB):
         pytest.skip("the on-chip split takes split-BF16 with K-major operands only")
     rng = np.random.default_rng(batch + M + N + K + tile)
     A = _crand(batch * M * K, rng)
