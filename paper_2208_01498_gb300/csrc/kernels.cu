@@ -146,7 +146,8 @@ struct TileOrder {
 __device__ __forceinline__ uint32_t tile_swz(uint32_t x) { return x ^ ((x >> 4) & 15u); }
 
 template <int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN), (BM * BN >= 8192) ? 1 : 2)
+__global__ void __launch_bounds__((BM / TM) * (BN / TN),
+                                  (BM * BN >= 8192) ? 1 : ((BM / TM) * (BN / TN) >= 256 ? 3 : 4))
     cgemm_simt_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
                       int64_t M, int64_t N, int64_t K, int transA, int transB, int64_t b0, int64_t kchunk,
                       int64_t part_stride, int staged, const __grid_constant__ OutMap om) {
