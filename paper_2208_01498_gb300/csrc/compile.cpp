@@ -107,8 +107,8 @@ void choose_gemm_kernel(GemmDesc& g) {
     // (the operands cross HBM once; long K prefetches the k-block after
     // next); very large M N re-read the operands from many tiles and run
     // faster from pre-split planes
-    if (g.form == TNC_SPLIT_BF16 && !g.transA && g.transB && g.N >= 64 && MN <= (double)(1 << 22))
-      g.tile = g.K >= 512 ? 5 : 4;
+    if (g.form == TNC_SPLIT_BF16 && !g.transA && g.transB && MN <= (double)(1 << 22))
+      g.tile = g.N >= 64 ? (g.K >= 512 ? 5 : 4) : (g.K >= 512 ? 7 : 6);
   }
   else if (g.N <= 32)
     g.kernel = KG_SIMT_64x32;
@@ -150,9 +150,13 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
     add(KG_TC, 1);
     if (g0.N >= 64) add(KG_TC, 2);
     if (g0.N >= 128) add(KG_TC, 3);
-    if (g0.form == TNC_SPLIT_BF16 && g0.N >= 64 && !g0.transA && g0.transB) {
-      add(KG_TC, 4);
-      add(KG_TC, 5);
+    if (g0.form == TNC_SPLIT_BF16 && !g0.transA && g0.transB) {
+      if (g0.N >= 64) {
+        add(KG_TC, 4);
+        add(KG_TC, 5);
+      }
+      add(KG_TC, 6);
+      add(KG_TC, 7);
     }
   }
   *n = k;

@@ -371,14 +371,15 @@ __global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
 // planes written, planes read back).
 //
 // Warps 0..3: accumulation and epilogue (TMEM lane quarter = warp); warp 4:
-// TMEM allocation and the MMA issuer (one lane); warps 5..16: converters.
+// TMEM allocation and the MMA issuer (one lane); warps 5 and up: converters
+// (12 for BN = 128 real output columns per CTA, 10 for BN = 64).
 // Finished accumulation chunks are added into a third TMEM region (the
 // running sum) instead of registers, so no thread holds a whole row.  The
 // register file is split between the SM's four sub-partitions (16K 32-bit
-// registers each); a 17-warp block puts 5 warps on one of them, which caps a
-// thread at 96 registers, and the converters are sized to fit that (one
-// k-block of loads in registers; the PREFETCH variant also sends the k-block
-// after next towards L2).  Two stages keep the block's shared memory under
+// registers each); the 17-warp block of BN = 128 puts 5 warps on one of them,
+// which caps a thread at 96 registers (the 15-warp BN = 64 block: 128), and
+// the converters are sized to fit that (one k-block of loads in registers;
+// the PREFETCH variant also sends the k-block after next towards L2).  Two stages keep the block's shared memory under
 // 196 KB: the SM's unified L1/shared storage then leaves about 90 KB of L1
 // for the converters' loads in flight (with three stages the carve-out rose
 // to 228 KB, L1 fell to 28 KB and the kernel ran 10-25 % slower).
@@ -386,12 +387,20 @@ __global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
 // memory into output order (BlockOrder) before storing.
 // Every wait is bounded as in tc_gemm_kernel; no asynchronous copies are in
 // flight at teardown (the converters' stores are synchronous).
-constexpr int kFzBN = 128;            // real output columns per CTA (64 complex)
 constexpr int kFzStages = 2;
-constexpr int kFzConvWarps = 12;   // 384 threads x 4 tasks = 1024 A + 512 B' chunks per k-block
-constexpr int kFzThreads = 32 * (5 + kFzConvWarps);
-constexpr uint32_t kFzTileBytes = BM * 128;                    // one plane tile: 128 rows x 64 bf16
-constexpr uint32_t kFzStageBytes = 4 * kFzTileBytes;            // A hi, A lo, B' hi, B' lo
+constexpr uint32_t kFzTileBytes = BM * 128;  // one A plane tile: 128 rows x 64 bf16
+
+// BN real output columns per CTA (BN / 2 complex): 128 or 64
+template <int BN>
+struct FzCfg {
+  static constexpr int kTasks = 1024 + 4 * BN;          // 16-byte chunks per k-block: A 128 x 8, B BN/2 x 8
+  static constexpr int kConvWarps = kTasks / 128;       // 4 tasks per converter thread: 12 or 10 warps
+  static constexpr int kConvThreads = 32 * kConvWarps;
+  static constexpr int kThreads = 32 * (5 + kConvWarps);
+  static constexpr uint32_t kBTileBytes = BN * 128;     // one B' plane tile: BN rows x 64 bf16
+  static constexpr uint32_t kStageBytes = 2 * kFzTileBytes + 2 * kBTileBytes;  // A hi, A lo, B' hi, B' lo
+  static constexpr int kTmemCols = 3 * BN <= 256 ? 256 : 512;                 // two slots + running sum
+};
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
   asm volatile(
@@ -476,10 +485,11 @@ struct BlockOrder {
 // the high 4, a bijection on 0..255
 __device__ __forceinline__ uint32_t stage_swz(uint32_t x) { return x ^ ((x >> 4) & 15u); }
 
-// One k-block of a converter thread: its 4 tasks (j = ct + 384 i) of 2 x 16
-// bytes each.  Task j < 1024: A tile row j / 8; otherwise complex column
-// (j - 1024) / 8 of B, giving B' rows 2n and 2n + 1.  Chunk j % 8 = ct % 8
-// in both cases.  1024 is a multiple of 32, so A/B tasks never mix in a warp.
+// One k-block of a converter thread: its 4 tasks (j = ct + T i, T = the
+// converter thread count, a multiple of 32 and of 8) of 2 x 16 bytes each.
+// Task j < 1024: A tile row j / 8; otherwise complex column (j - 1024) / 8 of
+// B, giving B' rows 2n and 2n + 1.  Chunk j % 8 = ct % 8 in both cases.  1024
+// is a multiple of 32, so A/B tasks never mix in a warp.
 struct FzRegs {
   float4 v[4][2];
 };
@@ -490,20 +500,22 @@ struct FzGeom {
 };
 
 // tile t -> (batch, first row, first real column); m-tiles fastest
+template <int BN>
 __device__ __forceinline__ void fz_tile(const FzGeom& g, int64_t t, int& bz, int& m0, int& n0) {
   const int64_t per_b = (int64_t)g.tiles_m * g.tiles_n;
   bz = (int)(t / per_b);
   const int r = (int)(t - (int64_t)bz * per_b);
   m0 = (r % g.tiles_m) * BM;
-  n0 = (r / g.tiles_m) * kFzBN;
+  n0 = (r / g.tiles_m) * BN;
 }
 
+template <int BN>
 __device__ __forceinline__ void fz_load(FzRegs& R, const float2* __restrict__ A, const float2* __restrict__ B,
                                         const FzGeom& g, int bz, int m0, int n0, int kb, int ct) {
   const int64_t koff = (int64_t)kb * 32 + 4 * (ct & 7);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int j = ct + 384 * i;
+    const int j = ct + FzCfg<BN>::kConvThreads * i;
     const float2* p = j < 1024 ? A + ((int64_t)bz * g.M + m0 + (j >> 3)) * g.K + koff
                                : B + ((int64_t)bz * g.N + n0 / 2 + ((j - 1024) >> 3)) * g.K + koff;
     R.v[i][0] = __ldg((const float4*)p);
@@ -513,24 +525,27 @@ __device__ __forceinline__ void fz_load(FzRegs& R, const float2* __restrict__ A,
 
 // L2 prefetch of a k-block's lines (one thread per 128-byte line), so that
 // a second k-block of loads is on its way without holding registers
+template <int BN>
 __device__ __forceinline__ void fz_prefetch(const float2* __restrict__ A, const float2* __restrict__ B,
                                             const FzGeom& g, int bz, int m0, int n0, int kb, int ct) {
   if (ct & 3) return;
   const int64_t koff = (int64_t)kb * 32 + 4 * (ct & 7);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int j = ct + 384 * i;
+    const int j = ct + FzCfg<BN>::kConvThreads * i;
     const float2* p = j < 1024 ? A + ((int64_t)bz * g.M + m0 + (j >> 3)) * g.K + koff
                                : B + ((int64_t)bz * g.N + n0 / 2 + ((j - 1024) >> 3)) * g.K + koff;
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
   }
 }
 
+template <int BN>
 __device__ __forceinline__ void fz_store(const FzRegs& R, uint32_t st, int ct) {
+  constexpr uint32_t kB = 2 * kFzTileBytes, kBl = kB + FzCfg<BN>::kBTileBytes;
   const int cc = ct & 7;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int j = ct + 384 * i;
+    const int j = ct + FzCfg<BN>::kConvThreads * i;
     uint32_t h[4], l[4];
     split_words(R.v[i][0], R.v[i][1], h, l);
     if (j < 1024) {
@@ -548,10 +563,10 @@ __device__ __forceinline__ void fz_store(const FzRegs& R, uint32_t st, int ct) {
         l1[q] = __byte_perm(l[q], 0, 0x1032);
       }
       const int r0 = 2 * ((j - 1024) >> 3);
-      sts128(st + 2 * kFzTileBytes + swz128(r0, cc), h0);
-      sts128(st + 3 * kFzTileBytes + swz128(r0, cc), l0);
-      sts128(st + 2 * kFzTileBytes + swz128(r0 + 1, cc), h1);
-      sts128(st + 3 * kFzTileBytes + swz128(r0 + 1, cc), l1);
+      sts128(st + kB + swz128(r0, cc), h0);
+      sts128(st + kBl + swz128(r0, cc), l0);
+      sts128(st + kB + swz128(r0 + 1, cc), h1);
+      sts128(st + kBl + swz128(r0 + 1, cc), l1);
     }
   }
 }
@@ -560,23 +575,24 @@ __device__ __forceinline__ void fz_store(const FzRegs& R, uint32_t st, int ct) {
 // ring, the two TMEM accumulator slots and their barriers run on across tile
 // boundaries, so a tile's epilogue overlaps the next tile's MMAs and the
 // converters keep two k-blocks of loads in flight through tile changes.
-template <bool PREFETCH>
-__global__ void __launch_bounds__(kFzThreads, 1)
+template <int BN, bool PREFETCH>
+__global__ void __launch_bounds__(FzCfg<BN>::kThreads, 1)
     tc_fused_bf16_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float* __restrict__ C,
                          const FzGeom geo, const __grid_constant__ OutMap om) {
   constexpr int CHUNK = 512 / 64;  // k-blocks (64 k') per accumulation chunk
-  constexpr uint32_t IDESC = instr_desc<false, kFzBN>();
+  constexpr uint32_t IDESC = instr_desc<false, BN>();
+  constexpr uint32_t kStageBytes = FzCfg<BN>::kStageBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + kFzStages * kFzStageBytes);
+  uint64_t* full = (uint64_t*)(smem + kFzStages * kStageBytes);
   uint64_t* empty = full + kFzStages;
   uint64_t* acc_full = empty + kFzStages;  // [2]
   uint64_t* acc_empty = acc_full + 2;      // [2]
   uint64_t* done = acc_empty + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   int* abort_flag = (int*)(tmem_slot + 1);
-  uint64_t* coltab = (uint64_t*)(tmem_slot + 4);  // [4 warps][kFzBN / 2]
-  uint32_t* blk_col = (uint32_t*)(coltab + 4 * (kFzBN / 2));  // [8] staging index of block column j
+  uint64_t* coltab = (uint64_t*)(tmem_slot + 4);  // [4 warps][BN / 2]
+  uint32_t* blk_col = (uint32_t*)(coltab + 4 * (BN / 2));  // [8] staging index of block column j
   uint64_t* blk_dep = (uint64_t*)(blk_col + 8);               // [8] output offset of staging index bits 5..7
   float2* stage_out = (float2*)(blk_dep + 8);                 // [4 warps][256]
 
@@ -588,7 +604,7 @@ __global__ void __launch_bounds__(kFzThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kFzStages; ++s) {
-      mbar_init(&full[s], 32 * kFzConvWarps);
+      mbar_init(&full[s], FzCfg<BN>::kConvThreads);
       mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
@@ -599,7 +615,7 @@ __global__ void __launch_bounds__(kFzThreads, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 4) tmem_alloc(tmem_slot, 512);  // slot 0, slot 1, running sum (128 columns each)
+  if (warp == 4) tmem_alloc(tmem_slot, FzCfg<BN>::kTmemCols);  // slot 0, slot 1, running sum (BN columns each)
   if (!om.ident && threadIdx.x < 8) {
     const BlockOrder bo(om);
     blk_col[threadIdx.x] = bo.index_col(threadIdx.x);
@@ -618,12 +634,12 @@ __global__ void __launch_bounds__(kFzThreads, 1)
     // load cursor: local tile lt_ld (coordinates bz, m0, n0), k-block kb_ld
     int64_t lt_ld = 0;
     int kb_ld = 0, bz = 0, m0 = 0, n0 = 0;
-    if (my_tiles > 0) fz_tile(geo, blockIdx.x, bz, m0, n0);
+    if (my_tiles > 0) fz_tile<BN>(geo, blockIdx.x, bz, m0, n0);
     auto load_next = [&](FzRegs& R) {
-      fz_load(R, A, B, geo, bz, m0, n0, kb_ld, ct);
+      fz_load<BN>(R, A, B, geo, bz, m0, n0, kb_ld, ct);
       if (++kb_ld == nk) {
         kb_ld = 0;
-        if (++lt_ld < my_tiles) fz_tile(geo, (int64_t)blockIdx.x + lt_ld * gridDim.x, bz, m0, n0);
+        if (++lt_ld < my_tiles) fz_tile<BN>(geo, (int64_t)blockIdx.x + lt_ld * gridDim.x, bz, m0, n0);
       }
     };
     if (total > 0) load_next(R0);
@@ -640,7 +656,7 @@ __global__ void __launch_bounds__(kFzThreads, 1)
         return false;
       }
       if (*(volatile int*)abort_flag) return false;
-      fz_store(R, smem_u32(smem + s * kFzStageBytes), ct);
+      fz_store<BN>(R, smem_u32(smem + s * kStageBytes), ct);
       // make the generic-proxy stores visible to the tensor core, then signal
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[s])) : "memory");
@@ -649,7 +665,7 @@ __global__ void __launch_bounds__(kFzThreads, 1)
         ph ^= 1u;
       }
       if (q + 1 < total) load_next(R);
-      if (PREFETCH && q + 2 < total) fz_prefetch(A, B, geo, bz, m0, n0, kb_ld, ct);  // cursor is at q + 2
+      if (PREFETCH && q + 2 < total) fz_prefetch<BN>(A, B, geo, bz, m0, n0, kb_ld, ct);  // cursor is at q + 2
       return true;
     };
     for (int64_t q = 0; q < total; ++q)
@@ -669,7 +685,7 @@ __global__ void __launch_bounds__(kFzThreads, 1)
             ok = false;
             break;
           }
-          const uint32_t dtm = tmem + slot * kFzBN;
+          const uint32_t dtm = tmem + slot * BN;
           const int kb_end = (c + 1) * CHUNK < nk ? (c + 1) * CHUNK : nk;
           for (int kb = c * CHUNK; kb < kb_end; ++kb) {
             if (!mbar_wait(&full[s], ph)) {
@@ -683,9 +699,10 @@ __global__ void __launch_bounds__(kFzThreads, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * kFzStageBytes);
+            const uint32_t sa = smem_u32(smem + s * kStageBytes);
             const uint64_t dAh = sw128_desc(sa), dAl = sw128_desc(sa + kFzTileBytes);
-            const uint64_t dBh = sw128_desc(sa + 2 * kFzTileBytes), dBl = sw128_desc(sa + 3 * kFzTileBytes);
+            const uint64_t dBh = sw128_desc(sa + 2 * kFzTileBytes);
+            const uint64_t dBl = sw128_desc(sa + 2 * kFzTileBytes + FzCfg<BN>::kBTileBytes);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
               const uint64_t adv = (uint64_t)((kk * 16 * 2) >> 4);
@@ -708,8 +725,8 @@ __global__ void __launch_bounds__(kFzThreads, 1)
   } else {
     // accumulation: row 32 warp + lane of each tile
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    const uint32_t tsum = tmem + lane_base + 2 * kFzBN;
-    uint64_t* ct = coltab + warp * (kFzBN / 2);
+    const uint32_t tsum = tmem + lane_base + 2 * BN;
+    uint64_t* ct = coltab + warp * (BN / 2);
     float2* so = stage_out + warp * 256;
     uint32_t idx_row = 0;
     uint64_t dep_lane = 0;
@@ -722,13 +739,11 @@ __global__ void __launch_bounds__(kFzThreads, 1)
     bool ok = true;
     for (int64_t lt = 0; lt < my_tiles && ok; ++lt) {
       int bz, m0, n0;
-      fz_tile(geo, (int64_t)blockIdx.x + lt * gridDim.x, bz, m0, n0);
+      fz_tile<BN>(geo, (int64_t)blockIdx.x + lt * gridDim.x, bz, m0, n0);
       const int row = m0 + warp * 32 + lane;
       const uint64_t roff = om.ident ? 0 : om.row(bz, m0 + warp * 32, geo.M, geo.N);  // lane bits clear
-      if (!om.ident) {
-        ct[lane] = om.col(n0 / 2 + lane);
-        ct[lane + 32] = om.col(n0 / 2 + lane + 32);
-      }
+      if (!om.ident)
+        for (int i = lane; i < BN / 2; i += 32) ct[i] = om.col(n0 / 2 + i);
       __syncwarp();
       for (int c = 0; c < nchunks; ++c, ++gc) {
         const int slot = (int)(gc & 1);
@@ -740,10 +755,10 @@ __global__ void __launch_bounds__(kFzThreads, 1)
         }
         tc_fence_after();
         const bool last = c == nchunks - 1;
-        const uint32_t tslot = tmem + lane_base + slot * kFzBN;
+        const uint32_t tslot = tmem + lane_base + slot * BN;
         const bool write_out = last && !*(volatile int*)abort_flag;
 #pragma unroll 1
-        for (int col = 0; col < kFzBN; col += 16) {
+        for (int col = 0; col < BN; col += 16) {
           float v[16];
           tmem_ld16(tslot + col, v);
           if (c > 0) {
@@ -785,7 +800,7 @@ __global__ void __launch_bounds__(kFzThreads, 1)
   __syncthreads();
   if (warp == 4) {
     tc_fence_after();
-    tmem_dealloc(tmem, 512);
+    tmem_dealloc(tmem, FzCfg<BN>::kTmemCols);
   }
 }
 
@@ -800,33 +815,34 @@ int sm_count() {
 
 // the kernel's register count times its block size fits the SM (checked
 // once per process; otherwise the tile runs through the planes)
+template <int BN>
 bool fused_launchable() {
   static int ok = -1;
   if (ok < 0) {
     cudaFuncAttributes fa;
-    ok = cudaFuncGetAttributes(&fa, tc_fused_bf16_kernel<false>) == cudaSuccess &&
-         fa.maxThreadsPerBlock >= kFzThreads;
+    ok = cudaFuncGetAttributes(&fa, tc_fused_bf16_kernel<BN, false>) == cudaSuccess &&
+         fa.maxThreadsPerBlock >= FzCfg<BN>::kThreads;
   }
   return ok == 1;
 }
 
-template <bool PREFETCH>
+template <int BN, bool PREFETCH>
 int run_tc_fused(const GemmDesc& d, const float2* A, const float2* B, float* C, cudaStream_t st) {
-  const size_t smem =
-      1024 + kFzStages * kFzStageBytes + (2 * kFzStages + 5) * 8 + 16 + 4 * kFzBN / 2 * 8 + 8 * 4 + 8 * 8 + 4 * 256 * 8;
+  const size_t smem = 1024 + kFzStages * FzCfg<BN>::kStageBytes + (2 * kFzStages + 5) * 8 + 16 + 4 * BN / 2 * 8 +
+                      8 * 4 + 8 * 8 + 4 * 256 * 8;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_fused_bf16_kernel<PREFETCH>,
+    cudaError_t e = cudaFuncSetAttribute(tc_fused_bf16_kernel<BN, PREFETCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
   FzGeom g;
   g.M = (int)d.M, g.N = (int)d.N, g.K = (int)d.K;
-  g.tiles_m = (int)(d.M / BM), g.tiles_n = (int)(2 * d.N / kFzBN), g.nk = (int)(d.K / 32);
+  g.tiles_m = (int)(d.M / BM), g.tiles_n = (int)(2 * d.N / BN), g.nk = (int)(d.K / 32);
   g.tiles = (int64_t)g.tiles_m * g.tiles_n * d.batch;
   const int64_t grid = g.tiles < sm_count() ? g.tiles : sm_count();
-  tc_fused_bf16_kernel<PREFETCH><<<(unsigned)grid, kFzThreads, smem, st>>>(A, B, C, g, out_map(d));
+  tc_fused_bf16_kernel<BN, PREFETCH><<<(unsigned)grid, FzCfg<BN>::kThreads, smem, st>>>(A, B, C, g, out_map(d));
   return (int)cudaGetLastError();
 }
 
@@ -1049,17 +1065,24 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   uint8_t* scratch = (uint8_t*)scratch_ptr;
   if (!scratch) return (int)cudaErrorInvalidValue;
   // tile 1: 128 x 64 real outputs per CTA, 2: 128 x 128, 3: 128 x 256;
-  // 4, 5: 128 x 128 with the split done on chip (split-BF16, K-major
-  // operands), 5 with an L2 prefetch of the k-block after next
+  // 4, 5: 128 x 128 and 6, 7: 128 x 64 with the split done on chip
+  // (split-BF16, K-major operands), 5 and 7 with an L2 prefetch of the
+  // k-block after next
   const int tile = d.tile ? d.tile : (d.N >= 64 ? 2 : 1);
-  if (tile < 1 || tile > 5 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
-      (tile >= 4 && (d.N < 64 || tf32 || d.transA || !d.transB)))
+  if (tile < 1 || tile > 7 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
+      (tile >= 4 && (tf32 || d.transA || !d.transB)) || ((tile == 4 || tile == 5) && d.N < 64))
     return (int)cudaErrorInvalidValue;
   if (tile >= 4) {
-    if (((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0 && fused_launchable()) {
-      return tile == 5 ? run_tc_fused<true>(d, A, B, (float*)C, st) : run_tc_fused<false>(d, A, B, (float*)C, st);
-    }
-    return run_tc<false, 128, 3>(d, A, B, (float*)C, scratch, st);  // unaligned operands: through the planes
+    const bool aligned = ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0;
+    if (aligned && tile <= 5 && fused_launchable<128>())
+      return tile == 5 ? run_tc_fused<128, true>(d, A, B, (float*)C, st)
+                       : run_tc_fused<128, false>(d, A, B, (float*)C, st);
+    if (aligned && tile >= 6 && fused_launchable<64>())
+      return tile == 7 ? run_tc_fused<64, true>(d, A, B, (float*)C, st)
+                       : run_tc_fused<64, false>(d, A, B, (float*)C, st);
+    // unaligned operands: through the planes
+    return d.N >= 64 ? run_tc<false, 128, 3>(d, A, B, (float*)C, scratch, st)
+                     : run_tc<false, 64, 4>(d, A, B, (float*)C, scratch, st);
   }
   if (tf32) {
     if (tile == 3) return run_tc<true, 256, 2>(d, A, B, (float*)C, scratch, st);
