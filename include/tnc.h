@@ -207,7 +207,8 @@ int tnc_cgemm(const void* d_A, const void* d_B, void* d_C, int64_t batch, int64_
 /* tnc_cgemm with the kernel variant named: kernel = TNC_KG_* below (-1: by
  * shape, as tnc_cgemm), tile = tensor-core tile width (1: 128 x 64 real
  * outputs per CTA, 2: 128 x 128, 3: 128 x 256; 4 and 5: 128 x 128, 6 and
- * 7: 128 x 64, with the split-BF16 split done on chip, persistent, for
+ * 7: 128 x 64, 8: 128 x 256 (K <= 256), with the split-BF16 split done on
+ * chip, persistent, for
  * K-major operands (transA = 0, transB = 1), 5 and 7 also prefetching the
  * k-block after next; these run through the hi/lo planes instead when an
  * operand is not 16-byte aligned; -1: any; 0 for the other kernels).  The variants are those a plan's autotuner may pick for the

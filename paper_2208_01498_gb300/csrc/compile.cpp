@@ -157,6 +157,7 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
       }
       add(KG_TC, 6);
       add(KG_TC, 7);
+      if (g0.N >= 128 && g0.K <= 256) add(KG_TC, 8);
     }
   }
   *n = k;

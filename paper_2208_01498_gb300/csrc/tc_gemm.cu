@@ -138,6 +138,18 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// the same for 64-byte rows with 64-byte swizzle (8-row groups 512 bytes
+// apart; 16-byte chunk c of row r at r * 64 + ((c ^ ((r / 2) % 4)) * 16))
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
+  d |= (uint64_t)(512 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)4 << 61;            // 64-byte swizzle
+  return d;
+}
+
 // instruction descriptor: D FP32, A/B BF16 (format 1) or TF32 (format 2),
 // both K-major, M = 128, N = BN
 template <bool kTF32, int BN>
@@ -364,15 +376,17 @@ __global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
 // The same 4M product, but without hi/lo planes in global memory: converter
 // warps read the complex64 operands (A [b][M][K], B [b][N][K]) straight from
 // global memory, split each value into bf16 hi + lo in registers and store
-// the A' and B'^T tiles into shared memory in the 128-byte-swizzled layout
-// the MMA descriptors read (16-byte chunk c of tile row r at
-// r * 128 + ((c ^ (r % 8)) * 16) within each 1024-byte group of 8 rows).
+// the A' and B'^T tiles into shared memory in the swizzled layout the MMA
+// descriptors read (128-byte rows: 16-byte chunk c of tile row r at
+// r * 128 + ((c ^ (r % 8)) * 16) within each 1024-byte group of 8 rows;
+// 64-byte rows: at r * 64 + ((c ^ ((r / 2) % 4)) * 16)).
 // Each operand byte then crosses HBM once instead of three times (read,
 // planes written, planes read back).
 //
 // Warps 0..3: accumulation and epilogue (TMEM lane quarter = warp); warp 4:
 // TMEM allocation and the MMA issuer (one lane); warps 5 and up: converters
-// (12 for BN = 128 real output columns per CTA, 10 for BN = 64).
+// (12 for BN = 128 real output columns per CTA, 10 for BN = 64, 8 for
+// BN = 256, whose 64-byte rows halve the converter work per k-block).
 // Finished accumulation chunks are added into a third TMEM region (the
 // running sum) instead of registers, so no thread holds a whole row.  The
 // register file is split between the SM's four sub-partitions (16K 32-bit
@@ -388,18 +402,33 @@ __global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
 // Every wait is bounded as in tc_gemm_kernel; no asynchronous copies are in
 // flight at teardown (the converters' stores are synchronous).
 constexpr int kFzStages = 2;
-constexpr uint32_t kFzTileBytes = BM * 128;  // one A plane tile: 128 rows x 64 bf16
 
-// BN real output columns per CTA (BN / 2 complex): 128 or 64
+// BN real output columns per CTA (BN / 2 complex): 64 or 128 with 128-byte
+// rows (64 k' per k-block) and a TMEM running sum; 256 with 64-byte rows
+// (32 k' per k-block, 64-byte swizzle), for K <= 256 only: one accumulation
+// chunk per tile, so two 256-column slots fill TMEM without a running sum.
 template <int BN>
 struct FzCfg {
-  static constexpr int kTasks = 1024 + 4 * BN;          // 16-byte chunks per k-block: A 128 x 8, B BN/2 x 8
-  static constexpr int kConvWarps = kTasks / 128;       // 4 tasks per converter thread: 12 or 10 warps
+  static constexpr int kRowBytes = BN == 256 ? 64 : 128;
+  static constexpr int kChunks = kRowBytes / 16;              // 16-byte chunks per row
+  static constexpr int kKC = kRowBytes / 4;                   // complex k per k-block
+  static constexpr int kKSteps = kRowBytes / 32;              // MMAs of K = 16 per k-block
+  static constexpr int kChunkKB = 512 / (kRowBytes / 2);      // k-blocks per 512 k' accumulation chunk
+  static constexpr int kATasks = 128 * kChunks;
+  static constexpr int kTasks = kATasks + (BN / 2) * kChunks;  // A 128 rows, B BN/2 complex rows
+  static constexpr int kConvWarps = kTasks / 128;             // 4 tasks per converter thread: 12, 10 or 8 warps
   static constexpr int kConvThreads = 32 * kConvWarps;
   static constexpr int kThreads = 32 * (5 + kConvWarps);
-  static constexpr uint32_t kBTileBytes = BN * 128;     // one B' plane tile: BN rows x 64 bf16
-  static constexpr uint32_t kStageBytes = 2 * kFzTileBytes + 2 * kBTileBytes;  // A hi, A lo, B' hi, B' lo
-  static constexpr int kTmemCols = 3 * BN <= 256 ? 256 : 512;                 // two slots + running sum
+  static constexpr uint32_t kATileBytes = 128 * kRowBytes;    // one A plane tile
+  static constexpr uint32_t kBTileBytes = BN * kRowBytes;     // one B' plane tile
+  static constexpr uint32_t kStageBytes = 2 * kATileBytes + 2 * kBTileBytes;  // A hi, A lo, B' hi, B' lo
+  static constexpr bool kSum = BN != 256;                     // TMEM running sum region
+  static constexpr int kTmemCols = BN == 256 ? 512 : (3 * BN <= 256 ? 256 : 512);
+  __device__ static uint32_t swz(int row, int chunk) {
+    if (kRowBytes == 128) return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+    return (uint32_t)(row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4));
+  }
+  __device__ static uint64_t desc(uint32_t saddr) { return kRowBytes == 128 ? sw128_desc(saddr) : sw64_desc(saddr); }
 };
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
@@ -412,10 +441,6 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
       "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
       "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
       : "memory");
-}
-
-__device__ __forceinline__ uint32_t swz128(int row, int chunk) {
-  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
 }
 
 // bf16 hi/lo words of 8 consecutive reals: word j packs elements 2j (low
@@ -486,10 +511,11 @@ struct BlockOrder {
 __device__ __forceinline__ uint32_t stage_swz(uint32_t x) { return x ^ ((x >> 4) & 15u); }
 
 // One k-block of a converter thread: its 4 tasks (j = ct + T i, T = the
-// converter thread count, a multiple of 32 and of 8) of 2 x 16 bytes each.
-// Task j < 1024: A tile row j / 8; otherwise complex column (j - 1024) / 8 of
-// B, giving B' rows 2n and 2n + 1.  Chunk j % 8 = ct % 8 in both cases.  1024
-// is a multiple of 32, so A/B tasks never mix in a warp.
+// converter thread count, a multiple of 32 and of the chunks per row C) of
+// 2 x 16 bytes each.  Task j < 128 C: A tile row j / C; otherwise complex
+// column (j - 128 C) / C of B, giving B' rows 2n and 2n + 1.  Chunk j % C =
+// ct % C in both cases.  128 C is a multiple of 32, so A/B tasks never mix in
+// a warp.
 struct FzRegs {
   float4 v[4][2];
 };
@@ -512,12 +538,13 @@ __device__ __forceinline__ void fz_tile(const FzGeom& g, int64_t t, int& bz, int
 template <int BN>
 __device__ __forceinline__ void fz_load(FzRegs& R, const float2* __restrict__ A, const float2* __restrict__ B,
                                         const FzGeom& g, int bz, int m0, int n0, int kb, int ct) {
-  const int64_t koff = (int64_t)kb * 32 + 4 * (ct & 7);
+  using Cf = FzCfg<BN>;
+  const int64_t koff = (int64_t)kb * Cf::kKC + 4 * (ct % Cf::kChunks);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int j = ct + FzCfg<BN>::kConvThreads * i;
-    const float2* p = j < 1024 ? A + ((int64_t)bz * g.M + m0 + (j >> 3)) * g.K + koff
-                               : B + ((int64_t)bz * g.N + n0 / 2 + ((j - 1024) >> 3)) * g.K + koff;
+    const int j = ct + Cf::kConvThreads * i;
+    const float2* p = j < Cf::kATasks ? A + ((int64_t)bz * g.M + m0 + j / Cf::kChunks) * g.K + koff
+                                      : B + ((int64_t)bz * g.N + n0 / 2 + (j - Cf::kATasks) / Cf::kChunks) * g.K + koff;
     R.v[i][0] = __ldg((const float4*)p);
     R.v[i][1] = __ldg((const float4*)p + 1);
   }
@@ -528,30 +555,32 @@ __device__ __forceinline__ void fz_load(FzRegs& R, const float2* __restrict__ A,
 template <int BN>
 __device__ __forceinline__ void fz_prefetch(const float2* __restrict__ A, const float2* __restrict__ B,
                                             const FzGeom& g, int bz, int m0, int n0, int kb, int ct) {
+  using Cf = FzCfg<BN>;
   if (ct & 3) return;
-  const int64_t koff = (int64_t)kb * 32 + 4 * (ct & 7);
+  const int64_t koff = (int64_t)kb * Cf::kKC + 4 * (ct % Cf::kChunks);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int j = ct + FzCfg<BN>::kConvThreads * i;
-    const float2* p = j < 1024 ? A + ((int64_t)bz * g.M + m0 + (j >> 3)) * g.K + koff
-                               : B + ((int64_t)bz * g.N + n0 / 2 + ((j - 1024) >> 3)) * g.K + koff;
+    const int j = ct + Cf::kConvThreads * i;
+    const float2* p = j < Cf::kATasks ? A + ((int64_t)bz * g.M + m0 + j / Cf::kChunks) * g.K + koff
+                                      : B + ((int64_t)bz * g.N + n0 / 2 + (j - Cf::kATasks) / Cf::kChunks) * g.K + koff;
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
   }
 }
 
 template <int BN>
 __device__ __forceinline__ void fz_store(const FzRegs& R, uint32_t st, int ct) {
-  constexpr uint32_t kB = 2 * kFzTileBytes, kBl = kB + FzCfg<BN>::kBTileBytes;
-  const int cc = ct & 7;
+  using Cf = FzCfg<BN>;
+  constexpr uint32_t kAl = Cf::kATileBytes, kB = 2 * Cf::kATileBytes, kBl = kB + Cf::kBTileBytes;
+  const int cc = ct % Cf::kChunks;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int j = ct + FzCfg<BN>::kConvThreads * i;
+    const int j = ct + Cf::kConvThreads * i;
     uint32_t h[4], l[4];
     split_words(R.v[i][0], R.v[i][1], h, l);
-    if (j < 1024) {
-      const uint32_t o = swz128(j >> 3, cc);
+    if (j < Cf::kATasks) {
+      const uint32_t o = Cf::swz(j / Cf::kChunks, cc);
       sts128(st + o, h);
-      sts128(st + kFzTileBytes + o, l);
+      sts128(st + kAl + o, l);
     } else {
       // words (br, bi) -> row 2n: (br, -bi), row 2n + 1: (bi, br)
       uint32_t h0[4], l0[4], h1[4], l1[4];
@@ -562,11 +591,11 @@ __device__ __forceinline__ void fz_store(const FzRegs& R, uint32_t st, int ct) {
         h1[q] = __byte_perm(h[q], 0, 0x1032);
         l1[q] = __byte_perm(l[q], 0, 0x1032);
       }
-      const int r0 = 2 * ((j - 1024) >> 3);
-      sts128(st + kB + swz128(r0, cc), h0);
-      sts128(st + kBl + swz128(r0, cc), l0);
-      sts128(st + kB + swz128(r0 + 1, cc), h1);
-      sts128(st + kBl + swz128(r0 + 1, cc), l1);
+      const int r0 = 2 * ((j - Cf::kATasks) / Cf::kChunks);
+      sts128(st + kB + Cf::swz(r0, cc), h0);
+      sts128(st + kBl + Cf::swz(r0, cc), l0);
+      sts128(st + kB + Cf::swz(r0 + 1, cc), h1);
+      sts128(st + kBl + Cf::swz(r0 + 1, cc), l1);
     }
   }
 }
@@ -579,7 +608,10 @@ template <int BN, bool PREFETCH>
 __global__ void __launch_bounds__(FzCfg<BN>::kThreads, 1)
     tc_fused_bf16_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float* __restrict__ C,
                          const FzGeom geo, const __grid_constant__ OutMap om) {
-  constexpr int CHUNK = 512 / 64;  // k-blocks (64 k') per accumulation chunk
+  using Cf = FzCfg<BN>;
+  // k-blocks per accumulation chunk (all of a tile's k-blocks without a
+  // running sum; the launcher admits only K <= 256 then)
+  constexpr int CHUNK = Cf::kSum ? Cf::kChunkKB : (1 << 30);
   constexpr uint32_t IDESC = instr_desc<false, BN>();
   constexpr uint32_t kStageBytes = FzCfg<BN>::kStageBytes;
   extern __shared__ uint8_t smem_raw[];
@@ -700,11 +732,11 @@ __global__ void __launch_bounds__(FzCfg<BN>::kThreads, 1)
             }
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + s * kStageBytes);
-            const uint64_t dAh = sw128_desc(sa), dAl = sw128_desc(sa + kFzTileBytes);
-            const uint64_t dBh = sw128_desc(sa + 2 * kFzTileBytes);
-            const uint64_t dBl = sw128_desc(sa + 2 * kFzTileBytes + FzCfg<BN>::kBTileBytes);
+            const uint64_t dAh = Cf::desc(sa), dAl = Cf::desc(sa + Cf::kATileBytes);
+            const uint64_t dBh = Cf::desc(sa + 2 * Cf::kATileBytes);
+            const uint64_t dBl = Cf::desc(sa + 2 * Cf::kATileBytes + Cf::kBTileBytes);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
+            for (int kk = 0; kk < Cf::kKSteps; ++kk) {
               const uint64_t adv = (uint64_t)((kk * 16 * 2) >> 4);
               const uint32_t first = (kb == c * CHUNK && kk == 0) ? 0u : 1u;
               mma<false>(dtm, dAh + adv, dBh + adv, IDESC, first);
@@ -828,8 +860,10 @@ bool fused_launchable() {
 
 template <int BN, bool PREFETCH>
 int run_tc_fused(const GemmDesc& d, const float2* A, const float2* B, float* C, cudaStream_t st) {
-  const size_t smem = 1024 + kFzStages * FzCfg<BN>::kStageBytes + (2 * kFzStages + 5) * 8 + 16 + 4 * BN / 2 * 8 +
+  // at least 117 KB so that one CTA (and one TMEM allocation) holds an SM
+  const size_t need = 1024 + kFzStages * FzCfg<BN>::kStageBytes + (2 * kFzStages + 5) * 8 + 16 + 4 * BN / 2 * 8 +
                       8 * 4 + 8 * 8 + 4 * 256 * 8;
+  const size_t smem = need > 117 * 1024 ? need : 117 * 1024;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(tc_fused_bf16_kernel<BN, PREFETCH>,
@@ -839,7 +873,7 @@ int run_tc_fused(const GemmDesc& d, const float2* A, const float2* B, float* C, 
   }
   FzGeom g;
   g.M = (int)d.M, g.N = (int)d.N, g.K = (int)d.K;
-  g.tiles_m = (int)(d.M / BM), g.tiles_n = (int)(2 * d.N / BN), g.nk = (int)(d.K / 32);
+  g.tiles_m = (int)(d.M / BM), g.tiles_n = (int)(2 * d.N / BN), g.nk = (int)(d.K / FzCfg<BN>::kKC);
   g.tiles = (int64_t)g.tiles_m * g.tiles_n * d.batch;
   const int64_t grid = g.tiles < sm_count() ? g.tiles : sm_count();
   tc_fused_bf16_kernel<BN, PREFETCH><<<(unsigned)grid, FzCfg<BN>::kThreads, smem, st>>>(A, B, C, g, out_map(d));
@@ -1065,21 +1099,23 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   uint8_t* scratch = (uint8_t*)scratch_ptr;
   if (!scratch) return (int)cudaErrorInvalidValue;
   // tile 1: 128 x 64 real outputs per CTA, 2: 128 x 128, 3: 128 x 256;
-  // 4, 5: 128 x 128 and 6, 7: 128 x 64 with the split done on chip
-  // (split-BF16, K-major operands), 5 and 7 with an L2 prefetch of the
-  // k-block after next
+  // 4, 5: 128 x 128, 6, 7: 128 x 64 and 8: 128 x 256 (K <= 256) with the
+  // split done on chip (split-BF16, K-major operands), 5 and 7 with an L2
+  // prefetch of the k-block after next
   const int tile = d.tile ? d.tile : (d.N >= 64 ? 2 : 1);
-  if (tile < 1 || tile > 7 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
-      (tile >= 4 && (tf32 || d.transA || !d.transB)) || ((tile == 4 || tile == 5) && d.N < 64))
+  if (tile < 1 || tile > 8 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
+      (tile >= 4 && (tf32 || d.transA || !d.transB)) || ((tile == 4 || tile == 5) && d.N < 64) ||
+      (tile == 8 && (d.N < 128 || d.K > 256)))
     return (int)cudaErrorInvalidValue;
   if (tile >= 4) {
     const bool aligned = ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0;
     if (aligned && tile <= 5 && fused_launchable<128>())
       return tile == 5 ? run_tc_fused<128, true>(d, A, B, (float*)C, st)
                        : run_tc_fused<128, false>(d, A, B, (float*)C, st);
-    if (aligned && tile >= 6 && fused_launchable<64>())
+    if (aligned && (tile == 6 || tile == 7) && fused_launchable<64>())
       return tile == 7 ? run_tc_fused<64, true>(d, A, B, (float*)C, st)
                        : run_tc_fused<64, false>(d, A, B, (float*)C, st);
+    if (aligned && tile == 8 && fused_launchable<256>()) return run_tc_fused<256, false>(d, A, B, (float*)C, st);
     // unaligned operands: through the planes
     return d.N >= 64 ? run_tc<false, 128, 3>(d, A, B, (float*)C, scratch, st)
                      : run_tc<false, 64, 4>(d, A, B, (float*)C, scratch, st);

@@ -93,11 +93,11 @@ def test_cgemm_scratch_too_small(tnc):
 
 
 TILE_SHAPES = [(2, 128, 128, 64, 0, 1), (1, 256, 256, 4096, 0, 1), (3, 512, 128, 128, 0, 1), (1, 256, 512, 1024, 1, 0),
-               (4, 256, 32, 128, 0, 1), (2, 128, 64, 1024, 0, 1)]
+               (4, 256, 32, 128, 0, 1), (2, 128, 64, 1024, 0, 1), (2, 256, 512, 256, 0, 1), (3, 128, 256, 32, 0, 1)]
 
 
 @pytest.mark.parametrize("shape", TILE_SHAPES)
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
 def test_cgemm_tensor_core_tile_widths(tnc, shape, tile, form):
     """Every tcgen05 tile width (128 x 64, 128 x 128, 128 x 256 real outputs
@@ -106,8 +106,10 @@ def test_cgemm_tensor_core_tile_widths(tnc, shape, tile, form):
     batch, M, N, K, tA, tB = shape
     if tile >= 4 and (form != "split_bf16" or tA or not tB):
         pytest.skip("the on-chip split takes split-BF16 with K-major operands only")
-    if (tile == 2 and N < 64) or (tile == 3 and N < 128) or (tile in (4, 5) and N < 64):
+    if (tile == 2 and N < 64) or (tile in (3, 8) and N < 128) or (tile in (4, 5) and N < 64):
         pytest.skip("tile wider than N")
+    if tile == 8 and K > 256:
+        pytest.skip("the 256-column on-chip split takes K <= 256")
     rng = np.random.default_rng(batch + M + N + K + tile)
     A = _crand(batch * M * K, rng)
     B = _crand(batch * K * N, rng)
