@@ -211,7 +211,9 @@ int tnc_cgemm(const void* d_A, const void* d_B, void* d_C, int64_t batch, int64_
  * chip, persistent, for
  * K-major operands (transA = 0, transB = 1), 5 and 7 also prefetching the
  * k-block after next; these run through the hi/lo planes instead when an
- * operand is not 16-byte aligned; -1: any; 0 for the other kernels).  The variants are those a plan's autotuner may pick for the
+ * operand is not 16-byte aligned; 9: 128 x 256 (K <= 256) and 10: 128 x 128,
+ * split-BF16 from the hi/lo planes in a persistent kernel; -1: any; 0 for
+ * the other kernels).  The variants are those a plan's autotuner may pick for the
  * shape; TNC_EINVAL for one that cannot run it. */
 #define TNC_KG_SIMT_128x64 0
 #define TNC_KG_SIMT_64x32 1

@@ -159,6 +159,8 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
       add(KG_TC, 7);
       if (g0.N >= 128 && g0.K <= 256) add(KG_TC, 8);
     }
+    if (g0.form == TNC_SPLIT_BF16 && g0.N >= 64) add(KG_TC, 10);
+    if (g0.form == TNC_SPLIT_BF16 && g0.N >= 128 && g0.K <= 256) add(KG_TC, 9);
   }
   *n = k;
 }

@@ -409,6 +409,8 @@ constexpr int kFzStages = 2;
 // chunk per tile, so two 256-column slots fill TMEM without a running sum.
 template <int BN>
 struct FzCfg {
+  static constexpr int kBN = BN;
+  static constexpr bool kPlanes = false;
   static constexpr int kRowBytes = BN == 256 ? 64 : 128;
   static constexpr int kChunks = kRowBytes / 16;              // 16-byte chunks per row
   static constexpr int kKC = kRowBytes / 4;                   // complex k per k-block
@@ -419,6 +421,7 @@ struct FzCfg {
   static constexpr int kConvWarps = kTasks / 128;             // 4 tasks per converter thread: 12, 10 or 8 warps
   static constexpr int kConvThreads = 32 * kConvWarps;
   static constexpr int kThreads = 32 * (5 + kConvWarps);
+  static constexpr int kFullArrivals = kConvThreads;          // arrivals completing a stage
   static constexpr uint32_t kATileBytes = 128 * kRowBytes;    // one A plane tile
   static constexpr uint32_t kBTileBytes = BN * kRowBytes;     // one B' plane tile
   static constexpr uint32_t kStageBytes = 2 * kATileBytes + 2 * kBTileBytes;  // A hi, A lo, B' hi, B' lo
@@ -461,6 +464,31 @@ __device__ __forceinline__ void sts128(uint32_t addr, const uint32_t* w) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
                : "memory");
 }
+
+// The same persistent pipeline fed by TMA from pre-split hi/lo planes
+// (written by prep_a_vec / prep_b_vec): 128-byte rows (64 k' per k-block),
+// one producer warp instead of the converters.  BN = 256 has no running sum
+// (one accumulation chunk per tile: K <= 256).
+template <int BN>
+struct PlCfg {
+  static constexpr int kBN = BN;
+  static constexpr bool kPlanes = true;
+  static constexpr int kKC = 32;  // complex k per k-block (128-byte rows of bf16)
+  static constexpr int kKSteps = 4;
+  static constexpr int kChunkKB = 8;
+  static constexpr int kThreads = 32 * 6;
+  static constexpr int kFullArrivals = 1;  // the producer's expect_tx arrival; the bytes complete it
+  static constexpr uint32_t kATileBytes = 128 * 128;
+  static constexpr uint32_t kBTileBytes = BN * 128;
+  static constexpr uint32_t kStageBytes = 2 * kATileBytes + 2 * kBTileBytes;
+  static constexpr bool kSum = BN != 256;
+  static constexpr int kTmemCols = BN == 256 ? 512 : (3 * BN <= 256 ? 256 : 512);
+  __device__ static uint64_t desc(uint32_t saddr) { return sw128_desc(saddr); }
+};
+
+struct PlMaps {
+  CUtensorMap ah, al, bh, bl;
+};
 
 // Output order of one warp's epilogue block: 32 rows (m bits 0..4, from the
 // lane) x 8 complex columns (n bits 0..2).  The consumer's layout puts these
@@ -604,16 +632,16 @@ __device__ __forceinline__ void fz_store(const FzRegs& R, uint32_t st, int ct) {
 // ring, the two TMEM accumulator slots and their barriers run on across tile
 // boundaries, so a tile's epilogue overlaps the next tile's MMAs and the
 // converters keep two k-blocks of loads in flight through tile changes.
-template <int BN, bool PREFETCH>
-__global__ void __launch_bounds__(FzCfg<BN>::kThreads, 1)
+template <class Cf, bool PREFETCH>
+__global__ void __launch_bounds__(Cf::kThreads, 1)
     tc_fused_bf16_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float* __restrict__ C,
-                         const FzGeom geo, const __grid_constant__ OutMap om) {
-  using Cf = FzCfg<BN>;
+                         const FzGeom geo, const __grid_constant__ OutMap om, const __grid_constant__ PlMaps maps) {
+  constexpr int BN = Cf::kBN;
   // k-blocks per accumulation chunk (all of a tile's k-blocks without a
   // running sum; the launcher admits only K <= 256 then)
   constexpr int CHUNK = Cf::kSum ? Cf::kChunkKB : (1 << 30);
   constexpr uint32_t IDESC = instr_desc<false, BN>();
-  constexpr uint32_t kStageBytes = FzCfg<BN>::kStageBytes;
+  constexpr uint32_t kStageBytes = Cf::kStageBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + kFzStages * kStageBytes);
@@ -636,7 +664,7 @@ __global__ void __launch_bounds__(FzCfg<BN>::kThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kFzStages; ++s) {
-      mbar_init(&full[s], FzCfg<BN>::kConvThreads);
+      mbar_init(&full[s], Cf::kFullArrivals);
       mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
@@ -647,7 +675,7 @@ __global__ void __launch_bounds__(FzCfg<BN>::kThreads, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 4) tmem_alloc(tmem_slot, FzCfg<BN>::kTmemCols);  // slot 0, slot 1, running sum (BN columns each)
+  if (warp == 4) tmem_alloc(tmem_slot, Cf::kTmemCols);  // slot 0, slot 1, running sum (BN columns each)
   if (!om.ident && threadIdx.x < 8) {
     const BlockOrder bo(om);
     blk_col[threadIdx.x] = bo.index_col(threadIdx.x);
@@ -658,7 +686,43 @@ __global__ void __launch_bounds__(FzCfg<BN>::kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp >= 5) {
+  int64_t tma_issued = 0;  // planes: k-blocks whose TMA loads were issued
+  if (Cf::kPlanes && warp == 5) {
+    // producer: TMA loads of the hi/lo plane tiles of every k-block
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      for (int64_t lt = 0; lt < my_tiles; ++lt) {
+        int bz, m0, n0;
+        fz_tile<BN>(geo, (int64_t)blockIdx.x + lt * gridDim.x, bz, m0, n0);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb) {
+          if (tma_issued >= kFzStages && !mbar_wait(&empty[s], ph ^ 1u)) {
+            atomicExch(&tc_error_flag, 7);
+            *(volatile int*)abort_flag = 1;
+            ok = false;
+            break;
+          }
+          if (*(volatile int*)abort_flag) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * kStageBytes;
+          mbar_expect_tx(&full[s], kStageBytes);
+          tma_load_3d(st, &maps.ah, &full[s], kb * 64, m0, bz);
+          tma_load_3d(st + Cf::kATileBytes, &maps.al, &full[s], kb * 64, m0, bz);
+          tma_load_3d(st + 2 * Cf::kATileBytes, &maps.bh, &full[s], kb * 64, n0, bz);
+          tma_load_3d(st + 2 * Cf::kATileBytes + Cf::kBTileBytes, &maps.bl, &full[s], kb * 64, n0, bz);
+          ++tma_issued;
+          if (++s == kFzStages) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (!Cf::kPlanes && warp >= 5) {
     // converters: global k-block q = (local tile) * nk + kb
     const int ct = threadIdx.x - 160;
     const int64_t total = my_tiles * nk;
@@ -830,9 +894,15 @@ __global__ void __launch_bounds__(FzCfg<BN>::kThreads, 1)
   if (threadIdx.x == 0 && !mbar_wait(done, 0)) atomicExch(&tc_error_flag, 5);
   tc_fence_before();
   __syncthreads();
+  // planes, after an abort: wait (bounded) for the TMA copies still in flight
+  if (Cf::kPlanes && warp == 5 && lane == 0 && *(volatile int*)abort_flag) {
+    for (int64_t q = (tma_issued > kFzStages ? tma_issued - kFzStages : 0); q < tma_issued; ++q)
+      mbar_wait(&full[q % kFzStages], (uint32_t)((q / kFzStages) & 1));
+  }
+  __syncthreads();
   if (warp == 4) {
     tc_fence_after();
-    tmem_dealloc(tmem, FzCfg<BN>::kTmemCols);
+    tmem_dealloc(tmem, Cf::kTmemCols);
   }
 }
 
@@ -852,32 +922,41 @@ bool fused_launchable() {
   static int ok = -1;
   if (ok < 0) {
     cudaFuncAttributes fa;
-    ok = cudaFuncGetAttributes(&fa, tc_fused_bf16_kernel<BN, false>) == cudaSuccess &&
+    ok = cudaFuncGetAttributes(&fa, tc_fused_bf16_kernel<FzCfg<BN>, false>) == cudaSuccess &&
          fa.maxThreadsPerBlock >= FzCfg<BN>::kThreads;
   }
   return ok == 1;
 }
 
-template <int BN, bool PREFETCH>
-int run_tc_fused(const GemmDesc& d, const float2* A, const float2* B, float* C, cudaStream_t st) {
+template <class Cf, bool PREFETCH>
+int launch_persistent(const GemmDesc& d, const float2* A, const float2* B, float* C, const PlMaps& maps,
+                      cudaStream_t st) {
+  constexpr int BN = Cf::kBN;
   // at least 117 KB so that one CTA (and one TMEM allocation) holds an SM
-  const size_t need = 1024 + kFzStages * FzCfg<BN>::kStageBytes + (2 * kFzStages + 5) * 8 + 16 + 4 * BN / 2 * 8 +
-                      8 * 4 + 8 * 8 + 4 * 256 * 8;
+  const size_t need = 1024 + kFzStages * Cf::kStageBytes + (2 * kFzStages + 5) * 8 + 16 + 4 * BN / 2 * 8 + 8 * 4 +
+                      8 * 8 + 4 * 256 * 8;
   const size_t smem = need > 117 * 1024 ? need : 117 * 1024;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_fused_bf16_kernel<BN, PREFETCH>,
+    cudaError_t e = cudaFuncSetAttribute(tc_fused_bf16_kernel<Cf, PREFETCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
   FzGeom g;
   g.M = (int)d.M, g.N = (int)d.N, g.K = (int)d.K;
-  g.tiles_m = (int)(d.M / BM), g.tiles_n = (int)(2 * d.N / BN), g.nk = (int)(d.K / FzCfg<BN>::kKC);
+  g.tiles_m = (int)(d.M / BM), g.tiles_n = (int)(2 * d.N / BN), g.nk = (int)(d.K / Cf::kKC);
   g.tiles = (int64_t)g.tiles_m * g.tiles_n * d.batch;
   const int64_t grid = g.tiles < sm_count() ? g.tiles : sm_count();
-  tc_fused_bf16_kernel<BN, PREFETCH><<<(unsigned)grid, FzCfg<BN>::kThreads, smem, st>>>(A, B, C, g, out_map(d));
+  tc_fused_bf16_kernel<Cf, PREFETCH><<<(unsigned)grid, Cf::kThreads, smem, st>>>(A, B, C, g, out_map(d), maps);
   return (int)cudaGetLastError();
+}
+
+template <int BN, bool PREFETCH>
+int run_tc_fused(const GemmDesc& d, const float2* A, const float2* B, float* C, cudaStream_t st) {
+  PlMaps none;
+  std::memset(&none, 0, sizeof(none));
+  return launch_persistent<FzCfg<BN>, PREFETCH>(d, A, B, C, none, st);
 }
 
 // ------------------------------------------------------------ prep kernels
@@ -1038,8 +1117,11 @@ int make_map(CUtensorMap* m, void* base, bool tf32, int64_t cols, int64_t rows, 
   return r == CUDA_SUCCESS ? 0 : (int)cudaErrorInvalidValue;
 }
 
-template <bool kTF32, int BN, int STAGES>
-int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_t* scratch, cudaStream_t st) {
+// hi/lo planes of A' and B'^T in the scratch and TMA maps over them (boxes
+// of 128-byte rows x 128 (A) or box_n (B) rows)
+template <bool kTF32>
+int prep_planes(const GemmDesc& d, const float2* A, const float2* B, uint8_t* scratch, int box_n, PlMaps& maps,
+                cudaStream_t st) {
   const int64_t M = d.M, N2 = 2 * d.N, K2 = 2 * d.K, nb = d.batch;
   const int es = kTF32 ? 4 : 2;
   uint8_t* a_hi = scratch;
@@ -1058,12 +1140,30 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
                                                              __builtin_ctzll((unsigned long long)d.K));
   else
     prep_b_kernel<kTF32><<<blocks(nbb), 256, 0, st>>>(B, b_hi, b_lo, d.N, d.K, nbb, d.transB);
-  CUtensorMap mAh, mAl, mBh, mBl;
   int r;
-  if ((r = make_map(&mAh, a_hi, kTF32, K2, M, nb, BM))) return r;
-  if ((r = make_map(&mAl, a_lo, kTF32, K2, M, nb, BM))) return r;
-  if ((r = make_map(&mBh, b_hi, kTF32, K2, N2, nb, BN))) return r;
-  if ((r = make_map(&mBl, b_lo, kTF32, K2, N2, nb, BN))) return r;
+  if ((r = make_map(&maps.ah, a_hi, kTF32, K2, M, nb, BM))) return r;
+  if ((r = make_map(&maps.al, a_lo, kTF32, K2, M, nb, BM))) return r;
+  if ((r = make_map(&maps.bh, b_hi, kTF32, K2, N2, nb, box_n))) return r;
+  if ((r = make_map(&maps.bl, b_lo, kTF32, K2, N2, nb, box_n))) return r;
+  return 0;
+}
+
+// persistent TMA-fed variant (split-BF16)
+template <int BN>
+int run_tc_planes(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_t* scratch, cudaStream_t st) {
+  PlMaps maps;
+  int r = prep_planes<false>(d, A, B, scratch, BN, maps, st);
+  if (r) return r;
+  return launch_persistent<PlCfg<BN>, false>(d, A, B, C, maps, st);
+}
+
+template <bool kTF32, int BN, int STAGES>
+int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_t* scratch, cudaStream_t st) {
+  const int64_t M = d.M, N2 = 2 * d.N, K2 = 2 * d.K, nb = d.batch;
+  PlMaps maps;
+  int r = prep_planes<kTF32>(d, A, B, scratch, BN, maps, st);
+  if (r) return r;
+  const CUtensorMap &mAh = maps.ah, &mAl = maps.al, &mBh = maps.bh, &mBl = maps.bl;
   constexpr uint32_t STAGE_BYTES = 2 * BM * 128 + 2 * BN * 128;
   const size_t smem = 1024 + STAGES * STAGE_BYTES + (2 * STAGES + 5) * 8 + 16 + BN / 2 * 8;
   static bool attr_set = false;
@@ -1101,12 +1201,15 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   // tile 1: 128 x 64 real outputs per CTA, 2: 128 x 128, 3: 128 x 256;
   // 4, 5: 128 x 128, 6, 7: 128 x 64 and 8: 128 x 256 (K <= 256) with the
   // split done on chip (split-BF16, K-major operands), 5 and 7 with an L2
-  // prefetch of the k-block after next
+  // prefetch of the k-block after next; 9: 128 x 256 (K <= 256) and
+  // 10: 128 x 128, persistent from the planes (split-BF16)
   const int tile = d.tile ? d.tile : (d.N >= 64 ? 2 : 1);
-  if (tile < 1 || tile > 8 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
-      (tile >= 4 && (tf32 || d.transA || !d.transB)) || ((tile == 4 || tile == 5) && d.N < 64) ||
-      (tile == 8 && (d.N < 128 || d.K > 256)))
+  if (tile < 1 || tile > 10 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
+      (tile >= 4 && tile <= 8 && (d.transA || !d.transB)) || (tile >= 4 && tf32) ||
+      ((tile == 4 || tile == 5 || tile == 10) && d.N < 64) || ((tile == 8 || tile == 9) && (d.N < 128 || d.K > 256)))
     return (int)cudaErrorInvalidValue;
+  if (tile == 9) return run_tc_planes<256>(d, A, B, (float*)C, scratch, st);
+  if (tile == 10) return run_tc_planes<128>(d, A, B, (float*)C, scratch, st);
   if (tile >= 4) {
     const bool aligned = ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0;
     if (aligned && tile <= 5 && fused_launchable<128>())

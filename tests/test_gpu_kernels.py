@@ -97,19 +97,22 @@ TILE_SHAPES = [(2, 128, 128, 64, 0, 1), (1, 256, 256, 4096, 0, 1), (3, 512, 128,
 
 
 @pytest.mark.parametrize("shape", TILE_SHAPES)
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 @pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
 def test_cgemm_tensor_core_tile_widths(tnc, shape, tile, form):
     """Every tcgen05 tile width (128 x 64, 128 x 128, 128 x 256 real outputs
-    per CTA; 128 x 128 and 128 x 64 with the split on chip, without and with
-    prefetch) on the same shapes, through tnc_cgemm_variant."""
+    per CTA; 128 x 128, 128 x 64 and 128 x 256 with the split on chip,
+    without and with prefetch; 128 x 256 and 128 x 128 persistent from the
+    planes) on the same shapes, through tnc_cgemm_variant."""
     batch, M, N, K, tA, tB = shape
-    if tile >= 4 and (form != "split_bf16" or tA or not tB):
+    if 4 <= tile <= 8 and (form != "split_bf16" or tA or not tB):
         pytest.skip("the on-chip split takes split-BF16 with K-major operands only")
-    if (tile == 2 and N < 64) or (tile in (3, 8) and N < 128) or (tile in (4, 5) and N < 64):
+    if tile >= 9 and form != "split_bf16":
+        pytest.skip("the persistent plane kernel takes split-BF16 only")
+    if (tile == 2 and N < 64) or (tile in (3, 8, 9) and N < 128) or (tile in (4, 5, 10) and N < 64):
         pytest.skip("tile wider than N")
-    if tile == 8 and K > 256:
-        pytest.skip("the 256-column on-chip split takes K <= 256")
+    if tile in (8, 9) and K > 256:
+        pytest.skip("the 256-column persistent tiles take K <= 256")
     rng = np.random.default_rng(batch + M + N + K + tile)
     A = _crand(batch * M * K, rng)
     B = _crand(batch * K * N, rng)
