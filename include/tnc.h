@@ -214,7 +214,12 @@ int tnc_cgemm(const void* d_A, const void* d_B, void* d_C, int64_t batch, int64_
  * operand is not 16-byte aligned; 9: 128 x 256 (K <= 256) and 10: 128 x 128,
  * split-BF16 from the hi/lo planes in a persistent kernel; -1: any; 0 for
  * the other kernels).  The variants are those a plan's autotuner may pick for the
- * shape; TNC_EINVAL for one that cannot run it. */
+ * shape; TNC_EINVAL for one that cannot run it.  c_pos (HOST, may be NULL):
+ * C stored in a consumer's bit order, as in a plan: with nN = log2 N,
+ * nM = log2 M, nB = log2 batch (all powers of two), bit i of n goes to output
+ * bit c_pos[i], bit i of m to c_pos[nN + i], bit i of b to c_pos[nN + nM + i];
+ * c_pos must be a permutation of 0 .. nN + nM + nB - 1 (TNC_EINVAL otherwise).
+ * NULL = [b][M][N]. */
 #define TNC_KG_SIMT_128x64 0
 #define TNC_KG_SIMT_64x32 1
 #define TNC_KG_NARROW 2
@@ -222,8 +227,8 @@ int tnc_cgemm(const void* d_A, const void* d_B, void* d_C, int64_t batch, int64_
 #define TNC_KG_TC 4
 #define TNC_KG_SIMT_32x128 5
 int tnc_cgemm_variant(const void* d_A, const void* d_B, void* d_C, int64_t batch, int64_t M, int64_t N, int64_t K,
-                      int transA, int transB, int form, int kernel, int tile, void* d_scratch, size_t scratch_bytes,
-                      void* cuda_stream);
+                      int transA, int transB, int form, int kernel, int tile, const int* c_pos, void* d_scratch,
+                      size_t scratch_bytes, void* cuda_stream);
 
 /* Device-side error flag of the kernels with bounded waits (the tcgen05
  * pipeline): 0 if no wait has timed out on the current device since load,

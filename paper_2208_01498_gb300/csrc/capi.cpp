@@ -656,14 +656,38 @@ size_t tnc_cgemm_scratch_bytes(int64_t batch, int64_t M, int64_t N, int64_t K, i
 }
 
 int tnc_cgemm_variant(const void* A, const void* B, void* Cp, int64_t batch, int64_t M, int64_t N, int64_t K,
-                      int tA, int tB, int form, int kernel, int tile, void* scratch, size_t scratch_bytes,
-                      void* stream) {
+                      int tA, int tB, int form, int kernel, int tile, const int* c_pos, void* scratch,
+                      size_t scratch_bytes, void* stream) {
   if (!A || !B || !Cp || batch < 1 || M < 1 || N < 1 || K < 1 || form < 0 || form > 2 || (tA & ~1) ||
       (tB & ~1)) {
     set_error("tnc_cgemm: invalid argument");
     return TNC_EINVAL;
   }
   GemmDesc g = make_gemm(batch, M, N, K, tA, tB, form);
+  if (c_pos) {
+    // C stored as a permutation of the bits of [b][M][N] (powers of two)
+    auto lg = [](int64_t v) { int r = 0; while (((int64_t)1 << r) < v) ++r; return ((int64_t)1 << r) == v ? r : -1; };
+    const int nN = lg(N), nM = lg(M), nB = lg(batch);
+    const int nb = nN + nM + nB;
+    if (nN < 0 || nM < 0 || nB < 0 || nb > kMaxRank) {
+      set_error("tnc_cgemm_variant: c_pos needs power-of-two batch, M, N");
+      return TNC_EINVAL;
+    }
+    uint64_t seen = 0;
+    for (int i = 0; i < nb; ++i) {
+      if (c_pos[i] < 0 || c_pos[i] >= nb || ((seen >> c_pos[i]) & 1)) {
+        set_error("tnc_cgemm_variant: c_pos is not a permutation of 0..%d", nb - 1);
+        return TNC_EINVAL;
+      }
+      seen |= (uint64_t)1 << c_pos[i];
+    }
+    g.c_ident = 1;
+    for (int i = 0; i < nb; ++i) {
+      g.c_pos[i] = (int8_t)c_pos[i];
+      if (c_pos[i] != i) g.c_ident = 0;
+    }
+    g.nN = nN, g.nM = nM, g.nB = nB;
+  }
   if (kernel >= 0) {
     GemmDesc cand[kMaxCandidates];
     int n = 0, hit = -1;
@@ -694,7 +718,7 @@ int tnc_cgemm_variant(const void* A, const void* B, void* Cp, int64_t batch, int
 
 int tnc_cgemm(const void* A, const void* B, void* Cp, int64_t batch, int64_t M, int64_t N, int64_t K, int tA,
               int tB, int form, void* scratch, size_t scratch_bytes, void* stream) {
-  return tnc_cgemm_variant(A, B, Cp, batch, M, N, K, tA, tB, form, -1, -1, scratch, scratch_bytes, stream);
+  return tnc_cgemm_variant(A, B, Cp, batch, M, N, K, tA, tB, form, -1, -1, nullptr, scratch, scratch_bytes, stream);
 }
 
 int tnc_plan_autotune(tnc_plan_t* plan, void* d_ws, size_t ws_bytes, void* stream, int reps, int* n_changed) {

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <cstdio>
 
 #include "outmap.cuh"
@@ -104,43 +105,11 @@ __global__ void __launch_bounds__(kPermThreads) permute_kernel(const float2* __r
 // many output bit positions; the tile is written into shared memory at the
 // rank of each element's output offset among the tile's (a bit compression)
 // and read back in that order, so consecutive threads store consecutive
-// output addresses wherever the tile's bits cover the low positions.
-template <int BM, int BN>
-struct TileOrder {
-  static constexpr int kMB = __builtin_ctz(BM), kNB = __builtin_ctz(BN), kBits = kMB + kNB;
-  int pos[kBits];   // output bit position of tile bit b (m bits first, then n bits)
-  int rank[kBits];  // rank of pos[b] among the tile's positions
-  __device__ explicit TileOrder(const OutMap& om) {
-#pragma unroll
-    for (int b = 0; b < kMB; ++b) pos[b] = om.pos[om.nN + b];
-#pragma unroll
-    for (int b = 0; b < kNB; ++b) pos[kMB + b] = om.pos[b];
-#pragma unroll
-    for (int b = 0; b < kBits; ++b) {
-      int r = 0;
-#pragma unroll
-      for (int k = 0; k < kBits; ++k) r += pos[k] < pos[b];
-      rank[b] = r;
-    }
-  }
-  __device__ uint32_t index_row(int r) const {
-    uint32_t x = 0;
-#pragma unroll
-    for (int b = 0; b < kMB; ++b) x |= (uint32_t)((r >> b) & 1) << rank[b];
-    return x;
-  }
-  __device__ uint32_t index_col(int c) const {
-    uint32_t x = 0;
-#pragma unroll
-    for (int b = 0; b < kNB; ++b) x |= (uint32_t)((c >> b) & 1) << rank[kMB + b];
-    return x;
-  }
-  __device__ uint64_t offset_of(uint32_t x) const {
-    uint64_t o = 0;
-#pragma unroll
-    for (int b = 0; b < kBits; ++b) o |= (uint64_t)((x >> rank[b]) & 1u) << pos[b];
-    return o;
-  }
+// output addresses wherever the tile's bits cover the low positions.  The
+// ranks are computed on the host (TileRank: m bits first, then n bits); each
+// block builds its row, column and offset tables in shared memory once.
+struct TileRank {
+  int8_t rank[kMaxRank];
 };
 
 __device__ __forceinline__ uint32_t tile_swz(uint32_t x) { return x ^ ((x >> 4) & 15u); }
@@ -150,7 +119,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN),
                                   (BM * BN >= 8192) ? 1 : ((BM / TM) * (BN / TN) >= 256 ? 3 : 4))
     cgemm_simt_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
                       int64_t M, int64_t N, int64_t K, int transA, int transB, int64_t b0, int64_t kchunk,
-                      int64_t part_stride, int staged, const __grid_constant__ OutMap om) {
+                      int64_t part_stride, int staged, const __grid_constant__ OutMap om,
+                      const __grid_constant__ TileRank tr) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
   // rows padded by 16 bytes: the transposing tile stores spread over banks
@@ -215,19 +185,46 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN),
   }
   if (staged) {
     // full tile (M % BM == N % BN == 0), scattered output, no split-K
+    constexpr int kMB = __builtin_ctz(BM), kNB = __builtin_ctz(BN), kBits = kMB + kNB;
     extern __shared__ __align__(16) uint8_t simt_dyn[];
-    float2* S = (float2*)simt_dyn;                                  // [BM * BN]
-    uint64_t* hi = (uint64_t*)(S + BM * BN);                        // [BM * BN / 32]
-    const TileOrder<BM, BN> to(om);
-    for (int e = tid; e < BM * BN / 32; e += NT) hi[e] = to.offset_of((uint32_t)e << 5);
+    float2* S = (float2*)simt_dyn;                        // [BM * BN]
+    uint64_t* hi = (uint64_t*)(S + BM * BN);              // [BM * BN / 32] offsets of staging bits 5..
+    uint32_t* rowidx = (uint32_t*)(hi + BM * BN / 32);    // [BM]
+    uint32_t* colidx = rowidx + BM;                       // [BN]
+    // output bit position of tile bit b
+    auto pos_of = [&](int b) -> int { return b < kMB ? om.pos[om.nN + b] : om.pos[b - kMB]; };
+    auto offset_of = [&](uint32_t x) -> uint64_t {
+      uint64_t o = 0;
+#pragma unroll
+      for (int b = 0; b < kBits; ++b) o |= (uint64_t)((x >> tr.rank[b]) & 1u) << pos_of(b);
+      return o;
+    };
+    for (int e = tid; e < BM * BN / 32; e += NT) hi[e] = offset_of((uint32_t)e << 5);
+    for (int r = tid; r < BM; r += NT) {
+      uint32_t x = 0;
+#pragma unroll
+      for (int b = 0; b < kMB; ++b) x |= (uint32_t)((r >> b) & 1) << tr.rank[b];
+      rowidx[r] = x;
+    }
+    for (int c = tid; c < BN; c += NT) {
+      uint32_t x = 0;
+#pragma unroll
+      for (int b = 0; b < kNB; ++b) x |= (uint32_t)((c >> b) & 1) << tr.rank[kMB + b];
+      colidx[c] = x;
+    }
+    const uint64_t lo = offset_of((uint32_t)(tid & 31));
+    __syncthreads();
+    uint32_t ci[TN];
+#pragma unroll
+    for (int j = 0; j < TN; ++j) ci[j] = colidx[tx * TN + j];
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-      const uint32_t ri = to.index_row(ty * TM + i);
+      const uint32_t ri = rowidx[ty * TM + i];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) S[tile_swz(ri | to.index_col(tx * TN + j))] = acc[i][j];
+      for (int j = 0; j < TN; ++j) S[tile_swz(ri | ci[j])] = acc[i][j];
     }
     __syncthreads();
-    float2* dst = C + om.row(bz, m0, M, N) + om.col(n0) + to.offset_of((uint32_t)(tid & 31));
+    float2* dst = C + om.row(bz, m0, M, N) + om.col(n0) + lo;
 #pragma unroll 4
     for (int e = tid; e < BM * BN; e += NT) dst[hi[e >> 5]] = S[tile_swz((uint32_t)e)];
     return;
@@ -523,7 +520,21 @@ int run_simt(const GemmDesc& d, const float2* A, const float2* B, float2* C, flo
   ident.ident = 1;
   // staged epilogue for full tiles of a scattered output
   const int staged = (splits == 1 && !d.c_ident && d.M % BM == 0 && d.N % BN == 0) ? 1 : 0;
-  const size_t dyn = staged ? (size_t)BM * BN * 8 + (size_t)BM * BN / 32 * 8 : 0;
+  const size_t dyn = staged ? (size_t)BM * BN * 8 + (size_t)BM * BN / 32 * 8 + (size_t)(BM + BN) * 4 : 0;
+  TileRank tr;
+  std::memset(&tr, 0, sizeof(tr));
+  if (staged) {
+    // rank of each tile bit's output position among the tile's positions
+    constexpr int kMB = __builtin_ctz(BM), kNB = __builtin_ctz(BN);
+    int pos[kMaxRank];
+    for (int b = 0; b < kMB; ++b) pos[b] = d.c_pos[d.nN + b];
+    for (int b = 0; b < kNB; ++b) pos[kMB + b] = d.c_pos[b];
+    for (int b = 0; b < kMB + kNB; ++b) {
+      int r = 0;
+      for (int k = 0; k < kMB + kNB; ++k) r += pos[k] < pos[b];
+      tr.rank[b] = (int8_t)r;
+    }
+  }
   static bool attr_set = false;
   if (staged && !attr_set) {
     cudaError_t e = cudaFuncSetAttribute(cgemm_simt_kernel<BM, BN, BK, TM, TN>,
@@ -535,7 +546,8 @@ int run_simt(const GemmDesc& d, const float2* A, const float2* B, float2* C, flo
     int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
     dim3 grid((unsigned)(mt * nt), (unsigned)splits, (unsigned)nb);
     cgemm_simt_kernel<BM, BN, BK, TM, TN><<<grid, NT, dyn, st>>>(A, B, dst, d.M, d.N, d.K, d.transA, d.transB,
-                                                                  b0, kchunk, nout, staged, splits > 1 ? ident : om);
+                                                                  b0, kchunk, nout, staged, splits > 1 ? ident : om,
+                                                                  tr);
   }
   if (splits > 1) {
     unsigned blocks = (unsigned)((nout + 255) / 256 < 152 * 16 ? (nout + 255) / 256 : 152 * 16);

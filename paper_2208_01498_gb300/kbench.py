@@ -46,7 +46,9 @@ def main():
     ap.add_argument("--tB", type=int, default=1)
     ap.add_argument("--form", default="split_bf16")
     ap.add_argument("--kernel", default=None, help="variant name of tnc.KG (default: chosen by shape)")
-    ap.add_argument("--tile", type=int, default=None, help="tensor-core tile width 1, 2 or 3")
+    ap.add_argument("--tile", type=int, default=None, help="tensor-core tile variant (see tnc_cgemm_variant)")
+    ap.add_argument("--c-pos", default=None,
+                    help="output bit order as a comma-separated list (n bits, m bits, batch bits; see tnc.h)")
     ap.add_argument("--iters", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     a = ap.parse_args()
@@ -63,10 +65,11 @@ def main():
     B = torch.randn(a.batch * a.K * a.N, dtype=torch.complex64, device="cuda")
     C = torch.empty((a.batch, a.M, a.N), dtype=torch.complex64, device="cuda")
     f = tnc.FORMS[a.form]
+    cpos = None if a.c_pos is None else [int(x) for x in a.c_pos.split(",")]
     need = tnc.lib.tnc_cgemm_scratch_bytes(a.batch, a.M, a.N, a.K, f)
     scr = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
     ms = _time(lambda: tnc.cgemm(A, B, a.batch, a.M, a.N, a.K, a.tA, a.tB, a.form, out=C, scratch=scr,
-                                   kernel=a.kernel, tile=a.tile),
+                                   kernel=a.kernel, tile=a.tile, c_pos=cpos),
                a.iters, a.warmup)
     flops = 8.0 * a.batch * a.M * a.N * a.K
     byts = 8.0 * a.batch * (a.M * a.K + a.K * a.N + a.M * a.N)

@@ -110,7 +110,7 @@ def _load():
         "tnc_plan_set_kernels": (i, [vp, C.POINTER(i), i]),
         "tnc_cgemm_scratch_bytes": (sz, [C.c_int64] * 4 + [i]),
         "tnc_cgemm": (i, [vp, vp, vp] + [C.c_int64] * 4 + [i, i, i, vp, sz, vp]),
-        "tnc_cgemm_variant": (i, [vp, vp, vp] + [C.c_int64] * 4 + [i, i, i, i, i, vp, sz, vp]),
+        "tnc_cgemm_variant": (i, [vp, vp, vp] + [C.c_int64] * 4 + [i, i, i, i, i, vp, vp, sz, vp]),
         "tnc_plan_get_profile": (i, [vp, C.POINTER(i), i, C.POINTER(C.c_double), C.POINTER(i),
                                      C.POINTER(i), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     }
@@ -360,10 +360,10 @@ def permute(x, src_bit, out=None, stream=None):
 
 
 def cgemm(A, B, batch, M, N, K, transA=0, transB=0, form="fp32", out=None, scratch=None, stream=None,
-          kernel=None, tile=None):
+          kernel=None, tile=None, c_pos=None):
     """``tnc_cgemm`` (``tnc_cgemm_variant`` when ``kernel`` is given, a name
     of ``KG`` or its number): batched complex GEMM of one tree node on
-    complex64 CUDA tensors."""
+    complex64 CUDA tensors.  ``c_pos``: output bit order (see tnc.h)."""
     import torch
     f = FORMS[form] if isinstance(form, str) else int(form)
     need = lib.tnc_cgemm_scratch_bytes(batch, M, N, K, f)
@@ -372,8 +372,10 @@ def cgemm(A, B, batch, M, N, K, transA=0, transB=0, form="fp32", out=None, scrat
     if scratch is None and need:
         scratch = torch.empty(need, dtype=torch.uint8, device=A.device)
     kg = -1 if kernel is None else (KG[kernel] if isinstance(kernel, str) else int(kernel))
+    cp = None if c_pos is None else np.ascontiguousarray(c_pos, np.int32)
     _check(lib.tnc_cgemm_variant(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()), C.c_void_p(out.data_ptr()),
                                  batch, M, N, K, int(transA), int(transB), f, kg, -1 if tile is None else int(tile),
+                                 _ptr(cp, C.c_int) if cp is not None else None,
                                  C.c_void_p(scratch.data_ptr() if scratch is not None else 0),
                                  scratch.numel() if scratch is not None else 0, _stream_ptr(stream)), "tnc_cgemm")
     return out

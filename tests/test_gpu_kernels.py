@@ -147,3 +147,40 @@ def test_cgemm_on_chip_split_unaligned_operands(tnc):
     ref = _ref(A[1:], B[1:], batch, M, N, K, 0, 1)
     err = np.linalg.norm(got.cpu().numpy().astype(np.complex128) - ref) / np.linalg.norm(ref)
     assert err <= TOL["split_bf16"]
+
+
+SCATTER_CASES = [  # batch, M, N, K, kernel, tile, form
+    (4, 64, 32, 8, "simt_64x32", 0, "fp32"), (2, 128, 64, 4, "simt_128x64", 0, "fp32"),
+    (8, 32, 128, 16, "simt_32x128", 0, "fp32"), (16, 256, 8, 4, "narrow", 0, "fp32"),
+    (4, 1, 1, 4096, "dot", 0, "fp32"), (4, 256, 128, 128, "tc", 2, "split_bf16"),
+    (4, 256, 128, 128, "tc", 4, "split_bf16"), (4, 256, 128, 256, "tc", 8, "split_bf16"),
+    (4, 256, 128, 256, "tc", 9, "split_bf16"), (8, 128, 32, 64, "tc", 6, "split_bf16"),
+    (2, 128, 64, 1024, "tc", 5, "split_bf16"), (2, 256, 64, 128, "tc", 10, "split_bf16"),
+    (4, 128, 64, 64, "tc", 2, "3xtf32"),
+]
+
+
+@pytest.mark.parametrize("case", SCATTER_CASES, ids=lambda c: f"{c[4]}{c[5]}-{c[6]}")
+def test_cgemm_scattered_output(tnc, case):
+    """Every kernel variant writing C in a shuffled bit order (as a plan's
+    consumer layout), element by element against NumPy."""
+    batch, M, N, K, kernel, tile, form = case
+    nN, nM, nB = N.bit_length() - 1, M.bit_length() - 1, batch.bit_length() - 1
+    rng = np.random.default_rng(M + N + K + tile)
+    c_pos = rng.permutation(nN + nM + nB)
+    A = _crand(batch * M * K, rng)
+    B = _crand(batch * K * N, rng)
+    got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, 0, 1, form,
+                    kernel=kernel, tile=tile, c_pos=c_pos).reshape(-1).cpu().numpy()
+    ref = _ref(A, B, batch, M, N, K, 0, 1)
+    b, m, n = np.meshgrid(np.arange(batch), np.arange(M), np.arange(N), indexing="ij")
+    addr = np.zeros(b.shape, np.int64)
+    for i in range(nN):
+        addr |= ((n >> i) & 1) << int(c_pos[i])
+    for i in range(nM):
+        addr |= ((m >> i) & 1) << int(c_pos[nN + i])
+    for i in range(nB):
+        addr |= ((b >> i) & 1) << int(c_pos[nN + nM + i])
+    placed = got[addr]
+    err = np.linalg.norm(placed.astype(np.complex128) - ref) / np.linalg.norm(ref)
+    assert err <= TOL[form], f"{case}: {err:.3g}"
