@@ -420,6 +420,7 @@ struct FzCfg {
   static constexpr int kTasks = kATasks + (BN / 2) * kChunks;  // A 128 rows, B BN/2 complex rows
   static constexpr int kConvWarps = kTasks / 128;             // 4 tasks per converter thread: 12, 10 or 8 warps
   static constexpr int kConvThreads = 32 * kConvWarps;
+  static constexpr int kEpiWarps = 4;
   static constexpr int kThreads = 32 * (5 + kConvWarps);
   static constexpr int kFullArrivals = kConvThreads;          // arrivals completing a stage
   static constexpr uint32_t kATileBytes = 128 * kRowBytes;    // one A plane tile
@@ -476,7 +477,8 @@ struct PlCfg {
   static constexpr int kKC = 32;  // complex k per k-block (128-byte rows of bf16)
   static constexpr int kKSteps = 4;
   static constexpr int kChunkKB = 8;
-  static constexpr int kThreads = 32 * 6;
+  static constexpr int kEpiWarps = 8;      // two per TMEM lane quarter, half of the columns each
+  static constexpr int kThreads = 32 * (kEpiWarps + 2);
   static constexpr int kFullArrivals = 1;  // the producer's expect_tx arrival; the bytes complete it
   static constexpr uint32_t kATileBytes = 128 * 128;
   static constexpr uint32_t kBTileBytes = BN * 128;
@@ -653,10 +655,13 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
   int* abort_flag = (int*)(tmem_slot + 1);
   uint64_t* coltab = (uint64_t*)(tmem_slot + 4);  // [4 warps][BN / 2]
   uint32_t* blk_col = (uint32_t*)(coltab + 4 * (BN / 2));  // [8] staging index of block column j
+                                                            // (coltab: [E warps][CW / 2], 4 BN / 2 in all)
   uint64_t* blk_dep = (uint64_t*)(blk_col + 8);               // [8] output offset of staging index bits 5..7
-  float2* stage_out = (float2*)(blk_dep + 8);                 // [4 warps][256]
+  float2* stage_out = (float2*)(blk_dep + 8);                 // [E warps][256]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int E = Cf::kEpiWarps;        // warps 0..E-1: epilogue; E: MMA; E+1..: producer / converters
+  constexpr int CW = BN * 4 / E;          // real columns per epilogue warp
   const int nk = geo.nk;
   const int nchunks = (nk + CHUNK - 1) / CHUNK;  // per tile
   const int64_t my_tiles = blockIdx.x < geo.tiles ? (geo.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -669,13 +674,13 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&acc_full[s], 1);
-      mbar_init(&acc_empty[s], 128);
+      mbar_init(&acc_empty[s], 32 * E);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 4) tmem_alloc(tmem_slot, Cf::kTmemCols);  // slot 0, slot 1, running sum (BN columns each)
+  if (warp == E) tmem_alloc(tmem_slot, Cf::kTmemCols);  // slot 0, slot 1, running sum (BN columns each)
   if (!om.ident && threadIdx.x < 8) {
     const BlockOrder bo(om);
     blk_col[threadIdx.x] = bo.index_col(threadIdx.x);
@@ -687,7 +692,7 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   int64_t tma_issued = 0;  // planes: k-blocks whose TMA loads were issued
-  if (Cf::kPlanes && warp == 5) {
+  if (Cf::kPlanes && warp == E + 1) {
     // producer: TMA loads of the hi/lo plane tiles of every k-block
     if (lane == 0) {
       int s = 0;
@@ -722,9 +727,9 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
         if (!ok) break;
       }
     }
-  } else if (!Cf::kPlanes && warp >= 5) {
+  } else if (!Cf::kPlanes && warp >= E + 1) {
     // converters: global k-block q = (local tile) * nk + kb
-    const int ct = threadIdx.x - 160;
+    const int ct = threadIdx.x - 32 * (E + 1);
     const int64_t total = my_tiles * nk;
     FzRegs R0;
     // load cursor: local tile lt_ld (coordinates bz, m0, n0), k-block kb_ld
@@ -766,7 +771,7 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
     };
     for (int64_t q = 0; q < total; ++q)
       if (!step(R0, q)) break;
-  } else if (warp == 4) {
+  } else if (warp == E) {
     if (lane == 0) {
       bool ok = true;
       int64_t gc = 0;       // global chunk counter
@@ -819,10 +824,12 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
       mma_commit(done);
     }
   } else {
-    // accumulation: row 32 warp + lane of each tile
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    // accumulation: row 32 (warp % 4) + lane of each tile, real columns
+    // [half * CW, half * CW + CW)
+    const int quarter = warp & 3, half = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     const uint32_t tsum = tmem + lane_base + 2 * BN;
-    uint64_t* ct = coltab + warp * (BN / 2);
+    uint64_t* ct = coltab + warp * (CW / 2);
     float2* so = stage_out + warp * 256;
     uint32_t idx_row = 0;
     uint64_t dep_lane = 0;
@@ -836,10 +843,10 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
     for (int64_t lt = 0; lt < my_tiles && ok; ++lt) {
       int bz, m0, n0;
       fz_tile<BN>(geo, (int64_t)blockIdx.x + lt * gridDim.x, bz, m0, n0);
-      const int row = m0 + warp * 32 + lane;
-      const uint64_t roff = om.ident ? 0 : om.row(bz, m0 + warp * 32, geo.M, geo.N);  // lane bits clear
+      const int row = m0 + quarter * 32 + lane;
+      const uint64_t roff = om.ident ? 0 : om.row(bz, m0 + quarter * 32, geo.M, geo.N);  // lane bits clear
       if (!om.ident)
-        for (int i = lane; i < BN / 2; i += 32) ct[i] = om.col(n0 / 2 + i);
+        for (int i = lane; i < CW / 2; i += 32) ct[i] = om.col(n0 / 2 + half * (CW / 2) + i);
       __syncwarp();
       for (int c = 0; c < nchunks; ++c, ++gc) {
         const int slot = (int)(gc & 1);
@@ -854,7 +861,7 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
         const uint32_t tslot = tmem + lane_base + slot * BN;
         const bool write_out = last && !*(volatile int*)abort_flag;
 #pragma unroll 1
-        for (int col = 0; col < BN; col += 16) {
+        for (int col = half * CW; col < half * CW + CW; col += 16) {
           float v[16];
           tmem_ld16(tslot + col, v);
           if (c > 0) {
@@ -877,7 +884,7 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
 #pragma unroll
               for (int j = 0; j < 8; ++j) so[stage_swz(idx_row | blk_col[j])] = make_float2(v[2 * j], v[2 * j + 1]);
               __syncwarp();
-              float2* C2 = (float2*)C + roff + ct[col / 2] + dep_lane;
+              float2* C2 = (float2*)C + roff + ct[(col - half * CW) / 2] + dep_lane;
 #pragma unroll
               for (int t = 0; t < 8; ++t) C2[blk_dep[t]] = so[stage_swz((uint32_t)(t * 32 + lane))];
               __syncwarp();
@@ -895,12 +902,12 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
   tc_fence_before();
   __syncthreads();
   // planes, after an abort: wait (bounded) for the TMA copies still in flight
-  if (Cf::kPlanes && warp == 5 && lane == 0 && *(volatile int*)abort_flag) {
+  if (Cf::kPlanes && warp == E + 1 && lane == 0 && *(volatile int*)abort_flag) {
     for (int64_t q = (tma_issued > kFzStages ? tma_issued - kFzStages : 0); q < tma_issued; ++q)
       mbar_wait(&full[q % kFzStages], (uint32_t)((q / kFzStages) & 1));
   }
   __syncthreads();
-  if (warp == 4) {
+  if (warp == E) {
     tc_fence_after();
     tmem_dealloc(tmem, Cf::kTmemCols);
   }
@@ -934,7 +941,7 @@ int launch_persistent(const GemmDesc& d, const float2* A, const float2* B, float
   constexpr int BN = Cf::kBN;
   // at least 117 KB so that one CTA (and one TMEM allocation) holds an SM
   const size_t need = 1024 + kFzStages * Cf::kStageBytes + (2 * kFzStages + 5) * 8 + 16 + 4 * BN / 2 * 8 + 8 * 4 +
-                      8 * 8 + 4 * 256 * 8;
+                      8 * 8 + Cf::kEpiWarps * 256 * 8;
   const size_t smem = need > 117 * 1024 ? need : 117 * 1024;
   static bool attr_set = false;
   if (!attr_set) {
