@@ -383,18 +383,21 @@ __global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
 // Each operand byte then crosses HBM once instead of three times (read,
 // planes written, planes read back).
 //
-// Warps 0..3: accumulation and epilogue (TMEM lane quarter = warp); warp 4:
-// TMEM allocation and the MMA issuer (one lane); warps 5 and up: converters
-// (12 for BN = 128 real output columns per CTA, 10 for BN = 64, 8 for
-// BN = 256, whose 64-byte rows halve the converter work per k-block).
+// Warps 0..E-1: accumulation and epilogue (TMEM lane quarter = warp % 4;
+// E = 4, or 8 with two warps per quarter, half of the columns each, for the
+// epilogue-bound 256-column and plane-fed tiles); warp E: TMEM allocation and
+// the MMA issuer (one lane); warps E+1 and up: converters (12 for BN = 128
+// real output columns per CTA, 10 for BN = 64, 8 for BN = 256, whose 64-byte
+// rows halve the converter work per k-block) or the TMA producer.
 // Finished accumulation chunks are added into a third TMEM region (the
 // running sum) instead of registers, so no thread holds a whole row.  The
 // register file is split between the SM's four sub-partitions (16K 32-bit
-// registers each); the 17-warp block of BN = 128 puts 5 warps on one of them,
-// which caps a thread at 96 registers (the 15-warp BN = 64 block: 128), and
-// the converters are sized to fit that (one k-block of loads in registers;
-// the PREFETCH variant also sends the k-block after next towards L2).  Two stages keep the block's shared memory under
-// 196 KB: the SM's unified L1/shared storage then leaves about 90 KB of L1
+// registers each); the 17-warp blocks (BN = 128, 256) put 5 warps on one of
+// them, which caps a thread at 96 registers (the 15-warp BN = 64 block: 128),
+// and the converters are sized to fit that (one k-block of loads in
+// registers; the PREFETCH variant also sends the k-block after next towards
+// L2).  Two stages keep the block's shared memory under 196 KB: the SM's
+// unified L1/shared storage then leaves about 90 KB of L1
 // for the converters' loads in flight (with three stages the carve-out rose
 // to 228 KB, L1 fell to 28 KB and the kernel ran 10-25 % slower).
 // The epilogue re-orders each warp's 32 x 8 complex block through shared
@@ -420,8 +423,8 @@ struct FzCfg {
   static constexpr int kTasks = kATasks + (BN / 2) * kChunks;  // A 128 rows, B BN/2 complex rows
   static constexpr int kConvWarps = kTasks / 128;             // 4 tasks per converter thread: 12, 10 or 8 warps
   static constexpr int kConvThreads = 32 * kConvWarps;
-  static constexpr int kEpiWarps = 4;
-  static constexpr int kThreads = 32 * (5 + kConvWarps);
+  static constexpr int kEpiWarps = BN == 256 ? 8 : 4;         // the short-K 256-column tiles are epilogue-bound
+  static constexpr int kThreads = 32 * (kEpiWarps + 1 + kConvWarps);
   static constexpr int kFullArrivals = kConvThreads;          // arrivals completing a stage
   static constexpr uint32_t kATileBytes = 128 * kRowBytes;    // one A plane tile
   static constexpr uint32_t kBTileBytes = BN * kRowBytes;     // one B' plane tile
