@@ -171,6 +171,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive TMEM columns of this thread's lane, loaded and waited for
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "{\n\ttcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n\t}"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // ------------------------------------------------------------ GEMM kernel
 // D[b][m][n'] = sum_k' A'[b][m][k'] B'^T[b][n'][k'], 3 products per k-step.
 // Warp 0: TMA producer; warp 1: MMA issuer; the remaining warps: accumulation
@@ -424,6 +437,7 @@ struct FzCfg {
   static constexpr int kConvWarps = kTasks / 128;             // 4 tasks per converter thread: 12, 10 or 8 warps
   static constexpr int kConvThreads = 32 * kConvWarps;
   static constexpr int kEpiWarps = BN == 256 ? 8 : 4;         // the short-K 256-column tiles are epilogue-bound
+  static constexpr int kStageBlocks = BN == 128 ? 1 : 2;      // BN = 128: no registers to spare at 96
   static constexpr int kThreads = 32 * (kEpiWarps + 1 + kConvWarps);
   static constexpr int kFullArrivals = kConvThreads;          // arrivals completing a stage
   static constexpr uint32_t kATileBytes = 128 * kRowBytes;    // one A plane tile
@@ -473,22 +487,25 @@ __device__ __forceinline__ void sts128(uint32_t addr, const uint32_t* w) {
 // (written by prep_a_vec / prep_b_vec): 128-byte rows (64 k' per k-block),
 // one producer warp instead of the converters.  BN = 256 has no running sum
 // (one accumulation chunk per tile: K <= 256).
-template <int BN>
+template <int BN, int ROW = 128>
 struct PlCfg {
   static constexpr int kBN = BN;
   static constexpr bool kPlanes = true;
-  static constexpr int kKC = 32;  // complex k per k-block (128-byte rows of bf16)
-  static constexpr int kKSteps = 4;
-  static constexpr int kChunkKB = 8;
+  static constexpr int kRowBytes = ROW;  // 64-byte rows keep BN = 256 at two stages of 48 KB
+  // staging blocks per epilogue step: two unless the shared memory is full
+  static constexpr int kStageBlocks = (BN == 256 && ROW == 128) ? 1 : 2;
+  static constexpr int kKC = kRowBytes / 4;               // complex k per k-block
+  static constexpr int kKSteps = kRowBytes / 32;
+  static constexpr int kChunkKB = 512 / (kRowBytes / 2);
   static constexpr int kEpiWarps = 8;      // two per TMEM lane quarter, half of the columns each
   static constexpr int kThreads = 32 * (kEpiWarps + 2);
   static constexpr int kFullArrivals = 1;  // the producer's expect_tx arrival; the bytes complete it
-  static constexpr uint32_t kATileBytes = 128 * 128;
-  static constexpr uint32_t kBTileBytes = BN * 128;
+  static constexpr uint32_t kATileBytes = 128 * kRowBytes;
+  static constexpr uint32_t kBTileBytes = BN * kRowBytes;
   static constexpr uint32_t kStageBytes = 2 * kATileBytes + 2 * kBTileBytes;
   static constexpr bool kSum = BN != 256;
   static constexpr int kTmemCols = BN == 256 ? 512 : (3 * BN <= 256 ? 256 : 512);
-  __device__ static uint64_t desc(uint32_t saddr) { return sw128_desc(saddr); }
+  __device__ static uint64_t desc(uint32_t saddr) { return kRowBytes == 128 ? sw128_desc(saddr) : sw64_desc(saddr); }
 };
 
 struct PlMaps {
@@ -660,7 +677,7 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
   uint32_t* blk_col = (uint32_t*)(coltab + 4 * (BN / 2));  // [8] staging index of block column j
                                                             // (coltab: [E warps][CW / 2], 4 BN / 2 in all)
   uint64_t* blk_dep = (uint64_t*)(blk_col + 8);               // [8] output offset of staging index bits 5..7
-  float2* stage_out = (float2*)(blk_dep + 8);                 // [E warps][256]
+  float2* stage_out = (float2*)(blk_dep + 8);                 // [E warps][2][256]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int E = Cf::kEpiWarps;        // warps 0..E-1: epilogue; E: MMA; E+1..: producer / converters
@@ -717,10 +734,11 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
           }
           uint8_t* st = smem + s * kStageBytes;
           mbar_expect_tx(&full[s], kStageBytes);
-          tma_load_3d(st, &maps.ah, &full[s], kb * 64, m0, bz);
-          tma_load_3d(st + Cf::kATileBytes, &maps.al, &full[s], kb * 64, m0, bz);
-          tma_load_3d(st + 2 * Cf::kATileBytes, &maps.bh, &full[s], kb * 64, n0, bz);
-          tma_load_3d(st + 2 * Cf::kATileBytes + Cf::kBTileBytes, &maps.bl, &full[s], kb * 64, n0, bz);
+          const int kx = kb * (Cf::kKC * 2);  // first bf16 column of the k-block
+          tma_load_3d(st, &maps.ah, &full[s], kx, m0, bz);
+          tma_load_3d(st + Cf::kATileBytes, &maps.al, &full[s], kx, m0, bz);
+          tma_load_3d(st + 2 * Cf::kATileBytes, &maps.bh, &full[s], kx, n0, bz);
+          tma_load_3d(st + 2 * Cf::kATileBytes + Cf::kBTileBytes, &maps.bl, &full[s], kx, n0, bz);
           ++tma_issued;
           if (++s == kFzStages) {
             s = 0;
@@ -833,7 +851,7 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     const uint32_t tsum = tmem + lane_base + 2 * BN;
     uint64_t* ct = coltab + warp * (CW / 2);
-    float2* so = stage_out + warp * 256;
+    float2* so = stage_out + warp * 256 * Cf::kStageBlocks;
     uint32_t idx_row = 0;
     uint64_t dep_lane = 0;
     if (!om.ident) {
@@ -863,33 +881,50 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
         const bool last = c == nchunks - 1;
         const uint32_t tslot = tmem + lane_base + slot * BN;
         const bool write_out = last && !*(volatile int*)abort_flag;
+        // NB staging blocks of 8 complex columns (16 real) per step
+        constexpr int NB = Cf::kStageBlocks;
 #pragma unroll 1
-        for (int col = half * CW; col < half * CW + CW; col += 16) {
-          float v[16];
-          tmem_ld16(tslot + col, v);
+        for (int col = half * CW; col < half * CW + CW; col += 16 * NB) {
+          float v[16 * NB];
+          if constexpr (NB == 2)
+            tmem_ld32(tslot + col, v);
+          else
+            tmem_ld16(tslot + col, v);
           if (c > 0) {
-            float w[16];
-            tmem_ld16(tsum + col, w);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] += w[i];
+            for (int h = 0; h < NB; ++h) {
+              float w[16];
+              tmem_ld16(tsum + col + 16 * h, w);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) v[16 * h + i] += w[i];
+            }
           }
           if (!last) {
-            tmem_st16(tsum + col, v);
+#pragma unroll
+            for (int h = 0; h < NB; ++h) tmem_st16(tsum + col + 16 * h, v + 16 * h);
           } else if (write_out) {
             if (om.ident) {
               float4* dst = (float4*)(C + ((int64_t)bz * geo.M + row) * N2 + n0 + col);
 #pragma unroll
-              for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+              for (int i = 0; i < 4 * NB; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             } else {
-              // through the warp's staging block: written by (row, column),
+              // through the warp's staging blocks: written by (row, column),
               // read back in output order, so that each store covers the
               // block's runs of consecutive output addresses
 #pragma unroll
-              for (int j = 0; j < 8; ++j) so[stage_swz(idx_row | blk_col[j])] = make_float2(v[2 * j], v[2 * j + 1]);
-              __syncwarp();
-              float2* C2 = (float2*)C + roff + ct[(col - half * CW) / 2] + dep_lane;
+              for (int j = 0; j < 8; ++j) {
+                const uint32_t x = stage_swz(idx_row | blk_col[j]);
 #pragma unroll
-              for (int t = 0; t < 8; ++t) C2[blk_dep[t]] = so[stage_swz((uint32_t)(t * 32 + lane))];
+                for (int h = 0; h < NB; ++h) so[256 * h + x] = make_float2(v[16 * h + 2 * j], v[16 * h + 2 * j + 1]);
+              }
+              __syncwarp();
+              const int cc = (col - half * CW) / 2;
+#pragma unroll
+              for (int t = 0; t < 8; ++t) {
+                const uint32_t x = stage_swz((uint32_t)(t * 32 + lane));
+#pragma unroll
+                for (int h = 0; h < NB; ++h) ((float2*)C + roff + ct[cc + 8 * h] + dep_lane)[blk_dep[t]] = so[256 * h + x];
+              }
               __syncwarp();
             }
           }
@@ -944,7 +979,7 @@ int launch_persistent(const GemmDesc& d, const float2* A, const float2* B, float
   constexpr int BN = Cf::kBN;
   // at least 117 KB so that one CTA (and one TMEM allocation) holds an SM
   const size_t need = 1024 + kFzStages * Cf::kStageBytes + (2 * kFzStages + 5) * 8 + 16 + 4 * BN / 2 * 8 + 8 * 4 +
-                      8 * 8 + Cf::kEpiWarps * 256 * 8;
+                      8 * 8 + Cf::kEpiWarps * Cf::kStageBlocks * 256 * 8;
   const size_t smem = need > 117 * 1024 ? need : 117 * 1024;
   static bool attr_set = false;
   if (!attr_set) {
@@ -955,7 +990,7 @@ int launch_persistent(const GemmDesc& d, const float2* A, const float2* B, float
   }
   FzGeom g;
   g.M = (int)d.M, g.N = (int)d.N, g.K = (int)d.K;
-  g.tiles_m = (int)(d.M / BM), g.tiles_n = (int)(2 * d.N / BN), g.nk = (int)(d.K / Cf::kKC);
+  g.tiles_m = (int)(d.M / BM), g.tiles_n = (int)(2 * d.N / BN), g.nk = (int)((d.K + Cf::kKC - 1) / Cf::kKC);
   g.tiles = (int64_t)g.tiles_m * g.tiles_n * d.batch;
   const int64_t grid = g.tiles < sm_count() ? g.tiles : sm_count();
   tc_fused_bf16_kernel<Cf, PREFETCH><<<(unsigned)grid, Cf::kThreads, smem, st>>>(A, B, C, g, out_map(d), maps);
@@ -1113,16 +1148,18 @@ EncodeTiledFn encode_fn() {
 }
 
 // 3D map over a plane [batch][rows][cols], box (128-byte row, box_rows, 1)
-int make_map(CUtensorMap* m, void* base, bool tf32, int64_t cols, int64_t rows, int64_t batch, int box_rows) {
+int make_map(CUtensorMap* m, void* base, bool tf32, int64_t cols, int64_t rows, int64_t batch, int box_rows,
+             int row_bytes = 128) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return (int)cudaErrorNotSupported;
   const int es = tf32 ? 4 : 2;
   cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
   cuuint64_t strides[2] = {(cuuint64_t)(cols * es), (cuuint64_t)(cols * rows * es)};
-  cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)(row_bytes / es), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides,
-                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : (int)cudaErrorInvalidValue;
 }
@@ -1131,7 +1168,7 @@ int make_map(CUtensorMap* m, void* base, bool tf32, int64_t cols, int64_t rows, 
 // of 128-byte rows x 128 (A) or box_n (B) rows)
 template <bool kTF32>
 int prep_planes(const GemmDesc& d, const float2* A, const float2* B, uint8_t* scratch, int box_n, PlMaps& maps,
-                cudaStream_t st) {
+                cudaStream_t st, int row_bytes = 128) {
   const int64_t M = d.M, N2 = 2 * d.N, K2 = 2 * d.K, nb = d.batch;
   const int es = kTF32 ? 4 : 2;
   uint8_t* a_hi = scratch;
@@ -1151,20 +1188,20 @@ int prep_planes(const GemmDesc& d, const float2* A, const float2* B, uint8_t* sc
   else
     prep_b_kernel<kTF32><<<blocks(nbb), 256, 0, st>>>(B, b_hi, b_lo, d.N, d.K, nbb, d.transB);
   int r;
-  if ((r = make_map(&maps.ah, a_hi, kTF32, K2, M, nb, BM))) return r;
-  if ((r = make_map(&maps.al, a_lo, kTF32, K2, M, nb, BM))) return r;
-  if ((r = make_map(&maps.bh, b_hi, kTF32, K2, N2, nb, box_n))) return r;
-  if ((r = make_map(&maps.bl, b_lo, kTF32, K2, N2, nb, box_n))) return r;
+  if ((r = make_map(&maps.ah, a_hi, kTF32, K2, M, nb, BM, row_bytes))) return r;
+  if ((r = make_map(&maps.al, a_lo, kTF32, K2, M, nb, BM, row_bytes))) return r;
+  if ((r = make_map(&maps.bh, b_hi, kTF32, K2, N2, nb, box_n, row_bytes))) return r;
+  if ((r = make_map(&maps.bl, b_lo, kTF32, K2, N2, nb, box_n, row_bytes))) return r;
   return 0;
 }
 
 // persistent TMA-fed variant (split-BF16)
-template <int BN>
+template <int BN, int ROW>
 int run_tc_planes(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_t* scratch, cudaStream_t st) {
   PlMaps maps;
-  int r = prep_planes<false>(d, A, B, scratch, BN, maps, st);
+  int r = prep_planes<false>(d, A, B, scratch, BN, maps, st, ROW);
   if (r) return r;
-  return launch_persistent<PlCfg<BN>, false>(d, A, B, C, maps, st);
+  return launch_persistent<PlCfg<BN, ROW>, false>(d, A, B, C, maps, st);
 }
 
 template <bool kTF32, int BN, int STAGES>
@@ -1199,8 +1236,11 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
 // (checked again below); the scratch holds the four planes.
 int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* C, void* scratch_ptr,
                    cudaStream_t st) {
-  if (d.M < BM || d.N < 32 || d.K < 32 || (d.M % BM) || (d.N % 32) || (d.K % 32) || d.M > (1 << 30) ||
-      2 * d.N > (1 << 30) || 2 * d.K > (1 << 30))
+  // the persistent plane tiles (9, 10) also take short K (a power of two
+  // >= 4): TMA fills the k-block beyond the plane rows with zeros
+  const bool short_k = (d.tile == 9 || d.tile == 10 || d.tile == 11) && d.K >= 4 && d.K < 32 && !(d.K & (d.K - 1));
+  if (d.M < BM || d.N < 32 || (d.K < 32 && !short_k) || (d.M % BM) || (d.N % 32) || (d.K % 32 && !short_k) ||
+      d.M > (1 << 30) || 2 * d.N > (1 << 30) || 2 * d.K > (1 << 30))
     return (int)cudaErrorInvalidValue;
   const bool tf32 = d.form == TNC_3XTF32;
   const uint64_t es = tf32 ? 4 : 2;
@@ -1212,14 +1252,17 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   // 4, 5: 128 x 128, 6, 7: 128 x 64 and 8: 128 x 256 (K <= 256) with the
   // split done on chip (split-BF16, K-major operands), 5 and 7 with an L2
   // prefetch of the k-block after next; 9: 128 x 256 (K <= 256) and
-  // 10: 128 x 128, persistent from the planes (split-BF16)
+  // 10: 128 x 128, persistent from the planes (split-BF16); 11: as 9 with
+  // 64-byte rows and two staging blocks per epilogue step
   const int tile = d.tile ? d.tile : (d.N >= 64 ? 2 : 1);
-  if (tile < 1 || tile > 10 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
+  if (tile < 1 || tile > 11 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
       (tile >= 4 && tile <= 8 && (d.transA || !d.transB)) || (tile >= 4 && tf32) ||
-      ((tile == 4 || tile == 5 || tile == 10) && d.N < 64) || ((tile == 8 || tile == 9) && (d.N < 128 || d.K > 256)))
+      ((tile == 4 || tile == 5 || tile == 10) && d.N < 64) ||
+      ((tile == 8 || tile == 9 || tile == 11) && (d.N < 128 || d.K > 256)))
     return (int)cudaErrorInvalidValue;
-  if (tile == 9) return run_tc_planes<256>(d, A, B, (float*)C, scratch, st);
-  if (tile == 10) return run_tc_planes<128>(d, A, B, (float*)C, scratch, st);
+  if (tile == 9) return run_tc_planes<256, 128>(d, A, B, (float*)C, scratch, st);
+  if (tile == 10) return run_tc_planes<128, 128>(d, A, B, (float*)C, scratch, st);
+  if (tile == 11) return run_tc_planes<256, 64>(d, A, B, (float*)C, scratch, st);
   if (tile >= 4) {
     const bool aligned = ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0;
     if (aligned && tile <= 5 && fused_launchable<128>())

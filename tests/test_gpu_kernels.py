@@ -97,7 +97,7 @@ TILE_SHAPES = [(2, 128, 128, 64, 0, 1), (1, 256, 256, 4096, 0, 1), (3, 512, 128,
 
 
 @pytest.mark.parametrize("shape", TILE_SHAPES)
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11])
 @pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
 def test_cgemm_tensor_core_tile_widths(tnc, shape, tile, form):
     """Every tcgen05 tile width (128 x 64, 128 x 128, 128 x 256 real outputs
@@ -109,9 +109,9 @@ def test_cgemm_tensor_core_tile_widths(tnc, shape, tile, form):
         pytest.skip("the on-chip split takes split-BF16 with K-major operands only")
     if tile >= 9 and form != "split_bf16":
         pytest.skip("the persistent plane kernel takes split-BF16 only")
-    if (tile == 2 and N < 64) or (tile in (3, 8, 9) and N < 128) or (tile in (4, 5, 10) and N < 64):
+    if (tile == 2 and N < 64) or (tile in (3, 8, 9, 11) and N < 128) or (tile in (4, 5, 10) and N < 64):
         pytest.skip("tile wider than N")
-    if tile in (8, 9) and K > 256:
+    if tile in (8, 9, 11) and K > 256:
         pytest.skip("the 256-column persistent tiles take K <= 256")
     rng = np.random.default_rng(batch + M + N + K + tile)
     A = _crand(batch * M * K, rng)
@@ -154,7 +154,8 @@ SCATTER_CASES = [  # batch, M, N, K, kernel, tile, form
     (8, 32, 128, 16, "simt_32x128", 0, "fp32"), (16, 256, 8, 4, "narrow", 0, "fp32"),
     (4, 1, 1, 4096, "dot", 0, "fp32"), (4, 256, 128, 128, "tc", 2, "split_bf16"),
     (4, 256, 128, 128, "tc", 4, "split_bf16"), (4, 256, 128, 256, "tc", 8, "split_bf16"),
-    (4, 256, 128, 256, "tc", 9, "split_bf16"), (8, 128, 32, 64, "tc", 6, "split_bf16"),
+    (4, 256, 128, 256, "tc", 9, "split_bf16"), (4, 256, 128, 64, "tc", 11, "split_bf16"),
+    (2, 512, 256, 8, "tc", 11, "split_bf16"), (8, 128, 32, 64, "tc", 6, "split_bf16"),
     (2, 128, 64, 1024, "tc", 5, "split_bf16"), (2, 256, 64, 128, "tc", 10, "split_bf16"),
     (4, 128, 64, 64, "tc", 2, "3xtf32"),
 ]
@@ -184,3 +185,20 @@ def test_cgemm_scattered_output(tnc, case):
     placed = got[addr]
     err = np.linalg.norm(placed.astype(np.complex128) - ref) / np.linalg.norm(ref)
     assert err <= TOL[form], f"{case}: {err:.3g}"
+
+
+@pytest.mark.parametrize("shape,tile", [((2, 256, 128, 8, 0, 1), 9), ((2, 256, 128, 8, 0, 1), 10),
+                                        ((4, 128, 64, 4, 0, 1), 10), ((1, 512, 256, 16, 1, 0), 9),
+                                        ((2, 256, 128, 8, 0, 1), 11), ((1, 256, 256, 4, 0, 1), 11)])
+def test_cgemm_short_k_plane_tiles(tnc, shape, tile):
+    """The persistent plane tiles on K < 32 (the k-block beyond the plane
+    rows is zero-filled by TMA), on plain and scattered outputs."""
+    batch, M, N, K, tA, tB = shape
+    rng = np.random.default_rng(M + N + K + tile)
+    A = _crand(batch * M * K, rng)
+    B = _crand(batch * K * N, rng)
+    ref = _ref(A, B, batch, M, N, K, tA, tB)
+    got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, tA, tB, "split_bf16",
+                    kernel="tc", tile=tile)
+    err = np.linalg.norm(got.cpu().numpy().astype(np.complex128) - ref) / np.linalg.norm(ref)
+    assert err <= TOL["split_bf16"], f"{shape} tile {tile}: {err:.3g}"
