@@ -160,13 +160,15 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
       if (g0.N >= 128 && g0.K <= 256) add(KG_TC, 8);
     }
     if (g0.form == TNC_SPLIT_BF16 && g0.N >= 64) add(KG_TC, 10);
+    if (g0.form == TNC_SPLIT_BF16) add(KG_TC, 12);
     if (g0.form == TNC_SPLIT_BF16 && g0.N >= 128 && g0.K <= 256) {
       add(KG_TC, 9);
       add(KG_TC, 11);
     }
-  } else if (g0.form == TNC_SPLIT_BF16 && pow2 && g0.M >= 128 && g0.N >= 64 && g0.K >= 4 && g0.K < 32) {
+  } else if (g0.form == TNC_SPLIT_BF16 && pow2 && g0.M >= 128 && g0.N >= 32 && g0.K >= 4 && g0.K < 32) {
     // short K: the persistent plane tiles (k-block zero-filled by TMA)
-    add(KG_TC, 10);
+    add(KG_TC, 12);
+    if (g0.N >= 64) add(KG_TC, 10);
     if (g0.N >= 128) {
       add(KG_TC, 9);
       add(KG_TC, 11);

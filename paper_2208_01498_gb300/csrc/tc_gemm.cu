@@ -1238,7 +1238,7 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
                    cudaStream_t st) {
   // the persistent plane tiles (9, 10) also take short K (a power of two
   // >= 4): TMA fills the k-block beyond the plane rows with zeros
-  const bool short_k = (d.tile == 9 || d.tile == 10 || d.tile == 11) && d.K >= 4 && d.K < 32 && !(d.K & (d.K - 1));
+  const bool short_k = d.tile >= 9 && d.tile <= 12 && d.K >= 4 && d.K < 32 && !(d.K & (d.K - 1));
   if (d.M < BM || d.N < 32 || (d.K < 32 && !short_k) || (d.M % BM) || (d.N % 32) || (d.K % 32 && !short_k) ||
       d.M > (1 << 30) || 2 * d.N > (1 << 30) || 2 * d.K > (1 << 30))
     return (int)cudaErrorInvalidValue;
@@ -1253,9 +1253,9 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   // split done on chip (split-BF16, K-major operands), 5 and 7 with an L2
   // prefetch of the k-block after next; 9: 128 x 256 (K <= 256) and
   // 10: 128 x 128, persistent from the planes (split-BF16); 11: as 9 with
-  // 64-byte rows and two staging blocks per epilogue step
+  // 64-byte rows and two staging blocks per epilogue step; 12: 128 x 64
   const int tile = d.tile ? d.tile : (d.N >= 64 ? 2 : 1);
-  if (tile < 1 || tile > 11 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
+  if (tile < 1 || tile > 12 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
       (tile >= 4 && tile <= 8 && (d.transA || !d.transB)) || (tile >= 4 && tf32) ||
       ((tile == 4 || tile == 5 || tile == 10) && d.N < 64) ||
       ((tile == 8 || tile == 9 || tile == 11) && (d.N < 128 || d.K > 256)))
@@ -1263,6 +1263,7 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   if (tile == 9) return run_tc_planes<256, 128>(d, A, B, (float*)C, scratch, st);
   if (tile == 10) return run_tc_planes<128, 128>(d, A, B, (float*)C, scratch, st);
   if (tile == 11) return run_tc_planes<256, 64>(d, A, B, (float*)C, scratch, st);
+  if (tile == 12) return run_tc_planes<64, 128>(d, A, B, (float*)C, scratch, st);
   if (tile >= 4) {
     const bool aligned = ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0;
     if (aligned && tile <= 5 && fused_launchable<128>())

@@ -64,8 +64,8 @@ struct GemmDesc {
   int tile;              // tensor-core tile width: 0 auto, 1 N = 64 real columns, 2 N = 128, 3 N = 256,
                         // 4, 5 N = 128, 6, 7 N = 64 and 8 N = 256 (K <= 256) with the
                         // split-BF16 split on chip (5, 7: with prefetch); 9 N = 256
-                        // (K <= 256), 10 N = 128, 11 N = 256 with 64-byte rows: persistent
-                        // from the planes (9-11 also for K = 4..16)
+                        // (K <= 256), 10 N = 128, 11 N = 256 with 64-byte rows, 12 N = 64:
+                        // persistent from the planes (9-12 also for K = 4..16)
 };
 
 // One problem of a grouped launch of narrow nodes (N, K <= 16): the same
@@ -109,7 +109,7 @@ void choose_gemm_kernel(GemmDesc& g);
 uint64_t gemm_scratch_bytes(const GemmDesc& g);
 // every kernel variant that can run this node (the default choice first)
 void gemm_candidates(const GemmDesc& g, GemmDesc* out, int* n);
-constexpr int kMaxCandidates = 16;
+constexpr int kMaxCandidates = 17;
 int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, void* stream);
 int launch_grouped_narrow(const GroupedDesc* d_descs, int n, int64_t total_blocks, const void* base, void* ws,
                           void* stream);

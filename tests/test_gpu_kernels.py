@@ -97,7 +97,7 @@ TILE_SHAPES = [(2, 128, 128, 64, 0, 1), (1, 256, 256, 4096, 0, 1), (3, 512, 128,
 
 
 @pytest.mark.parametrize("shape", TILE_SHAPES)
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
 @pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
 def test_cgemm_tensor_core_tile_widths(tnc, shape, tile, form):
     """Every tcgen05 tile width (128 x 64, 128 x 128, 128 x 256 real outputs
@@ -107,7 +107,7 @@ def test_cgemm_tensor_core_tile_widths(tnc, shape, tile, form):
     batch, M, N, K, tA, tB = shape
     if 4 <= tile <= 8 and (form != "split_bf16" or tA or not tB):
         pytest.skip("the on-chip split takes split-BF16 with K-major operands only")
-    if tile >= 9 and form != "split_bf16":
+    if tile >= 9 and form != "split_bf16":  # 9..12
         pytest.skip("the persistent plane kernel takes split-BF16 only")
     if (tile == 2 and N < 64) or (tile in (3, 8, 9, 11) and N < 128) or (tile in (4, 5, 10) and N < 64):
         pytest.skip("tile wider than N")
@@ -156,6 +156,7 @@ SCATTER_CASES = [  # batch, M, N, K, kernel, tile, form
     (4, 256, 128, 128, "tc", 4, "split_bf16"), (4, 256, 128, 256, "tc", 8, "split_bf16"),
     (4, 256, 128, 256, "tc", 9, "split_bf16"), (4, 256, 128, 64, "tc", 11, "split_bf16"),
     (2, 512, 256, 8, "tc", 11, "split_bf16"), (8, 128, 32, 64, "tc", 6, "split_bf16"),
+    (8, 256, 32, 4, "tc", 12, "split_bf16"), (4, 128, 64, 128, "tc", 12, "split_bf16"),
     (2, 128, 64, 1024, "tc", 5, "split_bf16"), (2, 256, 64, 128, "tc", 10, "split_bf16"),
     (4, 128, 64, 64, "tc", 2, "3xtf32"),
 ]
@@ -189,7 +190,8 @@ def test_cgemm_scattered_output(tnc, case):
 
 @pytest.mark.parametrize("shape,tile", [((2, 256, 128, 8, 0, 1), 9), ((2, 256, 128, 8, 0, 1), 10),
                                         ((4, 128, 64, 4, 0, 1), 10), ((1, 512, 256, 16, 1, 0), 9),
-                                        ((2, 256, 128, 8, 0, 1), 11), ((1, 256, 256, 4, 0, 1), 11)])
+                                        ((2, 256, 128, 8, 0, 1), 11), ((1, 256, 256, 4, 0, 1), 11),
+                                        ((4, 256, 32, 4, 0, 1), 12), ((2, 128, 64, 16, 1, 0), 12)])
 def test_cgemm_short_k_plane_tiles(tnc, shape, tile):
     """The persistent plane tiles on K < 32 (the k-block beyond the plane
     rows is zero-filled by TMA), on plain and scattered outputs."""
