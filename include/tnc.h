@@ -234,8 +234,17 @@ int tnc_cgemm_variant(const void* d_A, const void* d_B, void* d_C, int64_t batch
 /* Device-side error flag of the kernels with bounded waits (the tcgen05
  * pipeline): 0 if no wait has timed out on the current device since load,
  * else the code of the first timeout.  Synchronising read; *flag receives the
- * value.  A set flag means the affected contraction results are invalid. */
+ * value; returns TNC_ETIMEOUT when it is set.  A set flag means the affected
+ * contraction results are invalid. */
 int tnc_device_error(int* flag);
+
+/* Self-test of the bounded device wait the tcgen05 kernels use: one thread
+ * waits on an mbarrier phase that nothing completes, for limit_us
+ * microseconds (1 .. 10^6).  *timed_out receives 1 when the wait gave up (the
+ * expected outcome; returns TNC_ETIMEOUT), 0 otherwise (TNC_OK).  Touches no
+ * other state; the device stays usable.  Synchronous, on the current device.
+ * The paper has no counterpart. */
+int tnc_selftest_bounded_wait(unsigned limit_us, int* timed_out);
 
 /* Autotuner: for every contraction step of the plan, time each kernel
  * variant that can run it on this GPU (tile shapes of the CUDA-core cGEMM,

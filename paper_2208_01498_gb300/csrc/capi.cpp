@@ -17,6 +17,7 @@
 namespace tnc {
 
 int read_tc_error(int* flag);
+int bounded_wait_selftest(uint64_t limit_ns, int* timed_out);
 
 static thread_local std::string g_err;
 
@@ -869,6 +870,24 @@ int tnc_device_error(int* flag) {
   }
   int r = tnc::read_tc_error(flag);
   if (r) return cuda_fail((cudaError_t)r, "tnc_device_error");
+  if (*flag) {
+    set_error("tnc_device_error: a bounded device wait gave up (code %d)", *flag);
+    return TNC_ETIMEOUT;
+  }
+  return TNC_OK;
+}
+
+int tnc_selftest_bounded_wait(unsigned limit_us, int* timed_out) {
+  if (!timed_out || limit_us == 0 || limit_us > 1000000) {
+    set_error("tnc_selftest_bounded_wait: invalid argument");
+    return TNC_EINVAL;
+  }
+  int r = tnc::bounded_wait_selftest((uint64_t)limit_us * 1000, timed_out);
+  if (r) return cuda_fail((cudaError_t)r, "tnc_selftest_bounded_wait");
+  if (*timed_out) {
+    set_error("tnc_selftest_bounded_wait: the wait gave up after %u us", limit_us);
+    return TNC_ETIMEOUT;
+  }
   return TNC_OK;
 }
 

@@ -69,14 +69,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait on a phase of an mbarrier: false after kWaitLimitNs
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait on a phase of an mbarrier: false after limit_ns
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer() - t0 > kWaitLimitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
+}
+
+// The kernels' bounded wait on an mbarrier that nothing arrives at: result
+// 1 when the wait gave up after limit_ns (the expected outcome), 0 if the
+// phase completed.  One thread; no other state is touched.
+__global__ void bounded_wait_selftest_kernel(uint64_t limit_ns, int* result) {
+  __shared__ uint64_t bar;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  *result = mbar_wait(&bar, 0, limit_ns) ? 0 : 1;
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
@@ -1289,6 +1299,17 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
 
 int read_tc_error(int* flag) {
   return (int)cudaMemcpyFromSymbol(flag, tc_error_flag, sizeof(int));
+}
+
+int bounded_wait_selftest(uint64_t limit_ns, int* timed_out) {
+  int* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e != cudaSuccess) return (int)e;
+  bounded_wait_selftest_kernel<<<1, 1>>>(limit_ns, d);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(timed_out, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return (int)e;
 }
 
 }  // namespace tnc

@@ -66,7 +66,7 @@ EXPORTED = [
     "tnc_server_destroy", "tnc_plan_set_profiling", "tnc_plan_get_profile", "tnc_device_error",
     "tnc_contract_amplitudes_static", "tnc_permute", "tnc_cgemm_scratch_bytes", "tnc_cgemm",
     "tnc_ssa_separate", "tnc_centerpoint", "tnc_plan_autotune", "tnc_plan_get_kernels",
-    "tnc_plan_set_kernels", "tnc_cgemm_variant",
+    "tnc_plan_set_kernels", "tnc_cgemm_variant", "tnc_selftest_bounded_wait",
 ]
 
 # kernel variants of a contraction step (TNC_KG_* in tnc.h)
@@ -111,6 +111,7 @@ def _load():
         "tnc_cgemm_scratch_bytes": (sz, [C.c_int64] * 4 + [i]),
         "tnc_cgemm": (i, [vp, vp, vp] + [C.c_int64] * 4 + [i, i, i, vp, sz, vp]),
         "tnc_cgemm_variant": (i, [vp, vp, vp] + [C.c_int64] * 4 + [i, i, i, i, i, vp, vp, sz, vp]),
+        "tnc_selftest_bounded_wait": (i, [C.c_uint, C.POINTER(C.c_int)]),
         "tnc_plan_get_profile": (i, [vp, C.POINTER(i), i, C.POINTER(C.c_double), C.POINTER(i),
                                      C.POINTER(i), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     }

@@ -71,3 +71,20 @@ def test_tensor_core_error_flag_clear(tnc):
     flag = ctypes.c_int(-1)
     assert tnc.lib.tnc_device_error(ctypes.byref(flag)) == 0
     assert flag.value == 0
+
+
+def test_bounded_wait_gives_up_and_device_stays_usable(tnc):
+    """The kernels' bounded mbarrier wait, on a phase nothing completes, gives
+    up after its limit with TNC_ETIMEOUT; the context stays usable and the
+    kernels' error flag is untouched."""
+    import ctypes
+    timed_out = ctypes.c_int(-1)
+    rc = tnc.lib.tnc_selftest_bounded_wait(20000, ctypes.byref(timed_out))  # 20 ms
+    assert rc == tnc.TNC_ETIMEOUT and timed_out.value == 1
+    gl = C.random_2d(3, 3, 6, 1)
+    bits = C.random_bitstrings(9, 4, 2)
+    got, _ = _run(tnc, gl, bits, "split_bf16")
+    assert O.rel_error(got, O.statevector_amplitudes(gl, bits), 9).max() <= TOL["split_bf16"]
+    flag = ctypes.c_int(-1)
+    assert tnc.lib.tnc_device_error(ctypes.byref(flag)) == 0
+    assert flag.value == 0
