@@ -164,6 +164,7 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
     if (g0.form == TNC_SPLIT_BF16 && g0.N >= 128 && g0.K <= 256) {
       add(KG_TC, 9);
       add(KG_TC, 11);
+      if (!g0.transA) add(KG_TC, 13);
     }
   } else if (g0.form == TNC_SPLIT_BF16 && pow2 && g0.M >= 128 && g0.N >= 32 && g0.K >= 4 && g0.K < 32) {
     // short K: the persistent plane tiles (k-block zero-filled by TMA)
@@ -172,6 +173,7 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
     if (g0.N >= 128) {
       add(KG_TC, 9);
       add(KG_TC, 11);
+      if (g0.K >= 16 && !g0.transA) add(KG_TC, 13);
     }
   }
   *n = k;

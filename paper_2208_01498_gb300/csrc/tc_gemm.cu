@@ -437,6 +437,7 @@ template <int BN>
 struct FzCfg {
   static constexpr int kBN = BN;
   static constexpr bool kPlanes = false;
+  static constexpr bool kHybrid = false;
   static constexpr int kRowBytes = BN == 256 ? 64 : 128;
   static constexpr int kChunks = kRowBytes / 16;              // 16-byte chunks per row
   static constexpr int kKC = kRowBytes / 4;                   // complex k per k-block
@@ -501,6 +502,7 @@ template <int BN, int ROW = 128>
 struct PlCfg {
   static constexpr int kBN = BN;
   static constexpr bool kPlanes = true;
+  static constexpr bool kHybrid = false;
   static constexpr int kRowBytes = ROW;  // 64-byte rows keep BN = 256 at two stages of 48 KB
   // staging blocks per epilogue step: two unless the shared memory is full
   static constexpr int kStageBlocks = (BN == 256 && ROW == 128) ? 1 : 2;
@@ -516,6 +518,36 @@ struct PlCfg {
   static constexpr bool kSum = BN != 256;
   static constexpr int kTmemCols = BN == 256 ? 512 : (3 * BN <= 256 ? 256 : 512);
   __device__ static uint64_t desc(uint32_t saddr) { return kRowBytes == 128 ? sw128_desc(saddr) : sw64_desc(saddr); }
+};
+
+// Hybrid: A split on chip by converter warps (as FzCfg), B' streamed by TMA
+// from its pre-split planes (as PlCfg).  For nodes whose B is small and
+// re-read by many row tiles while A is large and read by few column tiles,
+// this drops the A plane pass (write + read back) of the plane kernels.
+// 256 columns, 64-byte rows (two 48 KB stages), K <= 256 (no running sum).
+struct HyCfg {
+  static constexpr int kBN = 256;
+  static constexpr bool kPlanes = true;
+  static constexpr bool kHybrid = true;
+  static constexpr int kRowBytes = 64;
+  static constexpr int kChunks = kRowBytes / 16;
+  static constexpr int kKC = kRowBytes / 4;
+  static constexpr int kKSteps = kRowBytes / 32;
+  static constexpr int kChunkKB = 512 / (kRowBytes / 2);
+  static constexpr int kATasks = 128 * kChunks;               // all converter tasks are A tasks
+  static constexpr int kConvWarps = kATasks / 128;            // 4 tasks per thread: 4 warps
+  static constexpr int kConvThreads = 32 * kConvWarps;
+  static constexpr int kEpiWarps = 8;
+  static constexpr int kStageBlocks = 2;
+  static constexpr int kThreads = 32 * (kEpiWarps + 2 + kConvWarps);
+  static constexpr int kFullArrivals = kConvThreads + 1;      // converters + the producer's expect_tx
+  static constexpr uint32_t kATileBytes = 128 * kRowBytes;
+  static constexpr uint32_t kBTileBytes = 256 * kRowBytes;
+  static constexpr uint32_t kStageBytes = 2 * kATileBytes + 2 * kBTileBytes;
+  static constexpr bool kSum = false;
+  static constexpr int kTmemCols = 512;
+  __device__ static uint32_t swz(int row, int chunk) { return (uint32_t)(row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4)); }
+  __device__ static uint64_t desc(uint32_t saddr) { return sw64_desc(saddr); }
 };
 
 struct PlMaps {
@@ -595,10 +627,9 @@ __device__ __forceinline__ void fz_tile(const FzGeom& g, int64_t t, int& bz, int
   n0 = (r / g.tiles_m) * BN;
 }
 
-template <int BN>
+template <class Cf>
 __device__ __forceinline__ void fz_load(FzRegs& R, const float2* __restrict__ A, const float2* __restrict__ B,
                                         const FzGeom& g, int bz, int m0, int n0, int kb, int ct) {
-  using Cf = FzCfg<BN>;
   const int64_t koff = (int64_t)kb * Cf::kKC + 4 * (ct % Cf::kChunks);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -612,10 +643,9 @@ __device__ __forceinline__ void fz_load(FzRegs& R, const float2* __restrict__ A,
 
 // L2 prefetch of a k-block's lines (one thread per 128-byte line), so that
 // a second k-block of loads is on its way without holding registers
-template <int BN>
+template <class Cf>
 __device__ __forceinline__ void fz_prefetch(const float2* __restrict__ A, const float2* __restrict__ B,
                                             const FzGeom& g, int bz, int m0, int n0, int kb, int ct) {
-  using Cf = FzCfg<BN>;
   if (ct & 3) return;
   const int64_t koff = (int64_t)kb * Cf::kKC + 4 * (ct % Cf::kChunks);
 #pragma unroll
@@ -627,9 +657,8 @@ __device__ __forceinline__ void fz_prefetch(const float2* __restrict__ A, const 
   }
 }
 
-template <int BN>
+template <class Cf>
 __device__ __forceinline__ void fz_store(const FzRegs& R, uint32_t st, int ct) {
-  using Cf = FzCfg<BN>;
   constexpr uint32_t kAl = Cf::kATileBytes, kB = 2 * Cf::kATileBytes, kBl = kB + Cf::kBTileBytes;
   const int cc = ct % Cf::kChunks;
 #pragma unroll
@@ -743,10 +772,14 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
             break;
           }
           uint8_t* st = smem + s * kStageBytes;
-          mbar_expect_tx(&full[s], kStageBytes);
           const int kx = kb * (Cf::kKC * 2);  // first bf16 column of the k-block
-          tma_load_3d(st, &maps.ah, &full[s], kx, m0, bz);
-          tma_load_3d(st + Cf::kATileBytes, &maps.al, &full[s], kx, m0, bz);
+          if (Cf::kHybrid) {
+            mbar_expect_tx(&full[s], 2 * Cf::kBTileBytes);  // the converters fill the A tiles
+          } else {
+            mbar_expect_tx(&full[s], kStageBytes);
+            tma_load_3d(st, &maps.ah, &full[s], kx, m0, bz);
+            tma_load_3d(st + Cf::kATileBytes, &maps.al, &full[s], kx, m0, bz);
+          }
           tma_load_3d(st + 2 * Cf::kATileBytes, &maps.bh, &full[s], kx, n0, bz);
           tma_load_3d(st + 2 * Cf::kATileBytes + Cf::kBTileBytes, &maps.bl, &full[s], kx, n0, bz);
           ++tma_issued;
@@ -758,9 +791,10 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
         if (!ok) break;
       }
     }
-  } else if (!Cf::kPlanes && warp >= E + 1) {
+  } else if (warp >= E + 1 + (Cf::kPlanes ? 1 : 0)) {
+   if constexpr (!Cf::kPlanes || Cf::kHybrid) {
     // converters: global k-block q = (local tile) * nk + kb
-    const int ct = threadIdx.x - 32 * (E + 1);
+    const int ct = threadIdx.x - 32 * (E + 1 + (Cf::kHybrid ? 1 : 0));
     const int64_t total = my_tiles * nk;
     FzRegs R0;
     // load cursor: local tile lt_ld (coordinates bz, m0, n0), k-block kb_ld
@@ -768,7 +802,7 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
     int kb_ld = 0, bz = 0, m0 = 0, n0 = 0;
     if (my_tiles > 0) fz_tile<BN>(geo, blockIdx.x, bz, m0, n0);
     auto load_next = [&](FzRegs& R) {
-      fz_load<BN>(R, A, B, geo, bz, m0, n0, kb_ld, ct);
+      fz_load<Cf>(R, A, B, geo, bz, m0, n0, kb_ld, ct);
       if (++kb_ld == nk) {
         kb_ld = 0;
         if (++lt_ld < my_tiles) fz_tile<BN>(geo, (int64_t)blockIdx.x + lt_ld * gridDim.x, bz, m0, n0);
@@ -788,7 +822,7 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
         return false;
       }
       if (*(volatile int*)abort_flag) return false;
-      fz_store<BN>(R, smem_u32(smem + s * kStageBytes), ct);
+      fz_store<Cf>(R, smem_u32(smem + s * kStageBytes), ct);
       // make the generic-proxy stores visible to the tensor core, then signal
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[s])) : "memory");
@@ -797,11 +831,12 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
         ph ^= 1u;
       }
       if (q + 1 < total) load_next(R);
-      if (PREFETCH && q + 2 < total) fz_prefetch<BN>(A, B, geo, bz, m0, n0, kb_ld, ct);  // cursor is at q + 2
+      if (PREFETCH && q + 2 < total) fz_prefetch<Cf>(A, B, geo, bz, m0, n0, kb_ld, ct);  // cursor is at q + 2
       return true;
     };
     for (int64_t q = 0; q < total; ++q)
       if (!step(R0, q)) break;
+   }
   } else if (warp == E) {
     if (lane == 0) {
       bool ok = true;
@@ -1178,7 +1213,7 @@ int make_map(CUtensorMap* m, void* base, bool tf32, int64_t cols, int64_t rows, 
 // of 128-byte rows x 128 (A) or box_n (B) rows)
 template <bool kTF32>
 int prep_planes(const GemmDesc& d, const float2* A, const float2* B, uint8_t* scratch, int box_n, PlMaps& maps,
-                cudaStream_t st, int row_bytes = 128) {
+                cudaStream_t st, int row_bytes = 128, bool with_a = true) {
   const int64_t M = d.M, N2 = 2 * d.N, K2 = 2 * d.K, nb = d.batch;
   const int es = kTF32 ? 4 : 2;
   uint8_t* a_hi = scratch;
@@ -1188,7 +1223,9 @@ int prep_planes(const GemmDesc& d, const float2* A, const float2* B, uint8_t* sc
   const int64_t na = nb * M * d.K, nbb = nb * d.N * d.K;
   auto blocks = [](int64_t n) { return (unsigned)(n / 256 + 1 < 152 * 32 ? n / 256 + 1 : 152 * 32); };
   const bool kpow2 = (d.K & (d.K - 1)) == 0;
-  if (!d.transA && ((uintptr_t)A & 15) == 0)
+  if (!with_a) {
+    // A is split on chip by the kernel
+  } else if (!d.transA && ((uintptr_t)A & 15) == 0)
     prep_a_vec_kernel<kTF32><<<blocks(na / 4), 256, 0, st>>>((const float4*)A, a_hi, a_lo, na / 4);
   else
     prep_a_kernel<kTF32><<<blocks(na), 256, 0, st>>>(A, a_hi, a_lo, M, d.K, na, d.transA);
@@ -1198,8 +1235,8 @@ int prep_planes(const GemmDesc& d, const float2* A, const float2* B, uint8_t* sc
   else
     prep_b_kernel<kTF32><<<blocks(nbb), 256, 0, st>>>(B, b_hi, b_lo, d.N, d.K, nbb, d.transB);
   int r;
-  if ((r = make_map(&maps.ah, a_hi, kTF32, K2, M, nb, BM, row_bytes))) return r;
-  if ((r = make_map(&maps.al, a_lo, kTF32, K2, M, nb, BM, row_bytes))) return r;
+  if (with_a && (r = make_map(&maps.ah, a_hi, kTF32, K2, M, nb, BM, row_bytes))) return r;
+  if (with_a && (r = make_map(&maps.al, a_lo, kTF32, K2, M, nb, BM, row_bytes))) return r;
   if ((r = make_map(&maps.bh, b_hi, kTF32, K2, N2, nb, box_n, row_bytes))) return r;
   if ((r = make_map(&maps.bl, b_lo, kTF32, K2, N2, nb, box_n, row_bytes))) return r;
   return 0;
@@ -1212,6 +1249,15 @@ int run_tc_planes(const GemmDesc& d, const float2* A, const float2* B, float* C,
   int r = prep_planes<false>(d, A, B, scratch, BN, maps, st, ROW);
   if (r) return r;
   return launch_persistent<PlCfg<BN, ROW>, false>(d, A, B, C, maps, st);
+}
+
+// hybrid: B' planes through TMA, A split on chip
+int run_tc_hybrid(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_t* scratch, cudaStream_t st) {
+  PlMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  int r = prep_planes<false>(d, A, B, scratch, 256, maps, st, HyCfg::kRowBytes, false);
+  if (r) return r;
+  return launch_persistent<HyCfg, false>(d, A, B, C, maps, st);
 }
 
 template <bool kTF32, int BN, int STAGES>
@@ -1248,7 +1294,8 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
                    cudaStream_t st) {
   // the persistent plane tiles (9, 10) also take short K (a power of two
   // >= 4): TMA fills the k-block beyond the plane rows with zeros
-  const bool short_k = d.tile >= 9 && d.tile <= 12 && d.K >= 4 && d.K < 32 && !(d.K & (d.K - 1));
+  const bool short_k = ((d.tile >= 9 && d.tile <= 12) || (d.tile == 13 && d.K >= 16)) && d.K >= 4 && d.K < 32 &&
+                       !(d.K & (d.K - 1));
   if (d.M < BM || d.N < 32 || (d.K < 32 && !short_k) || (d.M % BM) || (d.N % 32) || (d.K % 32 && !short_k) ||
       d.M > (1 << 30) || 2 * d.N > (1 << 30) || 2 * d.K > (1 << 30))
     return (int)cudaErrorInvalidValue;
@@ -1263,9 +1310,10 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   // split done on chip (split-BF16, K-major operands), 5 and 7 with an L2
   // prefetch of the k-block after next; 9: 128 x 256 (K <= 256) and
   // 10: 128 x 128, persistent from the planes (split-BF16); 11: as 9 with
-  // 64-byte rows and two staging blocks per epilogue step; 12: 128 x 64
+  // 64-byte rows and two staging blocks per epilogue step; 12: 128 x 64;
+  // 13: 128 x 256 (K <= 256) with A split on chip and B' from its planes
   const int tile = d.tile ? d.tile : (d.N >= 64 ? 2 : 1);
-  if (tile < 1 || tile > 12 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
+  if (tile < 1 || tile > 13 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
       (tile >= 4 && tile <= 8 && (d.transA || !d.transB)) || (tile >= 4 && tf32) ||
       ((tile == 4 || tile == 5 || tile == 10) && d.N < 64) ||
       ((tile == 8 || tile == 9 || tile == 11) && (d.N < 128 || d.K > 256)))
@@ -1274,6 +1322,12 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   if (tile == 10) return run_tc_planes<128, 128>(d, A, B, (float*)C, scratch, st);
   if (tile == 11) return run_tc_planes<256, 64>(d, A, B, (float*)C, scratch, st);
   if (tile == 12) return run_tc_planes<64, 128>(d, A, B, (float*)C, scratch, st);
+  if (tile == 13) {
+    // A split on chip: K-major, 16-byte aligned, K a multiple of 16
+    if (tf32 || d.transA || d.N < 128 || d.K > 256 || d.K % 16 || ((uintptr_t)A & 15))
+      return (int)cudaErrorInvalidValue;
+    return run_tc_hybrid(d, A, B, (float*)C, scratch, st);
+  }
   if (tile >= 4) {
     const bool aligned = ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0;
     if (aligned && tile <= 5 && fused_launchable<128>())
