@@ -215,7 +215,8 @@ int tnc_cgemm(const void* d_A, const void* d_B, void* d_C, int64_t batch, int64_
  * 11: 128 x 256 (K <= 256, 64-byte rows) and 12: 128 x 64, split-BF16 from
  * the hi/lo planes in a persistent kernel, also for K = 4, 8 or 16;
  * 13: 128 x 256 (K <= 256, transA = 0) with A split on chip and B' from its
- * planes; -1: any; 0 for the other kernels).  The variants are those a plan's autotuner may pick for the
+ * planes; 14 and 15: 128 x 256 split on chip for any K (15 with prefetch),
+ * K-major operands; -1: any; 0 for the other kernels).  The variants are those a plan's autotuner may pick for the
  * shape; TNC_EINVAL for one that cannot run it.  c_pos (HOST, may be NULL):
  * C stored in a consumer's bit order, as in a plan: with nN = log2 N,
  * nM = log2 M, nB = log2 batch (all powers of two), bit i of n goes to output

@@ -158,6 +158,10 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
       add(KG_TC, 6);
       add(KG_TC, 7);
       if (g0.N >= 128 && g0.K <= 256) add(KG_TC, 8);
+      if (g0.N >= 128) {
+        add(KG_TC, 14);
+        add(KG_TC, 15);
+      }
     }
     if (g0.form == TNC_SPLIT_BF16 && g0.N >= 64) add(KG_TC, 10);
     if (g0.form == TNC_SPLIT_BF16) add(KG_TC, 12);

@@ -438,6 +438,7 @@ struct FzCfg {
   static constexpr int kBN = BN;
   static constexpr bool kPlanes = false;
   static constexpr bool kHybrid = false;
+  static constexpr int kSlots = 2;  // TMEM accumulator slots (alternating chunks / tiles)
   static constexpr int kRowBytes = BN == 256 ? 64 : 128;
   static constexpr int kChunks = kRowBytes / 16;              // 16-byte chunks per row
   static constexpr int kKC = kRowBytes / 4;                   // complex k per k-block
@@ -503,6 +504,7 @@ struct PlCfg {
   static constexpr int kBN = BN;
   static constexpr bool kPlanes = true;
   static constexpr bool kHybrid = false;
+  static constexpr int kSlots = 2;
   static constexpr int kRowBytes = ROW;  // 64-byte rows keep BN = 256 at two stages of 48 KB
   // staging blocks per epilogue step: two unless the shared memory is full
   static constexpr int kStageBlocks = (BN == 256 && ROW == 128) ? 1 : 2;
@@ -529,6 +531,7 @@ struct HyCfg {
   static constexpr int kBN = 256;
   static constexpr bool kPlanes = true;
   static constexpr bool kHybrid = true;
+  static constexpr int kSlots = 2;
   static constexpr int kRowBytes = 64;
   static constexpr int kChunks = kRowBytes / 16;
   static constexpr int kKC = kRowBytes / 4;
@@ -548,6 +551,17 @@ struct HyCfg {
   static constexpr int kTmemCols = 512;
   __device__ static uint32_t swz(int row, int chunk) { return (uint32_t)(row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4)); }
   __device__ static uint64_t desc(uint32_t saddr) { return sw64_desc(saddr); }
+};
+
+// 256 columns split on chip for any K: one TMEM accumulator slot plus the
+// running sum (256 + 256 columns).  The MMA waits while the epilogue folds
+// each chunk into the sum; the converters, which set the pace on long-K
+// nodes, run on meanwhile, and each A tile is converted for half as many
+// column tiles as with 128 columns.
+struct FzWideCfg : FzCfg<256> {
+  static constexpr bool kSum = true;
+  static constexpr int kSlots = 1;
+  static constexpr int kTmemCols = 512;
 };
 
 struct PlMaps {
@@ -845,8 +859,8 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
       uint32_t ph = 0;      // ring wraps before it, mod 2
       for (int64_t lt = 0; lt < my_tiles && ok; ++lt) {
         for (int c = 0; c < nchunks && ok; ++c, ++gc) {
-          const int slot = (int)(gc & 1);
-          if (gc >= 2 && !mbar_wait(&acc_empty[slot], (uint32_t)(((gc >> 1) + 1) & 1))) {
+          const int slot = (int)(gc % Cf::kSlots);
+          if (gc >= Cf::kSlots && !mbar_wait(&acc_empty[slot], (uint32_t)(((gc / Cf::kSlots) + 1) & 1))) {
             atomicExch(&tc_error_flag, 4);
             *(volatile int*)abort_flag = 1;
             ok = false;
@@ -894,7 +908,7 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
     // [half * CW, half * CW + CW)
     const int quarter = warp & 3, half = warp >> 2;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-    const uint32_t tsum = tmem + lane_base + 2 * BN;
+    const uint32_t tsum = tmem + lane_base + Cf::kSlots * BN;
     uint64_t* ct = coltab + warp * (CW / 2);
     float2* so = stage_out + warp * 256 * Cf::kStageBlocks;
     uint32_t idx_row = 0;
@@ -915,8 +929,8 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
         for (int i = lane; i < CW / 2; i += 32) ct[i] = om.col(n0 / 2 + half * (CW / 2) + i);
       __syncwarp();
       for (int c = 0; c < nchunks; ++c, ++gc) {
-        const int slot = (int)(gc & 1);
-        if (!mbar_wait(&acc_full[slot], (uint32_t)((gc >> 1) & 1))) {
+        const int slot = (int)(gc % Cf::kSlots);
+        if (!mbar_wait(&acc_full[slot], (uint32_t)((gc / Cf::kSlots) & 1))) {
           atomicExch(&tc_error_flag, 3);
           *(volatile int*)abort_flag = 1;
           ok = false;
@@ -1311,9 +1325,11 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   // prefetch of the k-block after next; 9: 128 x 256 (K <= 256) and
   // 10: 128 x 128, persistent from the planes (split-BF16); 11: as 9 with
   // 64-byte rows and two staging blocks per epilogue step; 12: 128 x 64;
-  // 13: 128 x 256 (K <= 256) with A split on chip and B' from its planes
+  // 13: 128 x 256 (K <= 256) with A split on chip and B' from its planes;
+  // 14, 15: 128 x 256 split on chip for any K (one TMEM slot + running sum),
+  // 15 with the L2 prefetch
   const int tile = d.tile ? d.tile : (d.N >= 64 ? 2 : 1);
-  if (tile < 1 || tile > 13 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
+  if (tile < 1 || tile > 15 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
       (tile >= 4 && tile <= 8 && (d.transA || !d.transB)) || (tile >= 4 && tf32) ||
       ((tile == 4 || tile == 5 || tile == 10) && d.N < 64) ||
       ((tile == 8 || tile == 9 || tile == 11) && (d.N < 128 || d.K > 256)))
@@ -1322,6 +1338,17 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   if (tile == 10) return run_tc_planes<128, 128>(d, A, B, (float*)C, scratch, st);
   if (tile == 11) return run_tc_planes<256, 64>(d, A, B, (float*)C, scratch, st);
   if (tile == 12) return run_tc_planes<64, 128>(d, A, B, (float*)C, scratch, st);
+  if (tile == 14 || tile == 15) {
+    // 256 columns split on chip, any K (a multiple of 16)
+    if (tf32 || d.transA || !d.transB || d.N < 128 || d.K % 16) return (int)cudaErrorInvalidValue;
+    if (((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0 && fused_launchable<256>()) {
+      PlMaps none;
+      std::memset(&none, 0, sizeof(none));
+      return tile == 15 ? launch_persistent<FzWideCfg, true>(d, A, B, (float*)C, none, st)
+                        : launch_persistent<FzWideCfg, false>(d, A, B, (float*)C, none, st);
+    }
+    return run_tc<false, 128, 3>(d, A, B, (float*)C, scratch, st);
+  }
   if (tile == 13) {
     // A split on chip: K-major, 16-byte aligned, K a multiple of 16
     if (tf32 || d.transA || d.N < 128 || d.K > 256 || d.K % 16 || ((uintptr_t)A & 15))

@@ -66,7 +66,8 @@ struct GemmDesc {
                         // split-BF16 split on chip (5, 7: with prefetch); 9 N = 256
                         // (K <= 256), 10 N = 128, 11 N = 256 with 64-byte rows, 12 N = 64:
                         // persistent from the planes (9-12 also for K = 4..16); 13 N = 256
-                        // (K <= 256): A split on chip, B' from its planes
+                        // (K <= 256): A split on chip, B' from its planes; 14, 15 N = 256 split
+                        // on chip for any K (one TMEM slot + running sum; 15: with prefetch)
 };
 
 // One problem of a grouped launch of narrow nodes (N, K <= 16): the same
@@ -110,7 +111,7 @@ void choose_gemm_kernel(GemmDesc& g);
 uint64_t gemm_scratch_bytes(const GemmDesc& g);
 // every kernel variant that can run this node (the default choice first)
 void gemm_candidates(const GemmDesc& g, GemmDesc* out, int* n);
-constexpr int kMaxCandidates = 18;
+constexpr int kMaxCandidates = 20;
 int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, void* stream);
 int launch_grouped_narrow(const GroupedDesc* d_descs, int n, int64_t total_blocks, const void* base, void* ws,
                           void* stream);

@@ -97,7 +97,7 @@ TILE_SHAPES = [(2, 128, 128, 64, 0, 1), (1, 256, 256, 4096, 0, 1), (3, 512, 128,
 
 
 @pytest.mark.parametrize("shape", TILE_SHAPES)
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15])
 @pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
 def test_cgemm_tensor_core_tile_widths(tnc, shape, tile, form):
     """Every tcgen05 tile width (128 x 64, 128 x 128, 128 x 256 real outputs
@@ -105,13 +105,13 @@ def test_cgemm_tensor_core_tile_widths(tnc, shape, tile, form):
     without and with prefetch; 128 x 256 and 128 x 128 persistent from the
     planes) on the same shapes, through tnc_cgemm_variant."""
     batch, M, N, K, tA, tB = shape
-    if 4 <= tile <= 8 and (form != "split_bf16" or tA or not tB):
+    if (4 <= tile <= 8 or tile >= 14) and (form != "split_bf16" or tA or not tB):
         pytest.skip("the on-chip split takes split-BF16 with K-major operands only")
     if tile >= 9 and form != "split_bf16":  # 9..12
         pytest.skip("the persistent plane kernel takes split-BF16 only")
     if tile == 13 and (form != "split_bf16" or tA):
         pytest.skip("the hybrid tile splits a K-major A on chip (split-BF16)")
-    if (tile == 2 and N < 64) or (tile in (3, 8, 9, 11, 13) and N < 128) or (tile in (4, 5, 10) and N < 64):
+    if (tile == 2 and N < 64) or (tile in (3, 8, 9, 11, 13, 14, 15) and N < 128) or (tile in (4, 5, 10) and N < 64):
         pytest.skip("tile wider than N")
     if tile in (8, 9, 11, 13) and K > 256:
         pytest.skip("the 256-column persistent tiles take K <= 256")
@@ -160,6 +160,7 @@ SCATTER_CASES = [  # batch, M, N, K, kernel, tile, form
     (2, 512, 256, 8, "tc", 11, "split_bf16"), (8, 128, 32, 64, "tc", 6, "split_bf16"),
     (8, 256, 32, 4, "tc", 12, "split_bf16"), (4, 128, 64, 128, "tc", 12, "split_bf16"),
     (4, 256, 128, 128, "tc", 13, "split_bf16"), (2, 512, 256, 16, "tc", 13, "split_bf16"),
+    (2, 256, 128, 2048, "tc", 14, "split_bf16"), (2, 128, 256, 1024, "tc", 15, "split_bf16"),
     (2, 128, 64, 1024, "tc", 5, "split_bf16"), (2, 256, 64, 128, "tc", 10, "split_bf16"),
     (4, 128, 64, 64, "tc", 2, "3xtf32"),
 ]
