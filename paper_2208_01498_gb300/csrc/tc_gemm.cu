@@ -695,10 +695,30 @@ __device__ __forceinline__ void fz_store(const FzRegs& R, uint32_t st, int ct) {
         l1[q] = __byte_perm(l[q], 0, 0x1032);
       }
       const int r0 = 2 * ((j - Cf::kATasks) / Cf::kChunks);
-      sts128(st + kB + Cf::swz(r0, cc), h0);
-      sts128(st + kBl + Cf::swz(r0, cc), l0);
-      sts128(st + kB + Cf::swz(r0 + 1, cc), h1);
-      sts128(st + kBl + Cf::swz(r0 + 1, cc), l1);
+      if constexpr (Cf::kRowBytes == 64) {
+        // rows 2n and 2n + 1 are the two halves of one 128-byte line: odd
+        // chunks store row 2n + 1 first, so that each instruction fills both
+        // halves of every line it touches (no bank conflicts)
+        const bool odd = cc & 1;
+        uint32_t ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ah[q] = odd ? h1[q] : h0[q];
+          al[q] = odd ? l1[q] : l0[q];
+          bh[q] = odd ? h0[q] : h1[q];
+          bl[q] = odd ? l0[q] : l1[q];
+        }
+        const int ra = r0 + (odd ? 1 : 0), rb = r0 + (odd ? 0 : 1);
+        sts128(st + kB + Cf::swz(ra, cc), ah);
+        sts128(st + kBl + Cf::swz(ra, cc), al);
+        sts128(st + kB + Cf::swz(rb, cc), bh);
+        sts128(st + kBl + Cf::swz(rb, cc), bl);
+      } else {
+        sts128(st + kB + Cf::swz(r0, cc), h0);
+        sts128(st + kBl + Cf::swz(r0, cc), l0);
+        sts128(st + kB + Cf::swz(r0 + 1, cc), h1);
+        sts128(st + kBl + Cf::swz(r0 + 1, cc), l1);
+      }
     }
   }
 }
