@@ -431,7 +431,9 @@ def run_ours(args):
                    "seed": args.seed, "real_tflop_per_request": rep["real_flops"] / 1e12,
                    "paper_ops_log2": rep["tree_cost_log2"], "ws_bytes": rep["ws_bytes"],
                    "l2": f"working set {rep['ws_bytes'] / 1e9:.1f} GB per request > 129 MB L2",
-                   "parallelism": f"dp{world} (independent requests)", "autotuned_steps": tuned},
+                   "parallelism": f"dp{world} (independent requests)", "autotuned_steps": tuned,
+                   "timing": "value: eager launches with per-step CUDA events (the roofline's source); "
+                             "e2e: CUDA-graph replay per slice group, host buffers"},
         "effective_tflops": world * args.steps * rep["real_flops"] / (t_ms / 1e3) / 1e12,
         "roofline": roof,
         "kernel_breakdown": breakdown,
