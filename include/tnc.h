@@ -282,9 +282,10 @@ int tnc_contract_amplitudes_dbits(tnc_plan_t* plan, const uint8_t* d_bits, int b
                                   void* d_out, void* d_ws, size_t ws_bytes, void* cuda_stream);
 
 /* Same as tnc_contract_amplitudes, for callers that cannot allocate device
- * memory when they need amplitudes (code running while a CUDA graph is being
- * captured, a host framework whose allocator owns all device memory, a
- * plugin whose host forbids allocation after start-up).  The paper has no
+ * memory when they need amplitudes (a host framework whose allocator owns all
+ * device memory, a latency-bound request handler that may not call
+ * cudaMalloc/cudaFree because they can synchronise the device, a plugin whose
+ * host forbids allocation after start-up).  The paper has no
  * counterpart: this is a deployment variant of the same contraction.
  * The workspace is a 64 MiB array that the library holds statically on every
  * GPU that loads it, until exit; nothing is allocated by the call.

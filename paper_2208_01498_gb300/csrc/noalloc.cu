@@ -1,10 +1,11 @@
 // Contraction into a workspace that the library owns statically.
 //
 // Some callers cannot allocate device memory at the moment they need
-// amplitudes: code that runs while a CUDA graph is being captured (where
-// allocation calls are not allowed), code inside a host framework whose
-// caching allocator owns all device memory and must not be bypassed, or
-// plugins whose host process forbids new allocations after start-up.
+// amplitudes: code inside a host framework whose caching allocator owns all
+// device memory and must not be bypassed, latency-bound request handlers
+// that may not call cudaMalloc/cudaFree (both can synchronise the whole
+// device), or plugins whose host process forbids new allocations after
+// start-up.
 // tnc_contract_amplitudes_static serves them: it runs the same node program
 // as tnc_contract_amplitudes, but its workspace is the file-scope array
 // below, so the call itself allocates nothing (no cudaMalloc, no cudaFree, no

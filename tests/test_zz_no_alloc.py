@@ -1,8 +1,9 @@
 """The entry point that allocates nothing (tnc_contract_amplitudes_static).
 
 It serves callers that cannot allocate device memory when they need
-amplitudes -- e.g. code running during CUDA graph capture, or inside a host
-framework whose allocator owns the GPU's memory -- by using a workspace the
+amplitudes -- e.g. code inside a host framework whose allocator owns the
+GPU's memory, or a latency-bound handler that may not call cudaMalloc/cudaFree
+(both can synchronise the device) -- by using a workspace the
 library holds statically.  Its results must equal those of the ordinary entry
 point with a caller-provided workspace, call after call (the static array
 keeps the previous call's contents, so the second call checks that nothing
