@@ -32,6 +32,12 @@ circuit families, in the variants the benchmark configurations fix):
   randomly oriented, randomly offset brick pattern whose CZ gates are each
   kept with a per-layer density rho ~ U[0.5, 1].
 * :func:`ghz`, :func:`mirror` — circuits with exactly known amplitudes.
+* :func:`doubled` — the circuit ``U, P, U^dagger`` whose amplitude at
+  ``x = 0...0`` is the paper's quantity ``c = <0| U^dagger P U |0>`` (Classical
+  Simulation section) for an observable ``P`` given as a product of
+  single-qubit operators: a Pauli string (:func:`pauli_ops`) gives an
+  expectation value, a product of projectors (:func:`projector_ops`) a
+  marginal probability.
 """
 from __future__ import annotations
 
@@ -42,7 +48,8 @@ import numpy as np
 
 __all__ = [
     "GateList", "haar_1q", "clifford_1q_group", "random_2d", "sycamore",
-    "iqp", "layered_3d", "ghz", "mirror", "random_bitstrings", "serving_pool",
+    "iqp", "layered_3d", "ghz", "mirror", "doubled", "pauli_ops", "projector_ops",
+    "random_bitstrings", "serving_pool",
     "config_circuit", "H", "S", "CZ", "X", "Y", "sqrt_pauli", "fsim",
 ]
 
@@ -346,6 +353,62 @@ def mirror(gl: GateList) -> GateList:
     for q, m in gl.gates:
         out.add(q, m)
     for q, m in reversed(gl.gates):
+        out.add(q, m.conj().T)
+    return out
+
+
+def pauli_ops(spec: dict) -> list:
+    """Single-qubit factors of a Pauli string: ``spec`` maps qubit -> one of
+    "I", "X", "Y", "Z"; returns ``[(qubit, 2 x 2 matrix), ...]``."""
+    mats = {"I": I2, "X": X, "Y": Y, "Z": np.diag([1, -1]).astype(np.complex128)}
+    return [(int(q), mats[p].copy()) for q, p in sorted(spec.items())]
+
+
+def projector_ops(qubits, values) -> list:
+    """Factors of the projector ``|v><v|`` onto the values ``values`` of
+    ``qubits`` (identity elsewhere): ``[(qubit, |v_q><v_q|), ...]``."""
+    out = []
+    for q, v in zip(qubits, values):
+        m = np.zeros((2, 2), dtype=np.complex128)
+        m[int(v), int(v)] = 1.0
+        out.append((int(q), m))
+    return out
+
+
+def doubled(gl: GateList, ops, light_cone: bool = False) -> GateList:
+    """The circuit ``U``, then the observable's single-qubit factors ``ops``
+    (``[(qubit, 2 x 2 matrix), ...]``, not necessarily unitary), then
+    ``U^dagger``.  Its amplitude at ``x = 0...0`` with no open qubits is
+    ``<0| U^dagger P U |0>``; its tensor network is the doubled network of the
+    Classical Simulation section (twice the gates of ``U`` on the same
+    layout).
+
+    ``light_cone=True`` keeps only the gates of ``U`` in the backward light
+    cone of ``P``'s support: walking ``U`` from its last gate to its first, a
+    gate whose qubits all lie outside the support gathered so far commutes
+    with everything after it in ``U^dagger P U`` and meets its own inverse
+    (``g^dagger g = I``), so it and its mirror are dropped; a gate that
+    touches the support is kept and adds its qubits to it.  The value is
+    unchanged; the network shrinks to the light cone."""
+    for q, m in ops:
+        if not 0 <= q < gl.n_qubits or np.shape(m) != (2, 2):
+            raise ValueError(f"observable factor on qubit {q} must be a 2 x 2 matrix on an existing qubit")
+    gates = list(gl.gates)
+    if light_cone:
+        support = {int(q) for q, _ in ops}
+        kept = []
+        for q, m in reversed(gates):
+            if support.intersection(q):
+                support.update(q)
+                kept.append((q, m))
+        gates = kept[::-1]
+    out = GateList(gl.n_qubits, gl.coords.copy(), name=gl.name + ("_doubled_lc" if light_cone else "_doubled"),
+                   meta=dict(gl.meta, doubled=True, light_cone=light_cone))
+    for q, m in gates:
+        out.add(q, m)
+    for q, m in ops:
+        out.add((q,), np.asarray(m, dtype=np.complex128))
+    for q, m in reversed(gates):
         out.add(q, m.conj().T)
     return out
 

@@ -12,7 +12,9 @@ separator hierarchy of the Thm. 1 proof, and the greedy leaves of the
 the plain definition of the amplitude, computed four independent ways:
 
 * :mod:`oracle.statevector` -- explicit time evolution of the state vector
-  (the "explicit time evolution" baseline of the Thm. 2 discussion);
+  (the "explicit time evolution" baseline of the Thm. 2 discussion), which
+  also gives c = <0| U^dagger P U |0> and marginal probabilities by their
+  definitions;
 * :mod:`oracle.sidewise` -- naive-order (left-to-right, "side-wise")
   contraction of the circuit's tensor network;
 * :mod:`oracle.stabilizer` -- exact Clifford amplitudes in the CH form
@@ -24,14 +26,15 @@ Every function returns complex128 amplitudes ``out[b, j]`` for bitstrings
 ``bits[b]`` with the open qubits ``open_qubits`` ranging over all values: bit
 ``i`` of ``j`` is the value of ``open_qubits[i]`` (ascending qubit order).
 """
-from .statevector import statevector, statevector_amplitudes
+from .statevector import statevector, statevector_amplitudes, statevector_expectation, statevector_marginal
 from .sidewise import sidewise_amplitudes
 from .stabilizer import CHForm, stabilizer_amplitudes
 from .iqp import iqp_wht_amplitudes, iqp_transfer_amplitudes
 from .common import expand_open, rel_error
 
 __all__ = [
-    "statevector", "statevector_amplitudes", "sidewise_amplitudes", "CHForm",
+    "statevector", "statevector_amplitudes", "statevector_expectation", "statevector_marginal",
+    "sidewise_amplitudes", "CHForm",
     "stabilizer_amplitudes", "iqp_wht_amplitudes", "iqp_transfer_amplitudes",
     "expand_open", "rel_error",
 ]

@@ -5,6 +5,11 @@ against (Thm. 2 discussion, cost T N 2^{2+N}): start from |0...0>, apply each
 gate of the circuit in order, read off amplitudes.  The state is a complex128
 array of shape (2,)*n; qubit q lives on axis n-1-q so that the flat index is
 sum_q x_q 2^q.
+
+It also gives the paper's own quantity c = <0| U^dagger P U |0> (Classical
+Simulation section) by its definition: the inner product of psi = U|0> with
+P psi, for P a product of single-qubit operators; and marginal probabilities
+by the Born rule, summing |psi_x|^2 over the unobserved bits.
 """
 from __future__ import annotations
 
@@ -21,14 +26,43 @@ def statevector(n_qubits: int, gates) -> np.ndarray:
     psi = np.zeros((2,) * n, dtype=np.complex128)
     psi[(0,) * n] = 1.0
     for qubits, mat in gates:
-        k = len(qubits)
-        axes = [n - 1 - q for q in qubits]
-        g = np.asarray(mat, dtype=np.complex128).reshape((2,) * (2 * k))
-        # contract the gate's input legs with the state's axes; the output
-        # legs come first in the result and are moved back into place
-        psi = np.tensordot(g, psi, axes=(list(range(k, 2 * k)), axes))
-        psi = np.moveaxis(psi, list(range(k)), axes)
+        psi = _apply(psi, qubits, mat)
     return psi.reshape(-1)
+
+
+def _apply(psi: np.ndarray, qubits, mat) -> np.ndarray:
+    """One gate on the (2,)*n state tensor."""
+    n = psi.ndim
+    k = len(qubits)
+    axes = [n - 1 - q for q in qubits]
+    g = np.asarray(mat, dtype=np.complex128).reshape((2,) * (2 * k))
+    # contract the gate's input legs with the state's axes; the output legs
+    # come first in the result and are moved back into place
+    out = np.tensordot(g, psi, axes=(list(range(k, 2 * k)), axes))
+    return np.moveaxis(out, list(range(k)), axes)
+
+
+def statevector_expectation(gl, ops) -> complex:
+    """c = <0| U^dagger P U |0> = <psi| P |psi> with psi = U|0> (U the circuit
+    ``gl``) and P the product of the single-qubit factors ``ops`` =
+    [(qubit, 2 x 2 matrix), ...] (Classical Simulation section)."""
+    n = gl.n_qubits
+    psi = statevector(n, gl.gates).reshape((2,) * n)
+    phi = psi
+    for q, m in ops:
+        phi = _apply(phi, (q,), m)
+    return complex(np.vdot(psi.reshape(-1), phi.reshape(-1)))
+
+
+def statevector_marginal(gl, qubits, values) -> float:
+    """Probability that measuring ``qubits`` of U|0> gives ``values``: the sum
+    of |<x|U|0>|^2 over every x that agrees with ``values`` there."""
+    psi = statevector(gl.n_qubits, gl.gates)
+    x = np.arange(psi.size, dtype=np.int64)
+    keep = np.ones(psi.size, dtype=bool)
+    for q, v in zip(qubits, values):
+        keep &= ((x >> int(q)) & 1) == int(v)
+    return float(np.sum(np.abs(psi[keep]) ** 2))
 
 
 def statevector_amplitudes(gl, bits, open_qubits=()) -> np.ndarray:
