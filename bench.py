@@ -219,6 +219,50 @@ def serving_measure(tnc, torch, form: str, seed: int = 0, n_req: int = 240, cost
     return result
 
 
+def expectation_measure(tnc, torch, form: str, seed: int = 0, reps: int = 20, warmup: int = 3):
+    """The paper's quantity c = <0|U^dagger P U|0> (Classical Simulation
+    section) for P = Z_27 Z_28 on the 8 x 8 depth-8 random circuit (64 qubits,
+    Haar single-qubit gates): the light-cone-reduced doubled network
+    contracted at x = 0 by the same executor, autotuned, timed with CUDA
+    events per value after ``warmup`` untimed values; the same value in the
+    FP32 form gives the relative difference."""
+    gl = C.random_2d(8, 8, 8, seed)
+    ops = C.pauli_ops({27: "Z", 28: "Z"})
+    dg = C.doubled(gl, ops, light_cone=True)
+    stream = torch.cuda.current_stream()
+    d_bits = torch.zeros((1, gl.n_qubits), dtype=torch.uint8, device="cuda")
+    res = {"workload": "rand2d_8x8_d8 <Z27 Z28>, doubled network, light cone", "form": form}
+    vals = {}
+    for f in dict.fromkeys((form, "fp32")):
+        p = tnc.Plan(tnc.Network(dg), form=f, seed=1, ssa_trials=64)
+        ws = tnc.alloc_workspace(p)
+        out = torch.empty((1, 1), dtype=torch.complex128, device="cuda")
+        p.upload(stream)
+        p.autotune(ws, stream)
+        for _ in range(warmup):
+            tnc.contract_amplitudes_dbits(p, d_bits, out=out, ws=ws, stream=stream)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tnc.contract_amplitudes_dbits(p, d_bits, out=out, ws=ws, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        vals[f] = complex(out.cpu().numpy().ravel()[0])
+        if f == form:
+            rep_ = p.report
+            res.update({"paper_ops_log2": rep_["tree_cost_log2"], "real_tflop": rep_["real_flops"] / 1e12,
+                        "ms_p50": float(np.percentile(times, 50)), "ms_p99": float(np.percentile(times, 99)),
+                        "values_per_s": 1e3 / float(np.percentile(times, 50)),
+                        "effective_tflops": rep_["real_flops"] / (float(np.percentile(times, 50)) / 1e3) / 1e12})
+        del ws
+    res["c"] = [vals[form].real, vals[form].imag]
+    res["rel_diff_vs_fp32"] = abs(vals[form] - vals["fp32"]) / max(abs(vals["fp32"]), 2.0 ** -32)
+    return res
+
+
 def _traffic(step, kernel, form, tile=0):
     """DRAM bytes per launch of this step from the committed ncu summary
     (profiles/traffic.json), scaled by batch; None if that shape and kernel
@@ -453,6 +497,8 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_measure(tnc, torch, args.form, args.seed)
+    if rank == 0 and not args.no_expectation:
+        line["expectation"] = expectation_measure(tnc, torch, args.form, args.seed)
     if rank == 0 and not args.no_cpu_baseline:
         v, n_done, dt = _cpu_oracle(gl, bits[args.warmup:args.warmup + 1])
         line["cpu_baseline"] = {"value": v, "unit": "amplitudes/s", "cores": 1, "kind": "oracle",
@@ -476,6 +522,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-mix latency measurement")
+    ap.add_argument("--no-expectation", action="store_true",
+                    help="skip the doubled-network expectation-value measurement")
     ap.add_argument("--tune-cache", default=None, help="JSON file to save / reuse the autotuner's kernel choices")
     ap.add_argument("--rows", type=int, default=5, help="IQP lattice rows (the benchmark uses 5 x 8)")
     ap.add_argument("--cols", type=int, default=8)
