@@ -253,6 +253,9 @@ def expectation_measure(tnc, torch, form: str, seed: int = 0, reps: int = 20, wa
         vals[f] = complex(out.cpu().numpy().ravel()[0])
         if f == form:
             rep_ = p.report
+            bd = tnc.Network(gl).bounds()
+            res["bounds_log2"] = {k: (round(bd[k], 1) if math.isfinite(bd[k]) else None)
+                                  for k in ("thm2_log2", "thm2_pst_log2", "sidewise_log2", "explicit_log2")}
             res.update({"paper_ops_log2": rep_["tree_cost_log2"], "real_tflop": rep_["real_flops"] / 1e12,
                         "ms_p50": float(np.percentile(times, 50)), "ms_p99": float(np.percentile(times, 99)),
                         "values_per_s": 1e3 / float(np.percentile(times, 50)),
@@ -481,6 +484,9 @@ def run_ours(args):
         "config": {"workload": workload_name(args.rows, args.cols), "form": args.form, "bitstrings_per_request": REQ_BATCH,
                    "seed": args.seed, "real_tflop_per_request": rep["real_flops"] / 1e12,
                    "paper_ops_log2": rep["tree_cost_log2"], "ws_bytes": rep["ws_bytes"],
+                   "paper_bounds_log2": {k: (round(v, 1) if math.isfinite(v) else None)
+                                         for k, v in net.bounds().items()
+                                         if k in ("thm2_log2", "thm2_pst_log2", "sidewise_log2", "explicit_log2")},
                    "l2": f"working set {rep['ws_bytes'] / 1e9:.1f} GB per request > 129 MB L2",
                    "parallelism": f"dp{world} (independent requests)", "autotuned_steps": tuned,
                    "timing": "value: CUDA events around the K steps, device-resident bitstrings, CUDA-graph "

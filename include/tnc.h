@@ -137,6 +137,30 @@ int tnc_ssa_separate(const double* pos, const double* rad, int n, int dim, uint6
  * in R^D (D <= 4), pts[n][D], by iterated Radon points; c[D] receives it. */
 int tnc_centerpoint(const double* pts, int n, int D, uint64_t seed, double* c);
 
+/* The paper's analytic cost bounds for a circuit (host only), all as log2
+ * of a number of scalar operations for c = <0| U^dagger P U |0> (the doubled
+ * network of the Classical Simulation section), beside which a plan's
+ * tree_cost_log2 can be read.  From desc: N = n_qubits, d = dim, f(x_i) =
+ * two-qubit gates on qubit i, F = max f, S = sum f, l = largest distance
+ * between the qubits of a two-qubit gate, r = smallest distance between two
+ * qubits, T = time steps (gates packed into layers as early as their qubits
+ * allow).  Bounds that need d >= 2, a two-qubit gate or r > 0 are NaN
+ * without them.  TNC_EINVAL for an invalid desc (as tnc_load_network). */
+typedef struct {
+  int n_qubits, dim, depth;   /* N, d, T */
+  double sum_f, max_f;        /* S, F */
+  double l, r;                /* gate range, qubit spacing */
+  double n_tensors, k;        /* Thm. 2 proof: n = 2 S tensors, overlap k = 2 F (1 + l/r)^d */
+  double a_d, a2_pst;         /* Thm. 1's a_d = c_d / (2 - 2 ((d+1)/(d+2))^(1-1/d)); a_2' with c_PST = 1.971 */
+  double thm1_log2;           /* Thm. 1 at n, M = 16, k: 1 + log2(n) / log2((d+2)/(d+1)) + a_d k^(1/d) n^(1-1/d) log2 M */
+  double thm2_log2;           /* Thm. 2: log2(2 S) / log2((d+2)/(d+1)) + 1 + 8 a_d (1 + l/r) F^(1/d) S^(1-1/d) */
+  double thm2_pst_log2;       /* Thm. 2, d = 2 and l = r (PST): log2(W) / log2(3/2) + 1 + 4 a_2' sqrt(W),
+                                 W = sum f (2 + f/2); NaN otherwise */
+  double sidewise_log2;       /* left-to-right contraction: 1 + 4 F N^(1-1/d) + log2(N) / d */
+  double explicit_log2;       /* explicit time evolution: log2(T N) + 2 + N */
+} tnc_circuit_bounds;
+int tnc_circuit_bounds_eval(const tnc_network_desc* desc, tnc_circuit_bounds* out);
+
 /* Plan the contraction (host only, no GPU needed): separator hierarchy
  * (Thm. 1 proof, Algorithm 1), greedy leaves, index slicing to meet
  * mem_cap_bytes, and the compiled node program.  The plan keeps what it needs

@@ -39,6 +39,17 @@ class NetworkDesc(C.Structure):
                 ("mats", C.POINTER(C.c_double))]
 
 
+class CircuitBounds(C.Structure):
+    _fields_ = [("n_qubits", C.c_int), ("dim", C.c_int), ("depth", C.c_int), ("sum_f", C.c_double),
+                ("max_f", C.c_double), ("l", C.c_double), ("r", C.c_double), ("n_tensors", C.c_double),
+                ("k", C.c_double), ("a_d", C.c_double), ("a2_pst", C.c_double), ("thm1_log2", C.c_double),
+                ("thm2_log2", C.c_double), ("thm2_pst_log2", C.c_double), ("sidewise_log2", C.c_double),
+                ("explicit_log2", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class PlanOpts(C.Structure):
     _fields_ = [("n_open", C.c_int), ("open_qubits", C.POINTER(C.c_int)), ("max_batch", C.c_int),
                 ("mem_cap_bytes", C.c_size_t), ("form", C.c_int), ("seed", C.c_uint64),
@@ -66,7 +77,7 @@ EXPORTED = [
     "tnc_server_destroy", "tnc_plan_set_profiling", "tnc_plan_get_profile", "tnc_device_error",
     "tnc_contract_amplitudes_static", "tnc_permute", "tnc_cgemm_scratch_bytes", "tnc_cgemm",
     "tnc_ssa_separate", "tnc_centerpoint", "tnc_plan_autotune", "tnc_plan_get_kernels",
-    "tnc_plan_set_kernels", "tnc_cgemm_variant", "tnc_selftest_bounded_wait",
+    "tnc_plan_set_kernels", "tnc_cgemm_variant", "tnc_selftest_bounded_wait", "tnc_circuit_bounds_eval",
 ]
 
 # kernel variants of a contraction step (TNC_KG_* in tnc.h)
@@ -105,6 +116,7 @@ def _load():
         "tnc_ssa_separate": (i, [C.POINTER(C.c_double), C.POINTER(C.c_double), i, i, u64, i, C.POINTER(i),
                                  C.POINTER(i), C.POINTER(i)]),
         "tnc_centerpoint": (i, [C.POINTER(C.c_double), i, i, u64, C.POINTER(C.c_double)]),
+        "tnc_circuit_bounds_eval": (i, [C.POINTER(NetworkDesc), C.POINTER(CircuitBounds)]),
         "tnc_plan_autotune": (i, [vp, vp, sz, vp, i, C.POINTER(i)]),
         "tnc_plan_get_kernels": (i, [vp, C.POINTER(i), i, C.POINTER(i)]),
         "tnc_plan_set_kernels": (i, [vp, C.POINTER(i), i]),
@@ -147,15 +159,29 @@ class Network:
             coords, arity, qubits, mats = arrays
             n = coords.shape[0]
         coords = np.ascontiguousarray(coords, np.float64)
+        self._n = int(n)
         self._keep = (coords, np.ascontiguousarray(arity, np.int32),
                       np.ascontiguousarray(qubits, np.int32), np.ascontiguousarray(mats, np.float64))
-        c, a, q, m = self._keep
-        desc = NetworkDesc(int(n), int(c.shape[1]) if c.ndim == 2 else 1, _ptr(c, C.c_double),
-                           int(a.shape[0]), _ptr(a, C.c_int), _ptr(q, C.c_int), _ptr(m, C.c_double))
+        desc = self.desc()
         h = C.c_void_p()
         _check(lib.tnc_load_network(C.byref(desc), C.byref(h)), "tnc_load_network")
         self.handle = h
         self.n_qubits = int(n)
+
+    def desc(self) -> NetworkDesc:
+        """The descriptor of the arrays this object keeps alive."""
+        c, a, q, m = self._keep
+        return NetworkDesc(self._n, int(c.shape[1]) if c.ndim == 2 else 1, _ptr(c, C.c_double),
+                           int(a.shape[0]), _ptr(a, C.c_int), _ptr(q, C.c_int), _ptr(m, C.c_double))
+
+    def bounds(self) -> dict:
+        """``tnc_circuit_bounds_eval``: the paper's cost bounds (Thm. 1, Thm. 2
+        and its planar form, left-to-right, explicit time evolution) for this
+        circuit's c = <0|U^dagger P U|0>, in log2 of scalar operations."""
+        out = CircuitBounds()
+        d = self.desc()
+        _check(lib.tnc_circuit_bounds_eval(C.byref(d), C.byref(out)), "tnc_circuit_bounds_eval")
+        return out.as_dict()
 
     def close(self):
         if self.handle:
