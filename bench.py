@@ -266,6 +266,53 @@ def expectation_measure(tnc, torch, form: str, seed: int = 0, reps: int = 20, wa
     return res
 
 
+def op_counts(reps: int = 10, seed: int = 0):
+    """The shape of the paper's op-count curves (Examples section; the IQP
+    figure and its Sycamore-type and Poisson-cavity counterparts) for the
+    paper's own families: per lattice size L, the mean and standard error over
+    ``reps`` seeded realizations of log2 of explicit time evolution (idle
+    qubits removed, as in the figure), left-to-right contraction, Thm. 2 (its
+    planar form where it applies) and the separator planner's tree for c =
+    <0|U^dagger P U|0> with P projectors on every qubit.  For the IQP family
+    the planner also runs on the circuit with its commuting diagonal gates
+    fused per pair.  Host only: no GPU is used."""
+    from paper_2208_01498_gb300 import tnc
+
+    def stats(v):
+        v = np.asarray(v, float)
+        return [round(float(v.mean()), 2), round(float(v.std(ddof=1) / math.sqrt(len(v))) if len(v) > 1 else 0.0, 2)]
+
+    def ssa(gl):
+        ops = C.projector_ops(range(gl.n_qubits), [0] * gl.n_qubits)
+        return tnc.Plan(tnc.Network(C.doubled(gl, ops)), seed=1).report["tree_cost_log2"]
+
+    families = {
+        "iqp_paper (T = L^2, gamma = 3)": ([3, 4, 5, 6, 7, 8], lambda L, s: C.iqp_paper(L, s)),
+        "sycamore_periods (q = 5, p = 0.88)": ([4, 8, 12, 16], lambda L, s: C.sycamore_periods(L, 5, 0.88, s)),
+        "cavity_3d (alpha = 0.1, S = 5, sigma = 10)": ([10, 20, 30], lambda L, s: C.cavity_3d(L, s)),
+    }
+    out = {}
+    for name, (sizes, make) in families.items():
+        rows = []
+        for L in sizes:
+            acc = {"explicit": [], "sidewise": [], "thm2": [], "ssa": [], "ssa_fused": []}
+            for r in range(reps):
+                gl = make(L, seed + r)
+                b = tnc.Network(gl).bounds()
+                touched = {q for qs, _ in gl.gates if len(qs) == 2 for q in qs}
+                acc["explicit"].append(b["explicit_log2"] - (gl.n_qubits - len(touched)))
+                acc["sidewise"].append(b["sidewise_log2"])
+                t2 = b["thm2_pst_log2"] if math.isfinite(b["thm2_pst_log2"]) else b["thm2_log2"]
+                if math.isfinite(t2):
+                    acc["thm2"].append(t2)
+                acc["ssa"].append(ssa(gl))
+                if name.startswith("iqp"):
+                    acc["ssa_fused"].append(ssa(C.fuse_diagonal(gl)))
+            rows.append(dict({"L": L}, **{k: stats(v) for k, v in acc.items() if v}))
+        out[name] = rows
+    return {"op_counts_log2": out, "reps": reps, "columns": "[mean, standard error] of log2 scalar operations"}
+
+
 def _traffic(step, kernel, form, tile=0):
     """DRAM bytes per launch of this step from the committed ncu summary
     (profiles/traffic.json), scaled by batch; None if that shape and kernel
@@ -528,6 +575,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-mix latency measurement")
+    ap.add_argument("--op-counts", action="store_true",
+                    help="print the op-count curves of the paper's example families (host only) and exit")
     ap.add_argument("--no-expectation", action="store_true",
                     help="skip the doubled-network expectation-value measurement")
     ap.add_argument("--tune-cache", default=None, help="JSON file to save / reuse the autotuner's kernel choices")
@@ -536,6 +585,9 @@ def main():
     ap.add_argument("--steps-detail", default=None,
                     help="write a JSON table of every program step (shape, kernel, ms per launch, roofline ms)")
     args = ap.parse_args()
+    if args.op_counts:
+        print(json.dumps(op_counts()), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -32,6 +32,13 @@ circuit families, in the variants the benchmark configurations fix):
   randomly oriented, randomly offset brick pattern whose CZ gates are each
   kept with a per-layer density rho ~ U[0.5, 1].
 * :func:`ghz`, :func:`mirror` — circuits with exactly known amplitudes.
+* The paper's own example families (Examples section): :func:`iqp_paper`
+  (short-range IQP: random phase gates with probability 7/8, controlled
+  phases on nearest-neighbour pairs with probability 3/4 gamma ln N / N per
+  time step), :func:`sycamore_periods` (Sycamore-type periods of eight
+  coupling cycles with qubits inaccessible for a whole period) and
+  :func:`cavity_3d` ((2+1)D dense random circuits with Poisson-distributed
+  space-time cavities).
 * :func:`doubled` — the circuit ``U, P, U^dagger`` whose amplitude at
   ``x = 0...0`` is the paper's quantity ``c = <0| U^dagger P U |0>`` (Classical
   Simulation section) for an observable ``P`` given as a product of
@@ -49,6 +56,7 @@ import numpy as np
 __all__ = [
     "GateList", "haar_1q", "clifford_1q_group", "random_2d", "sycamore",
     "iqp", "layered_3d", "ghz", "mirror", "doubled", "pauli_ops", "projector_ops",
+    "iqp_paper", "sycamore_periods", "cavity_3d", "fuse_diagonal",
     "random_bitstrings", "serving_pool",
     "config_circuit", "H", "S", "CZ", "X", "Y", "sqrt_pauli", "fsim",
 ]
@@ -324,6 +332,172 @@ def layered_3d(L: int, layers: int, seed: int, clifford: bool = False) -> GateLi
                 gl.add((a, b), CZ)
     for q in range(n):
         gl.add((q,), one_q())
+    return gl
+
+
+def _nn_pairs(L: int):
+    out = []
+    for r in range(L):
+        for c in range(L):
+            if c + 1 < L:
+                out.append((r * L + c, r * L + c + 1))
+            if r + 1 < L:
+                out.append((r * L + c, (r + 1) * L + c))
+    return out
+
+
+def iqp_paper(L: int, seed: int, gamma: float = 3.0, steps: int | None = None) -> GateList:
+    """The paper's short-range IQP family (Examples, item 1) on L x L qubits:
+    an H layer; then ``steps`` time steps (default T = L^2), each placing
+    diag(1, e^{i pi m / 4}) with m uniform in {0..7} on every qubit (m = 0 is
+    the identity and is left out, so a phase gate appears with probability
+    7/8), then visiting the nearest-neighbour pairs in random order and, for
+    a pair neither of whose qubits has a two-qubit gate in this step yet,
+    drawing with probability gamma ln N / N a gate diag(1, 1, 1, i^m) with m
+    uniform in {0..3} (m = 0 again left out: probability 3/4 gamma ln N / N);
+    a final H layer."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = L * L
+    T = n if steps is None else steps
+    p = min(1.0, gamma * math.log(n) / n) if n > 1 else 0.0
+    gl = GateList(n, _grid_coords(L, L), name=f"iqp_paper_{L}x{L}_T{T}_s{seed}",
+                  meta=dict(family="iqp_paper", L=L, steps=T, gamma=gamma, seed=seed))
+    pairs = _nn_pairs(L)
+    for q in range(n):
+        gl.add((q,), H)
+    for _ in range(T):
+        for q in range(n):
+            m = int(rng.integers(8))
+            if m:
+                gl.add((q,), np.diag([1.0, np.exp(1j * math.pi * m / 4)]))
+        used = set()
+        for i in rng.permutation(len(pairs)):
+            a, b = pairs[int(i)]
+            if a in used or b in used or rng.uniform() >= p:
+                continue
+            m = int(rng.integers(4))
+            if m:
+                gl.add((a, b), np.diag([1.0, 1.0, 1.0, 1j ** m]))
+                used.update((a, b))
+    for q in range(n):
+        gl.add((q,), H)
+    return gl
+
+
+def fuse_diagonal(gl: GateList) -> GateList:
+    """An IQP circuit (an H layer, diagonal gates, an H layer) with its
+    diagonal gates merged: diagonal gates commute, so all of them on the same
+    qubit pair are one gate (the product of their diagonals, a pair's
+    single-qubit phases folded into it) and the remaining single-qubit phases
+    one gate per qubit.  The circuit's operator is unchanged; its tensor
+    network has at most one two-qubit tensor pair per coupled pair."""
+    n = gl.n_qubits
+    g = gl.gates
+    head, mid, tail = g[:n], g[n:len(g) - n], g[len(g) - n:]
+    for part in (head, tail):
+        if sorted(q[0] for q, m in part if len(q) == 1 and np.allclose(m, H)) != list(range(n)):
+            raise ValueError("fuse_diagonal: expected an H layer on every qubit at both ends")
+    one = {}
+    two = {}
+    for q, m in mid:
+        d = np.diag(m)
+        if not np.allclose(m, np.diag(d)):
+            raise ValueError("fuse_diagonal: a middle gate is not diagonal")
+        if len(q) == 1:
+            one[q[0]] = one.get(q[0], np.ones(2, complex)) * d
+        else:
+            a, b = q
+            if a > b:  # diag over |x_a x_b>: swap the middle entries for the (b, a) order
+                a, b, d = b, a, d[[0, 2, 1, 3]]
+            two[(a, b)] = two.get((a, b), np.ones(4, complex)) * d
+    for (a, b), d in two.items():  # fold single-qubit phases into one pair each
+        for qq, pos in ((a, 0), (b, 1)):
+            if qq in one:
+                ph = one.pop(qq)
+                d = d * (np.repeat(ph, 2) if pos == 0 else np.tile(ph, 2))
+        two[(a, b)] = d
+    out = GateList(n, gl.coords.copy(), name=gl.name + "_fused", meta=dict(gl.meta, fused=True))
+    for q, m in head:
+        out.add(q, m)
+    for q in sorted(one):
+        out.add((q,), np.diag(one[q]))
+    for (a, b) in sorted(two):
+        out.add((a, b), np.diag(two[(a, b)]))
+    for q, m in tail:
+        out.add(q, m)
+    return out
+
+
+def sycamore_periods(L: int, periods: int, p_inaccessible: float, seed: int) -> GateList:
+    """The paper's Sycamore-type family with inaccessible qubits (Examples,
+    item 2) on the L x L grid: ``periods`` periods of eight cycles with the
+    coupling patterns A B C D C D A B (so each pair is coupled twice per
+    period); at the start of a period every qubit is made inaccessible with
+    probability ``p_inaccessible`` for the whole period.  A cycle applies a
+    single-qubit gate from {sqrt X, sqrt Y, sqrt W} (never the qubit's
+    previous one) to every accessible qubit, then fSim(pi/2, pi/6) to the
+    pattern's pairs whose qubits are both accessible."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = L * L
+    Wm = (X + Y) / math.sqrt(2.0)
+    pool = [sqrt_pauli(X), sqrt_pauli(Y), sqrt_pauli(Wm)]
+    g2 = fsim(math.pi / 2, math.pi / 6)
+    gl = GateList(n, _grid_coords(L, L), name=f"sycamore_periods_{L}x{L}_q{periods}_p{p_inaccessible}_s{seed}",
+                  meta=dict(family="sycamore_periods", L=L, periods=periods, p=p_inaccessible, seed=seed))
+    prev = [-1] * n
+    for _ in range(periods):
+        active = rng.uniform(size=n) >= p_inaccessible
+        for pat in "ABCDCDAB":
+            for q in range(n):
+                if not active[q]:
+                    continue
+                choices = [i for i in range(len(pool)) if i != prev[q]]
+                k = choices[int(rng.integers(len(choices)))]
+                prev[q] = k
+                gl.add((q,), pool[k])
+            for (a, b) in _staggered_pattern(L, pat):
+                if active[a] and active[b]:
+                    gl.add((a, b), g2)
+    return gl
+
+
+def cavity_3d(L: int, seed: int, alpha: float = 0.1, S: int = 5, sigma: float = 10.0,
+              lam: float | None = None, steps: int | None = None) -> GateList:
+    """The paper's (2+1)D random circuits with Poisson-distributed cavities
+    (Examples, item 3) on L x L qubits: T = max(1, round(alpha L)) time steps
+    (or ``steps``), each a Haar single-qubit layer and then CZ gates densely
+    placed on a brick pattern of random orientation and offset, except inside
+    cavities.  The number of cavity candidates is Poisson(lam), lam = 5e4
+    (L/200)^3.5 by default; each candidate corner (x, y, t) is uniform in the
+    space-time box and is kept with probability exp(-(x^2/L^2 + y^2/L^2 +
+    t^2/T^2)/sigma^2); a kept cavity removes every gate in the S x S x S
+    block from its corner.  A final Haar layer follows."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = L * L
+    T = max(1, int(round(alpha * L))) if steps is None else steps
+    lam = 5e4 * (L / 200.0) ** 3.5 if lam is None else lam
+    holes = []
+    for _ in range(int(rng.poisson(lam))):
+        x, y, t = int(rng.integers(L)), int(rng.integers(L)), int(rng.integers(T))
+        if rng.uniform() < math.exp(-(x * x / L / L + y * y / L / L + t * t / T / T) / sigma ** 2):
+            holes.append((x, y, t))
+
+    def in_cavity(q, t):
+        r, c = divmod(q, L)
+        return any(x <= c < x + S and y <= r < y + S and tt <= t < tt + S for x, y, tt in holes)
+
+    gl = GateList(n, _grid_coords(L, L), name=f"cavity3d_{L}x{L}_T{T}_s{seed}",
+                  meta=dict(family="cavity_3d", L=L, steps=T, seed=seed, cavities=len(holes)))
+    for t in range(T):
+        for q in range(n):
+            if not in_cavity(q, t):
+                gl.add((q,), haar_1q(rng))
+        pat = ("AB" if int(rng.integers(2)) == 0 else "CD")[int(rng.integers(2))]
+        for (a, b) in _brick_pattern(L, L, pat):
+            if not (in_cavity(a, t) or in_cavity(b, t)):
+                gl.add((a, b), CZ)
+    for q in range(n):
+        gl.add((q,), haar_1q(rng))
     return gl
 
 
