@@ -446,6 +446,7 @@ struct FzCfg {
   static constexpr int kChunkKB = 512 / (kRowBytes / 2);      // k-blocks per 512 k' accumulation chunk
   static constexpr int kATasks = 128 * kChunks;
   static constexpr int kTasks = kATasks + (BN / 2) * kChunks;  // A 128 rows, B BN/2 complex rows
+  static constexpr int kTPT = 4;                              // tasks per converter thread
   static constexpr int kConvWarps = kTasks / 128;             // 4 tasks per converter thread: 12, 10 or 8 warps
   static constexpr int kConvThreads = 32 * kConvWarps;
   static constexpr int kEpiWarps = BN == 256 ? 8 : 4;         // the short-K 256-column tiles are epilogue-bound
@@ -514,6 +515,7 @@ struct PlCfg {
   static constexpr int kEpiWarps = 8;      // two per TMEM lane quarter, half of the columns each
   static constexpr int kThreads = 32 * (kEpiWarps + 2);
   static constexpr int kFullArrivals = 1;  // the producer's expect_tx arrival; the bytes complete it
+  static constexpr int kTPT = 4;           // (no converters)
   static constexpr uint32_t kATileBytes = 128 * kRowBytes;
   static constexpr uint32_t kBTileBytes = BN * kRowBytes;
   static constexpr uint32_t kStageBytes = 2 * kATileBytes + 2 * kBTileBytes;
@@ -538,7 +540,10 @@ struct HyCfg {
   static constexpr int kKSteps = kRowBytes / 32;
   static constexpr int kChunkKB = 512 / (kRowBytes / 2);
   static constexpr int kATasks = 128 * kChunks;               // all converter tasks are A tasks
-  static constexpr int kConvWarps = kATasks / 128;            // 4 tasks per thread: 4 warps
+  // 2 tasks per thread: 8 warps, twice the loads in flight of 4 warps with
+  // 4 tasks each (the A conversion of a tile is load-latency bound)
+  static constexpr int kTPT = 2;
+  static constexpr int kConvWarps = kATasks / (32 * kTPT);
   static constexpr int kConvThreads = 32 * kConvWarps;
   static constexpr int kEpiWarps = 8;
   static constexpr int kStageBlocks = 2;
@@ -620,14 +625,15 @@ struct BlockOrder {
 // the high 4, a bijection on 0..255
 __device__ __forceinline__ uint32_t stage_swz(uint32_t x) { return x ^ ((x >> 4) & 15u); }
 
-// One k-block of a converter thread: its 4 tasks (j = ct + T i, T = the
-// converter thread count, a multiple of 32 and of the chunks per row C) of
-// 2 x 16 bytes each.  Task j < 128 C: A tile row j / C; otherwise complex
+// One k-block of a converter thread: its kTPT tasks (4; 2 in the hybrid
+// tile), j = ct + T i with T the converter thread count (a multiple of 32
+// and of the chunks per row C), of 2 x 16 bytes each.  Task j < 128 C: A tile row j / C; otherwise complex
 // column (j - 128 C) / C of B, giving B' rows 2n and 2n + 1.  Chunk j % C =
 // ct % C in both cases.  128 C is a multiple of 32, so A/B tasks never mix in
 // a warp.
+template <int TPT>
 struct FzRegs {
-  float4 v[4][2];
+  float4 v[TPT][2];
 };
 
 struct FzGeom {
@@ -646,11 +652,11 @@ __device__ __forceinline__ void fz_tile(const FzGeom& g, int64_t t, int& bz, int
 }
 
 template <class Cf>
-__device__ __forceinline__ void fz_load(FzRegs& R, const float2* __restrict__ A, const float2* __restrict__ B,
+__device__ __forceinline__ void fz_load(FzRegs<Cf::kTPT>& R, const float2* __restrict__ A, const float2* __restrict__ B,
                                         const FzGeom& g, int bz, int m0, int n0, int kb, int ct) {
   const int64_t koff = (int64_t)kb * Cf::kKC + 4 * (ct % Cf::kChunks);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < Cf::kTPT; ++i) {
     const int j = ct + Cf::kConvThreads * i;
     const float2* p = j < Cf::kATasks ? A + ((int64_t)bz * g.M + m0 + j / Cf::kChunks) * g.K + koff
                                       : B + ((int64_t)bz * g.N + n0 / 2 + (j - Cf::kATasks) / Cf::kChunks) * g.K + koff;
@@ -667,7 +673,7 @@ __device__ __forceinline__ void fz_prefetch(const float2* __restrict__ A, const 
   if (ct & 3) return;
   const int64_t koff = (int64_t)kb * Cf::kKC + 4 * (ct % Cf::kChunks);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < Cf::kTPT; ++i) {
     const int j = ct + Cf::kConvThreads * i;
     const float2* p = j < Cf::kATasks ? A + ((int64_t)bz * g.M + m0 + j / Cf::kChunks) * g.K + koff
                                       : B + ((int64_t)bz * g.N + n0 / 2 + (j - Cf::kATasks) / Cf::kChunks) * g.K + koff;
@@ -676,11 +682,11 @@ __device__ __forceinline__ void fz_prefetch(const float2* __restrict__ A, const 
 }
 
 template <class Cf>
-__device__ __forceinline__ void fz_store(const FzRegs& R, uint32_t st, int ct) {
+__device__ __forceinline__ void fz_store(const FzRegs<Cf::kTPT>& R, uint32_t st, int ct) {
   constexpr uint32_t kAl = Cf::kATileBytes, kB = 2 * Cf::kATileBytes, kBl = kB + Cf::kBTileBytes;
   const int cc = ct % Cf::kChunks;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < Cf::kTPT; ++i) {
     const int j = ct + Cf::kConvThreads * i;
     uint32_t h[4], l[4];
     split_words(R.v[i][0], R.v[i][1], h, l);
@@ -834,12 +840,12 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
     // converters: global k-block q = (local tile) * nk + kb
     const int ct = threadIdx.x - 32 * (E + 1 + (Cf::kHybrid ? 1 : 0));
     const int64_t total = my_tiles * nk;
-    FzRegs R0;
+    FzRegs<Cf::kTPT> R0;
     // load cursor: local tile lt_ld (coordinates bz, m0, n0), k-block kb_ld
     int64_t lt_ld = 0;
     int kb_ld = 0, bz = 0, m0 = 0, n0 = 0;
     if (my_tiles > 0) fz_tile<BN>(geo, blockIdx.x, bz, m0, n0);
-    auto load_next = [&](FzRegs& R) {
+    auto load_next = [&](FzRegs<Cf::kTPT>& R) {
       fz_load<Cf>(R, A, B, geo, bz, m0, n0, kb_ld, ct);
       if (++kb_ld == nk) {
         kb_ld = 0;
@@ -853,7 +859,7 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
     // q + 1 into R; false after a timeout or an abort.  (Two register sets
     // for two k-blocks in flight need more than the 96 registers a thread
     // of this 17-warp block can have, and spill.)
-    auto step = [&](FzRegs& R, int64_t q) -> bool {
+    auto step = [&](FzRegs<Cf::kTPT>& R, int64_t q) -> bool {
       if (q >= kFzStages && !mbar_wait(&empty[s], ph ^ 1u)) {
         atomicExch(&tc_error_flag, 6);
         *(volatile int*)abort_flag = 1;
