@@ -125,6 +125,20 @@ static void set_splitk(GemmDesc& g) {
     int64_t s = g.K / 2048;
     while (s > 1 && (double)s * g.batch * g.M * g.N * 8 > (double)(256u << 20)) s >>= 1;
     g.splitk = (int)std::min<int64_t>(s, 4096);
+  } else if (simt && g.kernel != KG_DOT && g.K >= 512) {
+    // fewer output tiles than SMs (e.g. batch 1, M = N = 64, K = 4096: one
+    // block would run the whole sum): split K until about two tiles per SM,
+    // each split keeping at least 64 k
+    const int bm = g.kernel == KG_SIMT_128x64 ? 128 : g.kernel == KG_SIMT_64x32 ? 64 : 32;
+    const int bn = g.kernel == KG_SIMT_128x64 ? 64 : g.kernel == KG_SIMT_64x32 ? 32 : 128;
+    const double tiles = (double)g.batch * (double)((g.M + bm - 1) / bm) * (double)((g.N + bn - 1) / bn);
+    if (tiles < 152) {
+      int64_t s = 1;
+      while (tiles * (double)(2 * s) <= 2.0 * 152 && g.K / (2 * s) >= 64 &&
+             (double)(2 * s) * g.batch * g.M * g.N * 8 <= (double)(256u << 20))
+        s *= 2;
+      g.splitk = (int)s;
+    }
   }
 }
 
