@@ -411,7 +411,8 @@ __global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
 // epilogue-bound 256-column and plane-fed tiles); warp E: TMEM allocation and
 // the MMA issuer (one lane); warps E+1 and up: converters (12 for BN = 128
 // real output columns per CTA, 10 for BN = 64, 8 for BN = 256, whose 64-byte
-// rows halve the converter work per k-block) or the TMA producer.
+// rows halve the converter work per k-block; 8 with half the tasks each in
+// the hybrid tile, whose converters handle A only) or the TMA producer.
 // Finished accumulation chunks are added into a third TMEM region (the
 // running sum) instead of registers, so no thread holds a whole row.  The
 // register file is split between the SM's four sub-partitions (16K 32-bit
