@@ -411,8 +411,8 @@ __global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
 // epilogue-bound 256-column and plane-fed tiles); warp E: TMEM allocation and
 // the MMA issuer (one lane); warps E+1 and up: converters (12 for BN = 128
 // real output columns per CTA, 10 for BN = 64, 8 for BN = 256, whose 64-byte
-// rows halve the converter work per k-block; 8 with half the tasks each in
-// the hybrid tile, whose converters handle A only) or the TMA producer.
+// rows halve the converter work per k-block; 16 with one task each in the
+// hybrid tile, whose converters handle A only) or the TMA producer.
 // Finished accumulation chunks are added into a third TMEM region (the
 // running sum) instead of registers, so no thread holds a whole row.  The
 // register file is split between the SM's four sub-partitions (16K 32-bit
@@ -541,9 +541,11 @@ struct HyCfg {
   static constexpr int kKSteps = kRowBytes / 32;
   static constexpr int kChunkKB = 512 / (kRowBytes / 2);
   static constexpr int kATasks = 128 * kChunks;               // all converter tasks are A tasks
-  // 2 tasks per thread: 8 warps, twice the loads in flight of 4 warps with
-  // 4 tasks each (the A conversion of a tile is load-latency bound)
-  static constexpr int kTPT = 2;
+  // 1 task per thread: 16 warps (26 in the block, 72 registers), four times
+  // the loads in flight of 4 warps with 4 tasks each (the A conversion of a
+  // tile is load-latency bound: 4 -> 8 -> 16 warps took an M 4096 N 256
+  // K 128 node from 1.03 to 0.94 to 0.90 ms)
+  static constexpr int kTPT = 1;
   static constexpr int kConvWarps = kATasks / (32 * kTPT);
   static constexpr int kConvThreads = 32 * kConvWarps;
   static constexpr int kEpiWarps = 8;
@@ -626,7 +628,7 @@ struct BlockOrder {
 // the high 4, a bijection on 0..255
 __device__ __forceinline__ uint32_t stage_swz(uint32_t x) { return x ^ ((x >> 4) & 15u); }
 
-// One k-block of a converter thread: its kTPT tasks (4; 2 in the hybrid
+// One k-block of a converter thread: its kTPT tasks (4; 1 in the hybrid
 // tile), j = ct + T i with T the converter thread count (a multiple of 32
 // and of the chunks per row C), of 2 x 16 bytes each.  Task j < 128 C: A tile row j / C; otherwise complex
 // column (j - 128 C) / C of B, giving B' rows 2n and 2n + 1.  Chunk j % C =
