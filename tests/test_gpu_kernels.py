@@ -208,3 +208,33 @@ def test_cgemm_short_k_plane_tiles(tnc, shape, tile):
                     kernel="tc", tile=tile)
     err = np.linalg.norm(got.cpu().numpy().astype(np.complex128) - ref) / np.linalg.norm(ref)
     assert err <= TOL["split_bf16"], f"{shape} tile {tile}: {err:.3g}"
+
+
+@pytest.mark.parametrize("kernel", ["simt_128x64", "simt_64x32", "simt_32x128"])
+@pytest.mark.parametrize("shape", [(1, 64, 64, 4096, 0, 1), (2, 100, 36, 1000, 1, 0), (1, 32, 128, 600, 0, 0)])
+def test_cgemm_cuda_cores_split_k_small_grid(tnc, kernel, shape):
+    """Nodes with fewer output tiles than SMs and K >= 512 run the CUDA-core
+    kernels with K split over blocks and an FP64 reduction: every tile shape,
+    ragged sizes included, against NumPy; the power-of-two shape also with a
+    scattered output."""
+    batch, M, N, K, tA, tB = shape
+    rng = np.random.default_rng(M + N + K)
+    A = _crand(batch * M * K, rng)
+    B = _crand(batch * K * N, rng)
+    ref = _ref(A, B, batch, M, N, K, tA, tB)
+    got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, tA, tB, "fp32",
+                    kernel=kernel)
+    err = np.linalg.norm(got.cpu().numpy().astype(np.complex128) - ref) / np.linalg.norm(ref)
+    assert err <= TOL["fp32"], f"{shape} {kernel}: {err:.3g}"
+    if shape[0] == 1 and M == 64:
+        c_pos = np.random.default_rng(1).permutation(12)
+        got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, tA, tB, "fp32",
+                        kernel=kernel, c_pos=c_pos).reshape(-1).cpu().numpy()
+        m, n = np.meshgrid(np.arange(M), np.arange(N), indexing="ij")
+        addr = np.zeros(m.shape, np.int64)
+        for i in range(6):
+            addr |= ((n >> i) & 1) << int(c_pos[i])
+            addr |= ((m >> i) & 1) << int(c_pos[6 + i])
+        placed = got[addr]
+        err = np.linalg.norm(placed.astype(np.complex128) - ref[0]) / np.linalg.norm(ref[0])
+        assert err <= TOL["fp32"], f"scattered {kernel}: {err:.3g}"
