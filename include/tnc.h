@@ -84,7 +84,17 @@ typedef struct {
   int leaf_size;            /* clusters of at most this many tensors are contracted greedily */
   int max_group_log2;       /* at most 2^k slices run together in one launch per node */
   int use_graph;            /* 1: replay each slice group as a captured CUDA graph */
+  int embedding;            /* tensor positions given to the separator search: TNC_EMBED_AUTO (both
+                               below, the tree with the smaller Eq. 3 cost is kept), TNC_EMBED_COLLAPSED
+                               (time axis collapsed, the Thm. 2 proof) or TNC_EMBED_SPACETIME (the
+                               (d+1)-dimensional network before the collapse, Fig. 1a; d <= 2 only) */
+  int n_starts;             /* separator hierarchies built per embedding, with seeds seed, seed + 1, ...;
+                               the one with the smallest Eq. 3 cost is kept (0 = 1) */
 } tnc_plan_opts;
+
+#define TNC_EMBED_AUTO 0
+#define TNC_EMBED_COLLAPSED 1
+#define TNC_EMBED_SPACETIME 2
 
 typedef struct {
   double paper_ops;     /* sum over nodes and slices of 2 M (Eq. 3) */
@@ -101,6 +111,9 @@ typedef struct {
   int n_launches;       /* kernel launches per slice group */
   double plan_ms;       /* host time spent planning */
   double tree_cost_log2;/* log2 of the unsliced tree's paper_ops */
+  int embedding_used;   /* TNC_EMBED_COLLAPSED or TNC_EMBED_SPACETIME: the kept tree's embedding */
+  int seed_used;        /* seed of the kept tree's separator search */
+  double time_scale;    /* space-time embedding: distance between consecutive layers (lattice units) */
 } tnc_plan_report;
 
 /* Human-readable name of a status code. */
@@ -181,7 +194,12 @@ int tnc_plan_export_json(const tnc_plan_t* plan, char* buf, size_t cap, size_t* 
 
 /* Copy the plan's leaf tensors and node descriptors to the current CUDA
  * device (device memory owned by the plan, freed by tnc_free_plan).  Called
- * automatically by the first contraction if needed.  stream may be NULL. */
+ * automatically by the first contraction if needed.  stream may be NULL.
+ * For a plan whose workspace fits the static workspace of
+ * tnc_contract_amplitudes_static (64 MiB), the first upload on a device also
+ * loads every kernel of the library there and resolves that workspace's
+ * address (the set-up that entry point relies on; a failure of it is not an
+ * error of the upload). */
 int tnc_plan_upload(tnc_plan_t* plan, void* cuda_stream);
 
 /* Per-step CUDA-event profiling of the node program.  While enabled, every
@@ -316,8 +334,13 @@ int tnc_contract_amplitudes_dbits(tnc_plan_t* plan, const uint8_t* d_bits, int b
  * - The plan must already be resident on d_out's device (tnc_plan_upload),
  *   else TNC_ESTATE; profiling must be off, else TNC_ESTATE.
  * - A plan whose workspace (report.ws_bytes) exceeds 64 MiB: TNC_ENOMEM.
- * - The first call on a device looks up the array's device address once;
- *   make that first call before any stream capture.
+ * - Its set-up is done by tnc_plan_upload (which allocates anyway): for a
+ *   plan whose workspace fits the array, the upload loads every kernel of
+ *   the library onto the device and resolves the array's device address
+ *   there, once per device.  Without it (with lazy module loading, the CUDA
+ *   default) the first call would take device memory for the array and the
+ *   kernels.  If that set-up failed, this call returns TNC_ESTATE with the
+ *   reason.
  * - All calls share the array and it keeps the last call's contents; each
  *   call re-initialises what must start at zero.  Calls whose GPU work
  *   overlaps (several streams or threads) race on it: serialise them.

@@ -31,7 +31,7 @@ def _cuda_home() -> str:
 
 def _sources():
     srcs = sorted(f for f in os.listdir(CSRC) if f.endswith((".cpp", ".cu")))
-    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     hdrs.append(os.path.join(ROOT, "include", "tnc.h"))
     return [os.path.join(CSRC, s) for s in srcs], hdrs
 

@@ -18,6 +18,8 @@ namespace tnc {
 
 int read_tc_error(int* flag);
 int bounded_wait_selftest(uint64_t limit_ns, int* timed_out);
+size_t static_workspace_bytes();
+int prepare_static_workspace(int dev);
 
 static thread_local std::string g_err;
 
@@ -37,10 +39,14 @@ static int cuda_fail(cudaError_t e, const char* what) {
 
 // Planning view: fixed final wires are replaced by the beta bits of the
 // bitstring batch; open final wires and beta bits survive to the root.
+// time_scale > 0 places the tensors in (dim + 1)-dimensional space-time, the
+// extra coordinate being the gate's layer times time_scale (the network
+// before the collapse of the Thm. 2 proof, Fig. 1a); 0 keeps the time axis
+// collapsed.
 static void make_plan_net(const Network& net, const std::vector<int>& open_q, int beta_bits,
-                          PlanNet& pn, std::vector<int>& beta_labels) {
+                          PlanNet& pn, std::vector<int>& beta_labels, double time_scale = 0) {
   pn = PlanNet();
-  pn.dim = net.dim;
+  pn.dim = time_scale > 0 ? net.dim + 1 : net.dim;
   pn.n_leaves = (int)net.leaves.size();
   int nlab = (int)net.label_kind.size();
   beta_labels.clear();
@@ -66,6 +72,7 @@ static void make_plan_net(const Network& net, const std::vector<int>& open_q, in
     if (has_fixed)
       for (int x : beta_labels) pn.leaf_labels[l].push_back(x);
     for (int k = 0; k < 3; ++k) pn.pos[l][k] = L.pos[k];
+    if (time_scale > 0) pn.pos[l][net.dim] = L.layer * time_scale;
     pn.radius[l] = L.radius;
   }
   pn.holders.assign(pn.n_labels, {});
@@ -98,6 +105,10 @@ static int launches_per_group(const Plan& p) {
   }
   return per_group;
 }
+
+// distances between consecutive layers tried by the space-time embedding
+// (lattice units; the qubit spacing is 1)
+static const double kTimeScales[] = {0.25, 0.5, 1.0, 2.0};
 
 static void fill_report(Plan& p, double plan_ms) {
   tnc_plan_report& r = p.rep;
@@ -187,6 +198,8 @@ void tnc_plan_opts_default(tnc_plan_opts* o) {
   o->leaf_size = 8;
   o->max_group_log2 = 6;
   o->use_graph = 1;
+  o->embedding = TNC_EMBED_AUTO;
+  o->n_starts = 4;
 }
 
 int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** out, tnc_plan_report* rep) {
@@ -200,7 +213,8 @@ int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** o
   if (opts->n_open < 0 || opts->n_open > 20 || (opts->n_open > 0 && !opts->open_qubits) ||
       opts->max_batch < 1 || opts->max_batch > 65536 || opts->form < 0 || opts->form > 2 ||
       opts->ssa_trials < 0 || opts->leaf_size < 0 || opts->max_group_log2 < 0 ||
-      opts->max_group_log2 > 16) {
+      opts->max_group_log2 > 16 || opts->embedding < 0 || opts->embedding > 2 || opts->n_starts < 0 ||
+      opts->n_starts > 64 || (opts->embedding == TNC_EMBED_SPACETIME && N.dim > 2)) {
     set_error("tnc_plan: invalid options");
     return TNC_EINVAL;
   }
@@ -222,13 +236,37 @@ int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** o
   int bb = 0;
   while ((1 << bb) < opts->max_batch) ++bb;
   p.beta_bits = bb;
-  make_plan_net(p.net, p.open_qubits, bb, p.pn, p.beta_labels);
-  PlannerOpts po;
-  po.seed = opts->seed;
-  po.trials = p.opts.ssa_trials;
-  po.leaf_size = p.opts.leaf_size;
-  PlannerStats st;
-  p.tree = plan_tree(p.pn, po, &st);
+  // separator hierarchies over the embeddings and seeds asked for; the tree
+  // with the smallest Eq. 3 cost is kept (ties: the earlier candidate)
+  std::vector<double> scales;
+  if (opts->embedding != TNC_EMBED_SPACETIME) scales.push_back(0.0);
+  if (opts->embedding != TNC_EMBED_COLLAPSED && N.dim <= 2)
+    for (double h : kTimeScales) scales.push_back(h);
+  const int starts = std::max(1, opts->n_starts);
+  double best_cost = 1e300;
+  for (double h : scales) {
+    PlanNet pn;
+    std::vector<int> bl;
+    make_plan_net(p.net, p.open_qubits, bb, pn, bl, h);
+    for (int k = 0; k < starts; ++k) {
+      PlannerOpts po;
+      po.seed = opts->seed + (uint64_t)k;
+      po.trials = p.opts.ssa_trials;
+      po.leaf_size = p.opts.leaf_size;
+      PlannerStats st;
+      Tree t = plan_tree(pn, po, &st);
+      const double c = tree_cost_log2(t);
+      if (c < best_cost - 1e-9) {
+        best_cost = c;
+        p.tree = std::move(t);
+        p.pn = pn;
+        p.beta_labels = bl;
+        p.rep.embedding_used = h > 0 ? TNC_EMBED_SPACETIME : TNC_EMBED_COLLAPSED;
+        p.rep.seed_used = (int)po.seed;
+        p.rep.time_scale = h;
+      }
+    }
+  }
   p.rep.tree_cost_log2 = tree_cost_log2(p.tree);
   int rc = plan_slices(p, opts->mem_cap_bytes);
   if (rc == TNC_OK) rc = compile_program(p);
@@ -440,6 +478,15 @@ int tnc_plan_upload(tnc_plan_t* plan, void* stream) {
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "tnc_plan_upload: sync");
   p.device = dev;
+  // a plan that fits the static workspace may be contracted by
+  // tnc_contract_amplitudes_static, which allocates nothing: its set-up
+  // (kernels loaded, the array's address resolved) is done here, where
+  // allocating is allowed.  A failure only disables that entry point.
+  if (p.prog.ws_bytes <= static_workspace_bytes()) {
+    std::string keep = tnc_last_error();
+    if (prepare_static_workspace(dev) != TNC_OK) cudaGetLastError();
+    set_error("%s", keep.c_str());
+  }
   return TNC_OK;
 }
 

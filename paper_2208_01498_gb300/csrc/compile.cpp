@@ -132,9 +132,10 @@ static void set_splitk(GemmDesc& g) {
     const int bm = g.kernel == KG_SIMT_128x64 ? 128 : g.kernel == KG_SIMT_64x32 ? 64 : 32;
     const int bn = g.kernel == KG_SIMT_128x64 ? 64 : g.kernel == KG_SIMT_64x32 ? 32 : 128;
     const double tiles = (double)g.batch * (double)((g.M + bm - 1) / bm) * (double)((g.N + bn - 1) / bn);
-    if (tiles < 152) {
+    const double sms = (double)sm_count();  // of the current device (152 without one)
+    if (tiles < sms) {
       int64_t s = 1;
-      while (tiles * (double)(2 * s) <= 2.0 * 152 && g.K / (2 * s) >= 64 &&
+      while (tiles * (double)(2 * s) <= 2.0 * sms && g.K / (2 * s) >= 64 &&
              (double)(2 * s) * g.batch * g.M * g.N * 8 <= (double)(256u << 20))
         s *= 2;
       g.splitk = (int)s;

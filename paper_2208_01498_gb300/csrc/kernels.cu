@@ -10,10 +10,12 @@
 // (the node cost 2 M of Eq. 3 with M = batch * M * N * K).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <cstdio>
 
+#include "devonce.cuh"
 #include "outmap.cuh"
 #include "tnc_kernels.h"
 
@@ -535,12 +537,10 @@ int run_simt(const GemmDesc& d, const float2* A, const float2* B, float2* C, flo
       tr.rank[b] = (int8_t)r;
     }
   }
-  static bool attr_set = false;
-  if (staged && !attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(cgemm_simt_kernel<BM, BN, BK, TM, TN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return (int)e;
-    attr_set = true;
+  static std::atomic<int> attr_done[kMaxDevices];
+  if (staged) {
+    int e = smem_attr_once(attr_done, cgemm_simt_kernel<BM, BN, BK, TM, TN>, (int)dyn);
+    if (e) return e;
   }
   for (int64_t b0 = 0; b0 < d.batch; b0 += 65535) {
     int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
@@ -550,7 +550,8 @@ int run_simt(const GemmDesc& d, const float2* A, const float2* B, float2* C, flo
                                                                   tr);
   }
   if (splits > 1) {
-    unsigned blocks = (unsigned)((nout + 255) / 256 < 152 * 16 ? (nout + 255) / 256 : 152 * 16);
+    const int64_t cap = (int64_t)sm_count() * 16;
+    unsigned blocks = (unsigned)((nout + 255) / 256 < cap ? (nout + 255) / 256 : cap);
     splitk_reduce_kernel<<<blocks, 256, 0, st>>>(dst, C, splits, nout, d.M, d.N, om);
   }
   return (int)cudaGetLastError();
@@ -559,6 +560,26 @@ int run_simt(const GemmDesc& d, const float2* A, const float2* B, float2* C, flo
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
+// SM count of the current device, cached per device (152 without one)
+int sm_count() {
+  static std::atomic<int> n[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;  // no device: a GB300's count
+  }
+  if (dev < 0 || dev >= kMaxDevices) return 152;
+  int v = n[dev].load(std::memory_order_acquire);
+  if (!v) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 152;
+    }
+    n[dev].store(v, std::memory_order_release);
+  }
+  return v;
+}
+
 int launch_set_counter(uint64_t* d_ctr, uint64_t value, void* stream) {
   set_counter_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_ctr, value);
   return (int)cudaGetLastError();
@@ -662,7 +683,7 @@ int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp,
     case KG_NARROW: {
       if (d.N > 16 || d.K > 16) return (int)cudaErrorInvalidValue;
       int64_t blocks = (d.M + 255) / 256;
-      if (blocks > 152 * 16) blocks = 152 * 16;
+      if (blocks > (int64_t)sm_count() * 16) blocks = (int64_t)sm_count() * 16;
       for (int64_t b0 = 0; b0 < d.batch; b0 += 65535) {
         int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
         dim3 grid((unsigned)blocks, (unsigned)nb);
@@ -718,6 +739,33 @@ int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, voi
   if (blocks > 65535) blocks = 65535;
   accum_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>((const float2*)ws, (double2*)d_out, d, batch);
   return (int)cudaGetLastError();
+}
+
+// Loads every kernel of this file onto the current device.  With lazy module
+// loading (the CUDA default) a kernel is otherwise loaded, and device memory
+// taken for its code and the module's data, at its first launch.
+int preload_kernels_core() {
+  const void* fns[] = {
+      (const void*)set_counter_kernel,
+      (const void*)gather_kernel,
+      (const void*)permute_kernel,
+      (const void*)cgemm_simt_kernel<128, 64, 8, 8, 4>,
+      (const void*)cgemm_simt_kernel<64, 32, 8, 4, 4>,
+      (const void*)cgemm_simt_kernel<32, 128, 8, 4, 4>,
+      (const void*)cgemm_narrow_kernel,
+      (const void*)grouped_narrow_kernel,
+      (const void*)cgemm_dot_kernel,
+      (const void*)cgemm_dot11_kernel,
+      (const void*)dot_finish_kernel,
+      (const void*)accum_kernel,
+      (const void*)splitk_reduce_kernel,
+  };
+  cudaFuncAttributes fa;
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return (int)e;
+  }
+  return 0;
 }
 
 }  // namespace tnc

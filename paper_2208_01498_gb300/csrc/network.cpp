@@ -160,6 +160,7 @@ int build_network(const tnc_network_desc* d, Network* net) {
 
   std::vector<std::array<cd, 4>> pend(n, {cd(1), cd(0), cd(0), cd(1)});
   std::vector<int> cur_label(n, -1), cur_holder(n, -1);
+  std::vector<int> qlayer(n, 0);  // ASAP layer of the latest 2q gate on each qubit
   qoff = moff = 0;
   int g2 = 0;
   for (int g = 0; g < d->n_gates; ++g) {
@@ -238,6 +239,8 @@ int build_network(const tnc_network_desc* d, Network* net) {
       A.qubit = qa;
       B.qubit = qb;
       A.time = B.time = g2;
+      A.layer = B.layer = std::max(qlayer[qa], qlayer[qb]) + 1;
+      qlayer[qa] = qlayer[qb] = A.layer;
       net->leaves.push_back(std::move(A));
       net->leaves.push_back(std::move(B));
       const int ida = (int)net->leaves.size() - 2, idb = ida + 1;

@@ -18,10 +18,21 @@
 // staged bitstrings and the output) on every call.  Calls whose work overlaps
 // on the GPU (two streams, or two host threads) race on the array and give
 // wrong results: serialise them.
+//
+// Set-up happens in tnc_plan_upload, which allocates anyway: for a plan
+// whose workspace fits the array it loads every kernel of the library onto
+// the device and resolves the array's device address there, once per device.
+// With lazy module loading (the CUDA default) both would otherwise happen at
+// the first use on that device, and both take device memory (the array
+// itself is allocated when its module is loaded).
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <cstdio>
 #include <mutex>
+#include <string>
 
+#include "devonce.cuh"
 #include "tnc_internal.h"
 
 namespace tnc {
@@ -32,33 +43,54 @@ int run_request(tnc_plan_t* plan, const uint8_t* host_bits, int batch, void* d_o
 namespace {
 
 constexpr size_t kStaticWsBytes = (size_t)64 << 20;
-constexpr int kMaxDevices = 64;
 
 // The workspace.  In host code `g_static_ws` only names a host-side stand-in;
 // its device address comes from cudaGetSymbolAddress (per device).
 static __device__ __align__(256) unsigned char g_static_ws[kStaticWsBytes];
 
 std::mutex g_mu;
-void* g_ws_addr[kMaxDevices] = {};
+std::atomic<void*> g_ws_addr[tnc::kMaxDevices];
+std::string g_setup_error[tnc::kMaxDevices];  // guarded by g_mu
 
-// Device address of the array on device `dev` (which must be current); the
-// first call on a device looks it up once.
-int static_ws(int dev, void** out) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_ws_addr[dev]) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_ws);
-    if (e != cudaSuccess) {
-      tnc::set_error("tnc_contract_amplitudes_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-      return TNC_ECUDA;
-    }
-    g_ws_addr[dev] = ptr;
+}  // namespace
+
+namespace tnc {
+
+int preload_kernels_core();
+int preload_kernels_tc();
+
+size_t static_workspace_bytes() { return kStaticWsBytes; }
+
+// Set-up of the static workspace on device `dev`, which must be current:
+// every kernel loaded, the array's address resolved.  Called by
+// tnc_plan_upload; idempotent.
+int prepare_static_workspace(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("static workspace: device %d out of range", dev);
+    return TNC_EINVAL;
   }
-  *out = g_ws_addr[dev];
+  if (g_ws_addr[dev].load(std::memory_order_acquire)) return TNC_OK;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_ws_addr[dev].load(std::memory_order_acquire)) return TNC_OK;
+  int r = preload_kernels_core();
+  if (!r) r = preload_kernels_tc();
+  void* ptr = nullptr;
+  cudaError_t e = r ? (cudaError_t)r : cudaGetSymbolAddress(&ptr, g_static_ws);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", r ? "loading the kernels" : "cudaGetSymbolAddress",
+             cudaGetErrorString(e));
+    g_setup_error[dev] = buf;
+    set_error("static workspace set-up on device %d: %s", dev, buf);
+    return TNC_ECUDA;
+  }
+  g_setup_error[dev].clear();
+  g_ws_addr[dev].store(ptr, std::memory_order_release);
   return TNC_OK;
 }
 
-}  // namespace
+}  // namespace tnc
 
 extern "C" int tnc_contract_amplitudes_static(tnc_plan_t* plan, const uint8_t* bits, int batch, void* d_out,
                                               void* stream) {
@@ -80,7 +112,7 @@ extern "C" int tnc_contract_amplitudes_static(tnc_plan_t* plan, const uint8_t* b
     tnc::set_error("tnc_contract_amplitudes_static: d_out is not device memory");
     return TNC_EINVAL;
   }
-  if (attr.device < 0 || attr.device >= kMaxDevices) {
+  if (attr.device < 0 || attr.device >= tnc::kMaxDevices) {
     tnc::set_error("tnc_contract_amplitudes_static: device %d out of range", attr.device);
     return TNC_EINVAL;
   }
@@ -100,8 +132,15 @@ extern "C" int tnc_contract_amplitudes_static(tnc_plan_t* plan, const uint8_t* b
     tnc::set_error("tnc_contract_amplitudes_static: disable profiling first (it creates CUDA events)");
     return TNC_ESTATE;
   }
-  void* ws = nullptr;
-  int rc = static_ws(attr.device, &ws);
-  if (rc != TNC_OK) return rc;
+  // set up by tnc_plan_upload (this call only reads the cached address)
+  void* ws = g_ws_addr[attr.device].load(std::memory_order_acquire);
+  if (!ws) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    tnc::set_error("tnc_contract_amplitudes_static: the static workspace of device %d is not set up (%s)",
+                   attr.device,
+                   g_setup_error[attr.device].empty() ? "tnc_plan_upload sets it up"
+                                                      : g_setup_error[attr.device].c_str());
+    return TNC_ESTATE;
+  }
   return tnc::run_request(plan, bits, batch, d_out, ws, kStaticWsBytes, stream);
 }

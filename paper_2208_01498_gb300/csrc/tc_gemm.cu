@@ -28,6 +28,7 @@
 #include <cstring>
 
 #include "../../include/tnc.h"
+#include "devonce.cuh"
 #include "outmap.cuh"
 #include "tnc_kernels.h"
 
@@ -1043,26 +1044,20 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
   }
 }
 
-int sm_count() {
-  static int n[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return 152;
-  if (!n[dev] && cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n[dev] = 152;
-  return n[dev];
-}
 
 // the kernel's register count times its block size fits the SM (checked
 // once per process; otherwise the tile runs through the planes)
 template <int BN>
 bool fused_launchable() {
-  static int ok = -1;
-  if (ok < 0) {
+  static std::atomic<int> ok{-1};
+  int v = ok.load(std::memory_order_acquire);
+  if (v < 0) {
     cudaFuncAttributes fa;
-    ok = cudaFuncGetAttributes(&fa, tc_fused_bf16_kernel<FzCfg<BN>, false>) == cudaSuccess &&
-         fa.maxThreadsPerBlock >= FzCfg<BN>::kThreads;
+    v = cudaFuncGetAttributes(&fa, tc_fused_bf16_kernel<FzCfg<BN>, false>) == cudaSuccess &&
+        fa.maxThreadsPerBlock >= FzCfg<BN>::kThreads;
+    ok.store(v, std::memory_order_release);
   }
-  return ok == 1;
+  return v == 1;
 }
 
 template <class Cf, bool PREFETCH>
@@ -1073,13 +1068,8 @@ int launch_persistent(const GemmDesc& d, const float2* A, const float2* B, float
   const size_t need = 1024 + kFzStages * Cf::kStageBytes + (2 * kFzStages + 5) * 8 + 16 + 4 * BN / 2 * 8 + 8 * 4 +
                       8 * 8 + Cf::kEpiWarps * Cf::kStageBlocks * 256 * 8;
   const size_t smem = need > 117 * 1024 ? need : 117 * 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_fused_bf16_kernel<Cf, PREFETCH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    attr_set = true;
-  }
+  static std::atomic<int> attr_done[kMaxDevices];
+  if (int e = smem_attr_once(attr_done, tc_fused_bf16_kernel<Cf, PREFETCH>, (int)smem)) return e;
   FzGeom g;
   g.M = (int)d.M, g.N = (int)d.N, g.K = (int)d.K;
   g.tiles_m = (int)(d.M / BM), g.tiles_n = (int)(2 * d.N / BN), g.nk = (int)((d.K + Cf::kKC - 1) / Cf::kKC);
@@ -1268,7 +1258,8 @@ int prep_planes(const GemmDesc& d, const float2* A, const float2* B, uint8_t* sc
   uint8_t* b_hi = a_lo + nb * M * K2 * es;
   uint8_t* b_lo = b_hi + nb * N2 * K2 * es;
   const int64_t na = nb * M * d.K, nbb = nb * d.N * d.K;
-  auto blocks = [](int64_t n) { return (unsigned)(n / 256 + 1 < 152 * 32 ? n / 256 + 1 : 152 * 32); };
+  const int64_t cap = (int64_t)sm_count() * 32;
+  auto blocks = [cap](int64_t n) { return (unsigned)(n / 256 + 1 < cap ? n / 256 + 1 : cap); };
   const bool kpow2 = (d.K & (d.K - 1)) == 0;
   if (!with_a) {
     // A is split on chip by the kernel
@@ -1316,13 +1307,8 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
   const CUtensorMap &mAh = maps.ah, &mAl = maps.al, &mBh = maps.bh, &mBl = maps.bl;
   constexpr uint32_t STAGE_BYTES = 2 * BM * 128 + 2 * BN * 128;
   const size_t smem = 1024 + STAGES * STAGE_BYTES + (2 * STAGES + 5) * 8 + 16 + BN / 2 * 8;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kTF32, BN, STAGES>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    attr_set = true;
-  }
+  static std::atomic<int> attr_done[kMaxDevices];
+  if (int e = smem_attr_once(attr_done, tc_gemm_kernel<kTF32, BN, STAGES>, (int)smem)) return e;
   const int64_t tiles = (M / BM) * (N2 / BN);
   for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
     int64_t cnt = nb - b0 < 65535 ? nb - b0 : 65535;
@@ -1424,6 +1410,45 @@ int bounded_wait_selftest(uint64_t limit_ns, int* timed_out) {
   if (e == cudaSuccess) e = cudaMemcpy(timed_out, d, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(d);
   return (int)e;
+}
+
+// Loads every kernel of this file onto the current device (see
+// preload_kernels_core in kernels.cu).
+int preload_kernels_tc() {
+  const void* fns[] = {
+      (const void*)tc_gemm_kernel<true, 256, 2>,
+      (const void*)tc_gemm_kernel<true, 128, 3>,
+      (const void*)tc_gemm_kernel<true, 64, 4>,
+      (const void*)tc_gemm_kernel<false, 256, 2>,
+      (const void*)tc_gemm_kernel<false, 128, 3>,
+      (const void*)tc_gemm_kernel<false, 64, 4>,
+      (const void*)tc_fused_bf16_kernel<FzCfg<128>, false>,
+      (const void*)tc_fused_bf16_kernel<FzCfg<128>, true>,
+      (const void*)tc_fused_bf16_kernel<FzCfg<64>, false>,
+      (const void*)tc_fused_bf16_kernel<FzCfg<64>, true>,
+      (const void*)tc_fused_bf16_kernel<FzCfg<256>, false>,
+      (const void*)tc_fused_bf16_kernel<FzWideCfg, false>,
+      (const void*)tc_fused_bf16_kernel<FzWideCfg, true>,
+      (const void*)tc_fused_bf16_kernel<HyCfg, false>,
+      (const void*)tc_fused_bf16_kernel<PlCfg<256, 128>, false>,
+      (const void*)tc_fused_bf16_kernel<PlCfg<128, 128>, false>,
+      (const void*)tc_fused_bf16_kernel<PlCfg<256, 64>, false>,
+      (const void*)tc_fused_bf16_kernel<PlCfg<64, 128>, false>,
+      (const void*)prep_a_kernel<false>,
+      (const void*)prep_a_kernel<true>,
+      (const void*)prep_b_kernel<false>,
+      (const void*)prep_b_kernel<true>,
+      (const void*)prep_a_vec_kernel<false>,
+      (const void*)prep_a_vec_kernel<true>,
+      (const void*)prep_b_vec_kernel<false>,
+      (const void*)prep_b_vec_kernel<true>,
+  };
+  cudaFuncAttributes fa;
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return (int)e;
+  }
+  return 0;
 }
 
 }  // namespace tnc

@@ -27,7 +27,8 @@ struct Leaf {
   double pos[3] = {0, 0, 0};
   double radius = 0;
   int qubit = -1;
-  int time = 0;
+  int time = 0;   // index of the 2q gate among the circuit's 2q gates
+  int layer = 0;  // ASAP layer: 1 + the latest layer on either of its qubits (0 for a bare wire)
 };
 
 struct Network {

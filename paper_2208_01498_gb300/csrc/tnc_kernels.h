@@ -116,6 +116,8 @@ int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, voi
 int launch_grouped_narrow(const GroupedDesc* d_descs, int n, int64_t total_blocks, const void* base, void* ws,
                           void* stream);
 int launch_zero(void* ptr, size_t bytes, void* stream);
+// SM count of the current device (152, a GB300's, when there is none)
+int sm_count();
 int launch_set_counter(uint64_t* d_ctr, uint64_t value, void* stream);
 
 // kernel variants of launch_gemm

@@ -25,6 +25,7 @@ TNC_ESTATE = -6
 TNC_ENOTFOUND = -7
 
 FORMS = {"fp32": 0, "3xtf32": 1, "split_bf16": 2}
+EMBEDDINGS = {"auto": 0, "collapsed": 1, "spacetime": 2}
 
 
 class TncError(RuntimeError):
@@ -54,7 +55,7 @@ class PlanOpts(C.Structure):
     _fields_ = [("n_open", C.c_int), ("open_qubits", C.POINTER(C.c_int)), ("max_batch", C.c_int),
                 ("mem_cap_bytes", C.c_size_t), ("form", C.c_int), ("seed", C.c_uint64),
                 ("ssa_trials", C.c_int), ("leaf_size", C.c_int), ("max_group_log2", C.c_int),
-                ("use_graph", C.c_int)]
+                ("use_graph", C.c_int), ("embedding", C.c_int), ("n_starts", C.c_int)]
 
 
 class PlanReport(C.Structure):
@@ -62,7 +63,8 @@ class PlanReport(C.Structure):
                 ("peak_bytes", C.c_double), ("ws_bytes", C.c_size_t), ("n_slices", C.c_double),
                 ("n_slice_groups", C.c_int), ("n_sliced", C.c_int), ("n_nodes", C.c_int),
                 ("n_leaves", C.c_int), ("max_rank", C.c_int), ("n_launches", C.c_int),
-                ("plan_ms", C.c_double), ("tree_cost_log2", C.c_double)]
+                ("plan_ms", C.c_double), ("tree_cost_log2", C.c_double), ("embedding_used", C.c_int),
+                ("seed_used", C.c_int), ("time_scale", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -204,7 +206,8 @@ class Plan:
 
     def __init__(self, net: Network, open_qubits=(), max_batch: int = 1, mem_cap_bytes: int = 0,
                  form: str = "fp32", seed: int = 1, ssa_trials: int = 32, leaf_size: int = 8,
-                 max_group_log2: int = 6, use_graph: bool = True):
+                 max_group_log2: int = 6, use_graph: bool = True, embedding: str = "auto",
+                 n_starts: int = 0):
         o = PlanOpts()
         lib.tnc_plan_opts_default(C.byref(o))
         self._open = np.ascontiguousarray(sorted(int(q) for q in open_qubits), np.int32)
@@ -218,6 +221,9 @@ class Plan:
         o.leaf_size = int(leaf_size)
         o.max_group_log2 = int(max_group_log2)
         o.use_graph = int(bool(use_graph))
+        o.embedding = EMBEDDINGS[embedding] if isinstance(embedding, str) else int(embedding)
+        if n_starts:
+            o.n_starts = int(n_starts)
         rep = PlanReport()
         h = C.c_void_p()
         _check(lib.tnc_plan(net.handle, C.byref(o), C.byref(h), C.byref(rep)), "tnc_plan")

@@ -7,7 +7,10 @@ GPU's memory, or a latency-bound handler that may not call cudaMalloc/cudaFree
 library holds statically.  Its results must equal those of the ordinary entry
 point with a caller-provided workspace, call after call (the static array
 keeps the previous call's contents, so the second call checks that nothing
-stale leaks through).  Collected last on purpose.
+stale leaks through), and the device's free memory must not change across
+the calls (its set-up happens in tnc_plan_upload).  The tensor-core plans put
+their hi/lo operand planes in the same static array.  Collected last on
+purpose.
 """
 import ctypes
 
@@ -35,21 +38,46 @@ def _call(tnc, p, bits, out):
                                                   ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
 
 
-def test_static_workspace_matches_caller_workspace(tnc):
-    gl = C.random_2d(4, 4, 8, 21)
-    oq = [1, 6]
-    p = tnc.Plan(tnc.Network(gl), open_qubits=oq, max_batch=4)
+def _free_bytes():
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
+# (circuit, open qubits, batch, form, kernel choice of the tensor-core steps, tolerance vs the oracle)
+CASES = {
+    "fp32_4x4": (lambda: C.random_2d(4, 4, 8, 21), [1, 6], 4, "fp32", None, 1e-5),
+    "split_bf16_5x5": (lambda: C.random_2d(5, 5, 8, 1), [0, 3], 16, "split_bf16", None, 1e-4),
+    # every tensor-core step on the plane-fed tile: its hi/lo planes are scratch inside the static array
+    "split_bf16_5x5_planes": (lambda: C.random_2d(5, 5, 8, 1), [0, 3], 16, "split_bf16", 1, 1e-4),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_static_workspace_matches_caller_workspace(tnc, case):
+    make, oq, batch, form, tc_tile, tol = CASES[case]
+    gl = make()
+    n = gl.n_qubits
+    p = tnc.Plan(tnc.Network(gl), open_qubits=oq, max_batch=batch, form=form)
     assert p.ws_bytes <= 64 << 20
+    if tc_tile is not None:
+        ch = [[k, tc_tile if k == tnc.KG["tc"] else t] for k, t in p.get_kernels()]
+        p.set_kernels(ch)
+    if form != "fp32":
+        assert any(k == tnc.KG["tc"] for k, _ in p.get_kernels()), "the plan has no tensor-core step"
     p.upload()
-    for call, seed in enumerate((3, 4)):
-        bits = C.random_bitstrings(16, 4, seed)
-        ref = tnc.contract_amplitudes(p, bits).cpu().numpy()
-        out = torch.full((4, 4), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
-        assert _call(tnc, p, bits, out) == tnc.TNC_OK, tnc.lib.tnc_last_error()
-        torch.cuda.synchronize()
-        got = out.cpu().numpy()
-        assert O.rel_error(got, ref, 16).max() <= 1e-5, f"call {call}"
-        assert O.rel_error(got, O.statevector_amplitudes(gl, bits, oq), 16).max() <= 1e-5
+    seeds = (3, 4)
+    bits = [C.random_bitstrings(n, batch, s) for s in seeds]
+    refs = [tnc.contract_amplitudes(p, b).cpu().numpy() for b in bits]
+    outs = [torch.full((batch, 1 << len(oq)), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
+            for _ in seeds]
+    free0 = _free_bytes()
+    for call in range(len(seeds)):
+        assert _call(tnc, p, bits[call], outs[call]) == tnc.TNC_OK, tnc.lib.tnc_last_error()
+        assert _free_bytes() == free0, f"call {call} changed the device's free memory"
+    for call in range(len(seeds)):
+        got = outs[call].cpu().numpy()
+        assert O.rel_error(got, refs[call], n).max() <= 1e-5, f"call {call}"
+        assert O.rel_error(got, O.statevector_amplitudes(gl, bits[call], oq), n).max() <= tol, f"call {call}"
 
 
 def test_static_workspace_limits(tnc):
