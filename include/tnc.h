@@ -90,6 +90,10 @@ typedef struct {
                                (d+1)-dimensional network before the collapse, Fig. 1a; d <= 2 only) */
   int n_starts;             /* separator hierarchies built per embedding, with seeds seed, seed + 1, ...;
                                the one with the smallest Eq. 3 cost is kept (0 = 1) */
+  int refine_window;        /* 0: the separator tree as built; 3..12: each tree is refined by exact
+                               re-association of windows of up to this many subtrees (an addition to
+                               the paper's method; it never raises the Eq. 3 cost nor enlarges the
+                               largest intermediate) */
 } tnc_plan_opts;
 
 #define TNC_EMBED_AUTO 0
@@ -114,6 +118,8 @@ typedef struct {
   int embedding_used;   /* TNC_EMBED_COLLAPSED or TNC_EMBED_SPACETIME: the kept tree's embedding */
   int seed_used;        /* seed of the kept tree's separator search */
   double time_scale;    /* space-time embedding: distance between consecutive layers (lattice units) */
+  double sep_cost_log2; /* log2 of the kept tree's paper_ops before refinement */
+  int n_refined;        /* windows rebuilt by the refinement */
 } tnc_plan_report;
 
 /* Human-readable name of a status code. */

@@ -200,6 +200,7 @@ void tnc_plan_opts_default(tnc_plan_opts* o) {
   o->use_graph = 1;
   o->embedding = TNC_EMBED_AUTO;
   o->n_starts = 4;
+  o->refine_window = 8;
 }
 
 int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** out, tnc_plan_report* rep) {
@@ -214,7 +215,8 @@ int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** o
       opts->max_batch < 1 || opts->max_batch > 65536 || opts->form < 0 || opts->form > 2 ||
       opts->ssa_trials < 0 || opts->leaf_size < 0 || opts->max_group_log2 < 0 ||
       opts->max_group_log2 > 16 || opts->embedding < 0 || opts->embedding > 2 || opts->n_starts < 0 ||
-      opts->n_starts > 64 || (opts->embedding == TNC_EMBED_SPACETIME && N.dim > 2)) {
+      opts->n_starts > 64 || (opts->embedding == TNC_EMBED_SPACETIME && N.dim > 2) || opts->refine_window < 0 ||
+      (opts->refine_window > 0 && opts->refine_window < 3) || opts->refine_window > 12) {
     set_error("tnc_plan: invalid options");
     return TNC_EINVAL;
   }
@@ -236,14 +238,23 @@ int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** o
   int bb = 0;
   while ((1 << bb) < opts->max_batch) ++bb;
   p.beta_bits = bb;
-  // separator hierarchies over the embeddings and seeds asked for; the tree
-  // with the smallest Eq. 3 cost is kept (ties: the earlier candidate)
+  // separator hierarchies over the embeddings and seeds asked for (each
+  // refined if asked); without a cap the cheapest tree by Eq. 3 whose
+  // intermediates the executor can address is kept, with a cap the cheapest
+  // after slicing among the four cheapest trees (ties: the earlier candidate)
+  struct Cand {
+    Tree tree;
+    PlanNet pn;
+    std::vector<int> beta_labels;
+    double cost, sep_cost, time_scale;
+    int n_refined, embedding, seed, max_rank;
+  };
+  std::vector<Cand> cands;
   std::vector<double> scales;
   if (opts->embedding != TNC_EMBED_SPACETIME) scales.push_back(0.0);
   if (opts->embedding != TNC_EMBED_COLLAPSED && N.dim <= 2)
     for (double h : kTimeScales) scales.push_back(h);
   const int starts = std::max(1, opts->n_starts);
-  double best_cost = 1e300;
   for (double h : scales) {
     PlanNet pn;
     std::vector<int> bl;
@@ -254,18 +265,53 @@ int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** o
       po.trials = p.opts.ssa_trials;
       po.leaf_size = p.opts.leaf_size;
       PlannerStats st;
-      Tree t = plan_tree(pn, po, &st);
-      const double c = tree_cost_log2(t);
-      if (c < best_cost - 1e-9) {
-        best_cost = c;
-        p.tree = std::move(t);
-        p.pn = pn;
-        p.beta_labels = bl;
-        p.rep.embedding_used = h > 0 ? TNC_EMBED_SPACETIME : TNC_EMBED_COLLAPSED;
-        p.rep.seed_used = (int)po.seed;
-        p.rep.time_scale = h;
-      }
+      Cand c;
+      c.tree = plan_tree(pn, po, &st);
+      c.sep_cost = tree_cost_log2(c.tree);
+      c.n_refined = opts->refine_window ? refine_tree(pn, c.tree, opts->refine_window, 4) : 0;
+      c.cost = tree_cost_log2(c.tree);
+      c.max_rank = tree_max_rank(c.tree);
+      c.pn = pn;
+      c.beta_labels = bl;
+      c.time_scale = h;
+      c.embedding = h > 0 ? TNC_EMBED_SPACETIME : TNC_EMBED_COLLAPSED;
+      c.seed = (int)po.seed;
+      cands.push_back(std::move(c));
     }
+  }
+  std::vector<int> idx(cands.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cands[a].cost < cands[b].cost - 1e-9; });
+  int pick = -1;
+  if (!opts->mem_cap_bytes) {
+    for (int i : idx)
+      if (cands[i].max_rank <= kMaxRank) {
+        pick = i;
+        break;
+      }
+    if (pick < 0) pick = idx[0];  // compile_program reports the rank limit
+  } else {
+    double best_total = 1e300;
+    for (size_t r = 0; r < idx.size() && r < 4; ++r) {
+      Cand& c = cands[idx[r]];
+      std::vector<int> S;
+      double total = 0;
+      Tree t = c.tree;
+      if (choose_slices(c.pn, t, p.opts.form, opts->mem_cap_bytes, S, &total) != TNC_OK) continue;
+      if (total < best_total - 1e-9) best_total = total, pick = idx[r];
+    }
+    if (pick < 0) pick = idx[0];  // plan_slices reports why it cannot slice
+  }
+  {
+    Cand& c = cands[pick];
+    p.tree = std::move(c.tree);
+    p.pn = std::move(c.pn);
+    p.beta_labels = c.beta_labels;
+    p.rep.embedding_used = c.embedding;
+    p.rep.seed_used = c.seed;
+    p.rep.time_scale = c.time_scale;
+    p.rep.sep_cost_log2 = c.sep_cost;
+    p.rep.n_refined = c.n_refined;
   }
   p.rep.tree_cost_log2 = tree_cost_log2(p.tree);
   int rc = plan_slices(p, opts->mem_cap_bytes);

@@ -270,59 +270,127 @@ PlanNet exec_net(const PlanNet& base, const std::vector<int>& ser, const std::ve
   return pn;
 }
 
+// Fast model of the sliced tree: node output labels and operand labels of
+// the unsliced tree; a set S of sliced labels removes its labels from every
+// node.  Cost of all slices (log2 paper ops): |S| + log2 sum_v 2 M_v / 2^|L_v n S|
+// (L_v: the distinct labels of v's operands, M_v = 2^|L_v|, Eq. 3); peak: the
+// live-memory recursion of evaluate() with the sliced sizes.
+class SliceModel {
+ public:
+  SliceModel(const PlanNet& pn, Tree& t, int form) : t_(t), form_(form) {
+    annotate_tree(pn, t);
+    const size_t n = t.nodes.size();
+    out_.resize(n);
+    ops_.resize(n);
+    for (size_t v = 0; v < n; ++v) out_[v] = t.nodes[v].out;
+    for (size_t v = 0; v < n; ++v) {
+      const TreeNode& nd = t.nodes[v];
+      if (nd.left < 0) continue;
+      std::vector<int>& L = ops_[v];
+      std::set_union(out_[nd.left].begin(), out_[nd.left].end(), out_[nd.right].begin(), out_[nd.right].end(),
+                     std::back_inserter(L));
+    }
+  }
+
+  double cost_log2(const std::vector<char>& inS, int nS) const {
+    double mx = -1e300;
+    std::vector<double> c(t_.nodes.size(), -1e300);
+    for (size_t v = 0; v < t_.nodes.size(); ++v) {
+      if (t_.nodes[v].left < 0) continue;
+      int k = 0;
+      for (int x : ops_[v]) k += inS[x];
+      c[v] = (double)ops_[v].size() - k;
+      mx = std::max(mx, c[v]);
+    }
+    if (mx < -1e299) return 0;
+    double sum = 0;
+    for (double cv : c)
+      if (cv > -1e299) sum += std::exp2(cv - mx);
+    return nS + mx + std::log2(sum) + 1;
+  }
+
+  // peak live bytes of one slice; *big receives every node whose output
+  // alone exceeds `over` bytes
+  double peak(const std::vector<char>& inS, double over = -1, std::vector<int>* big = nullptr) const {
+    std::function<double(int)> rec = [&](int v) -> double {
+      const TreeNode& nd = t_.nodes[v];
+      const double self = size(v, inS);
+      if (big && over >= 0 && self > over) big->push_back(v);
+      if (nd.left < 0) return self;
+      const double pl = rec(nd.left), pr = rec(nd.right);
+      const double sl = size(nd.left, inS), sr = size(nd.right, inS);
+      const double first = std::min(std::max(pl, sl + pr), std::max(pr, sr + pl));
+      double work = sl + sr + self + std::max(sl, sr);
+      if (form_ != TNC_FP32) work += sl + sr + 2 * std::min(sl, sr);
+      return std::max(first, work);
+    };
+    return rec(t_.root);
+  }
+
+  const std::vector<int>& out(int v) const { return out_[v]; }
+
+ private:
+  double size(int v, const std::vector<char>& inS) const {
+    int k = 0;
+    for (int x : out_[v]) k += inS[x];
+    return std::exp2((double)out_[v].size() - k) * 8;
+  }
+  const Tree& t_;
+  int form_;
+  std::vector<std::vector<int>> out_, ops_;
+};
+
 }  // namespace
 
-int plan_slices(Plan& p, size_t cap_bytes) {
-  const PlanNet& base = p.pn;
-  p.sliced_serial.clear();
-  p.sliced_par.clear();
-  const int form = p.opts.form;
-  Tree t = p.tree;
-  PlanNet pn = exec_net(base, {}, {});
-  Eval ev = evaluate(pn, t, form);
-  if (cap_bytes == 0 || ev.peak_bytes <= (double)cap_bytes) return TNC_OK;
-  std::vector<int> S;
-  std::vector<char> in_S(base.n_labels, 0);
-  while (ev.peak_bytes > (double)cap_bytes) {
-    // candidates: contracted labels of the node at the peak and its children
+// Sliced labels for one tree under a memory cap: greedy additions scored by
+// the added work per halving of the peak, over the contracted labels of every
+// intermediate larger than the cap; then labels are dropped while the peak
+// stays under the cap, and single swaps are tried that keep it there and
+// lower the total work.  Returns TNC_ENOMEM when no set reaches the cap.
+int choose_slices(const PlanNet& base, Tree& t, int form, size_t cap_bytes, std::vector<int>& S,
+                  double* total_log2) {
+  S.clear();
+  SliceModel m(base, t, form);
+  std::vector<char> inS(base.n_labels, 0);
+  const double cap = (double)cap_bytes;
+  double peak = m.peak(inS);
+  double cost = m.cost_log2(inS, 0);
+  if (cap_bytes == 0 || peak <= cap) {
+    if (total_log2) *total_log2 = cost;
+    return TNC_OK;
+  }
+  auto sliceable = [&](int x) { return !base.global_out[x] && base.holders[x].size() >= 2; };
+  while (peak > cap) {
+    // candidates: contracted labels of every intermediate above the cap
+    std::vector<int> big;
+    m.peak(inS, cap / 2, &big);
     std::set<int> cand;
-    auto add = [&](int v) {
-      if (v < 0) return;
-      for (int x : t.nodes[v].out)
-        if (!base.global_out[x] && !in_S[x] && base.holders[x].size() >= 2) cand.insert(x);
-    };
-    add(ev.peak_node);
-    if (ev.peak_node >= 0) {
-      add(t.nodes[ev.peak_node].left);
-      add(t.nodes[ev.peak_node].right);
-    }
-    if (cand.empty()) {
-      // widen to every label of the largest intermediate
-      int big = -1;
+    for (int v : big)
+      for (int x : m.out(v))
+        if (!inS[x] && sliceable(x)) cand.insert(x);
+    if (cand.empty())
       for (size_t v = 0; v < t.nodes.size(); ++v)
-        if (big < 0 || t.nodes[v].out.size() > t.nodes[big].out.size()) big = (int)v;
-      add(big);
-    }
+        for (int x : m.out((int)v))
+          if (!inS[x] && sliceable(x)) cand.insert(x);
     if (cand.empty() || S.size() >= 40) {
-      set_error("tnc_plan: cannot slice the plan under mem_cap_bytes = %zu (peak %.3g bytes)",
-                cap_bytes, ev.peak_bytes);
+      set_error("tnc_plan: cannot slice the plan under mem_cap_bytes = %zu (peak %.3g bytes)", cap_bytes, peak);
       return TNC_ENOMEM;
     }
     int best = -1;
-    Eval bev;
-    double best_total = 1e300;
+    double best_score = 1e300, best_peak = 0, best_cost = 0;
     for (int x : cand) {
-      std::vector<int> S2 = S;
-      S2.push_back(x);
-      PlanNet pn2 = exec_net(base, S2, {});
-      Tree t2 = p.tree;
-      Eval e2 = evaluate(pn2, t2, form);
-      if (e2.peak_bytes >= ev.peak_bytes) continue;
-      double total = e2.cost_log2 + S2.size();  // log2 of total work
-      if (total < best_total - 1e-9 || (std::fabs(total - best_total) <= 1e-9 && e2.peak_bytes < bev.peak_bytes)) {
-        best_total = total;
+      inS[x] = 1;
+      const double p2 = m.peak(inS);
+      const double c2 = m.cost_log2(inS, (int)S.size() + 1);
+      inS[x] = 0;
+      if (!(p2 < peak)) continue;
+      // added log2 work per halving of the peak (fewer bits first on ties)
+      const double score = (c2 - cost) / std::log2(peak / p2);
+      if (score < best_score - 1e-12 || (std::fabs(score - best_score) <= 1e-12 && p2 < best_peak)) {
+        best_score = score;
         best = x;
-        bev = e2;
+        best_peak = p2;
+        best_cost = c2;
       }
     }
     if (best < 0) {
@@ -330,22 +398,101 @@ int plan_slices(Plan& p, size_t cap_bytes) {
       return TNC_ENOMEM;
     }
     S.push_back(best);
-    in_S[best] = 1;
-    PlanNet pn2 = exec_net(base, S, {});
-    t = p.tree;
-    ev = evaluate(pn2, t, form);
+    inS[best] = 1;
+    peak = best_peak;
+    cost = best_cost;
   }
-  // group as many sliced labels as fit (most recently chosen first)
+  // drop labels that are no longer needed (the costliest first)
+  for (bool again = true; again;) {
+    again = false;
+    int drop = -1;
+    double drop_cost = cost;
+    for (size_t i = 0; i < S.size(); ++i) {
+      inS[S[i]] = 0;
+      if (m.peak(inS) <= cap) {
+        const double c2 = m.cost_log2(inS, (int)S.size() - 1);
+        if (c2 < drop_cost) drop_cost = c2, drop = (int)i;
+      }
+      inS[S[i]] = 1;
+    }
+    if (drop >= 0) {
+      inS[S[drop]] = 0;
+      S.erase(S.begin() + drop);
+      cost = drop_cost;
+      again = true;
+    }
+  }
+  // single swaps that keep the cap and lower the work
+  std::set<int> pool;
+  {
+    std::vector<int> big;
+    std::vector<char> none(base.n_labels, 0);
+    m.peak(none, cap / 2, &big);
+    for (int v : big)
+      for (int x : m.out(v))
+        if (sliceable(x)) pool.insert(x);
+  }
+  for (int round = 0; round < 4; ++round) {
+    bool improved = false;
+    for (size_t i = 0; i < S.size(); ++i) {
+      int best_y = -1;
+      double best_c = cost;
+      inS[S[i]] = 0;
+      for (int y : pool) {
+        if (inS[y] || y == S[i]) continue;
+        inS[y] = 1;
+        if (m.peak(inS) <= cap) {
+          const double c2 = m.cost_log2(inS, (int)S.size());
+          if (c2 < best_c - 1e-9) best_c = c2, best_y = y;
+        }
+        inS[y] = 0;
+      }
+      if (best_y >= 0) {
+        S[i] = best_y;
+        cost = best_c;
+        improved = true;
+      }
+      inS[S[i]] = 1;
+    }
+    if (!improved) break;
+  }
+  if (total_log2) *total_log2 = cost;
+  return TNC_OK;
+}
+
+int plan_slices(Plan& p, size_t cap_bytes) {
+  const PlanNet& base = p.pn;
+  p.sliced_serial.clear();
+  p.sliced_par.clear();
+  const int form = p.opts.form;
+  std::vector<int> S;
+  Tree t = p.tree;
+  int rc = choose_slices(base, t, form, cap_bytes, S, nullptr);
+  if (rc != TNC_OK) return rc;
+  if (S.empty()) return TNC_OK;
+  // group sliced labels while the group still fits the cap: each time the
+  // serial label whose grouping raises the peak the least
   std::vector<int> ser = S, par;
   while (!ser.empty() && (int)par.size() < p.opts.max_group_log2) {
-    std::vector<int> ser2(ser.begin(), ser.end() - 1), par2 = par;
-    par2.push_back(ser.back());
-    PlanNet pn2 = exec_net(base, ser2, par2);
-    Tree t2 = p.tree;
-    Eval e2 = evaluate(pn2, t2, form);
-    if (e2.peak_bytes > (double)cap_bytes) break;
-    ser.swap(ser2);
-    par.swap(par2);
+    int best = -1;
+    double best_peak = (double)cap_bytes;
+    for (size_t i = 0; i < ser.size(); ++i) {
+      std::vector<int> ser2 = ser, par2 = par;
+      ser2.erase(ser2.begin() + i);
+      par2.push_back(ser[i]);
+      PlanNet pn2 = exec_net(base, ser2, par2);
+      Tree t2 = p.tree;
+      Eval e2 = evaluate(pn2, t2, form);
+      if (e2.peak_bytes <= best_peak) best_peak = e2.peak_bytes, best = (int)i;
+    }
+    if (best < 0) break;
+    par.push_back(ser[best]);
+    ser.erase(ser.begin() + best);
+  }
+  if (ser.size() > 30) {
+    set_error("tnc_plan: %zu serial sliced labels (2^%zu slice groups) exceed the executor's 2^30", ser.size(),
+              ser.size());
+    return TNC_ENOMEM;
   }
   p.sliced_serial = ser;
   p.sliced_par = par;
@@ -362,6 +509,17 @@ int compile_program(Plan& p) {
   Tree& t = p.tree;
   annotate_tree(pn, t);
   const int form = p.opts.form;
+  // the kernels address a tensor by at most kMaxRank binary indices (and a
+  // node's operands and output by at most kMaxRank bits each)
+  for (const TreeNode& nd : t.nodes) {
+    const int r = (int)nd.out.size();
+    if (r > kMaxRank) {
+      set_error("tnc_plan: an intermediate of rank %d exceeds the executor's %d binary indices; "
+                "set mem_cap_bytes to slice it",
+                r, kMaxRank);
+      return TNC_ENOMEM;
+    }
+  }
 
   std::vector<char> is_open(net.n_qubits, 0);
   for (int q : p.open_qubits) is_open[q] = 1;

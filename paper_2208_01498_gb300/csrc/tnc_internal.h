@@ -91,6 +91,9 @@ int centerpoint_points(const double* pts, int n, int D, uint64_t seed, double* c
 // the root; cost and size in log2.
 void annotate_tree(const PlanNet& pn, Tree& t);
 double tree_cost_log2(const Tree& t);       // log2 sum_nodes 2 M
+// exact re-association of windows of at most max_items subtrees (refine.cpp);
+// returns the number of windows rebuilt
+int refine_tree(const PlanNet& pn, Tree& t, int max_items, int max_passes);
 int tree_max_rank(const Tree& t);
 
 // ------------------------------------------------------------------ program
@@ -160,6 +163,10 @@ struct Plan {
 
 int compile_program(Plan& p);
 int plan_slices(Plan& p, size_t cap_bytes);
+// sliced labels of one tree under a memory cap (compile.cpp); *total_log2 =
+// log2 of the paper ops of all slices
+int choose_slices(const PlanNet& base, Tree& t, int form, size_t cap_bytes, std::vector<int>& S,
+                  double* total_log2);
 
 }  // namespace tnc
 

@@ -55,7 +55,8 @@ class PlanOpts(C.Structure):
     _fields_ = [("n_open", C.c_int), ("open_qubits", C.POINTER(C.c_int)), ("max_batch", C.c_int),
                 ("mem_cap_bytes", C.c_size_t), ("form", C.c_int), ("seed", C.c_uint64),
                 ("ssa_trials", C.c_int), ("leaf_size", C.c_int), ("max_group_log2", C.c_int),
-                ("use_graph", C.c_int), ("embedding", C.c_int), ("n_starts", C.c_int)]
+                ("use_graph", C.c_int), ("embedding", C.c_int), ("n_starts", C.c_int),
+                ("refine_window", C.c_int)]
 
 
 class PlanReport(C.Structure):
@@ -64,7 +65,8 @@ class PlanReport(C.Structure):
                 ("n_slice_groups", C.c_int), ("n_sliced", C.c_int), ("n_nodes", C.c_int),
                 ("n_leaves", C.c_int), ("max_rank", C.c_int), ("n_launches", C.c_int),
                 ("plan_ms", C.c_double), ("tree_cost_log2", C.c_double), ("embedding_used", C.c_int),
-                ("seed_used", C.c_int), ("time_scale", C.c_double)]
+                ("seed_used", C.c_int), ("time_scale", C.c_double), ("sep_cost_log2", C.c_double),
+                ("n_refined", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -207,7 +209,7 @@ class Plan:
     def __init__(self, net: Network, open_qubits=(), max_batch: int = 1, mem_cap_bytes: int = 0,
                  form: str = "fp32", seed: int = 1, ssa_trials: int = 32, leaf_size: int = 8,
                  max_group_log2: int = 6, use_graph: bool = True, embedding: str = "auto",
-                 n_starts: int = 0):
+                 n_starts: int = 0, refine_window: int | None = None):
         o = PlanOpts()
         lib.tnc_plan_opts_default(C.byref(o))
         self._open = np.ascontiguousarray(sorted(int(q) for q in open_qubits), np.int32)
@@ -224,6 +226,8 @@ class Plan:
         o.embedding = EMBEDDINGS[embedding] if isinstance(embedding, str) else int(embedding)
         if n_starts:
             o.n_starts = int(n_starts)
+        if refine_window is not None:
+            o.refine_window = int(refine_window)
         rep = PlanReport()
         h = C.c_void_p()
         _check(lib.tnc_plan(net.handle, C.byref(o), C.byref(h), C.byref(rep)), "tnc_plan")

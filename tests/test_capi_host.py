@@ -12,6 +12,7 @@ import circuits as C
 import oracle as O
 from paper_2208_01498_gb300 import tnc
 from host_emulator import contract_tree, emulate_program
+from plan_cases import GROUPED_CASE, SLICING_CAPS
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -114,7 +115,7 @@ def test_program_matches_oracle_families(family):
     assert O.rel_error(emulate_program(e, bits), ref, n).max() < 1e-5
 
 
-@pytest.mark.parametrize("cap,group", [(1 << 16, 0), (1 << 17, 3), (1 << 18, 6)])
+@pytest.mark.parametrize("cap,group", SLICING_CAPS)
 def test_slicing_sums_to_the_unsliced_result(cap, group):
     gl = C.random_2d(4, 5, 10, 2)
     bits = C.random_bitstrings(20, 2, 3)
@@ -131,12 +132,25 @@ def test_slicing_sums_to_the_unsliced_result(cap, group):
     assert O.rel_error(parts + rest, ref, 20).max() < 1e-5
 
 
+def test_grouped_case_sums_to_the_unsliced_result():
+    gl = C.random_2d(*GROUPED_CASE["shape"])
+    bits = C.random_bitstrings(20, GROUPED_CASE["batch"], 5)
+    ref = O.statevector_amplitudes(gl, bits)
+    p = tnc.Plan(tnc.Network(gl), max_batch=GROUPED_CASE["batch"], mem_cap_bytes=GROUPED_CASE["cap"],
+                 max_group_log2=GROUPED_CASE["max_group_log2"])
+    e = p.export()
+    assert len(e["sliced_par"]) >= 1
+    assert O.rel_error(emulate_program(e, bits), ref, 20).max() < 1e-5
+
+
 def test_grouped_slices_run_as_batch():
     gl = C.random_2d(3, 4, 8, 5)
     bits = C.random_bitstrings(12, 1, 1)
     ref = O.statevector_amplitudes(gl, bits)
-    full = tnc.Plan(tnc.Network(gl)).report
-    p = tnc.Plan(tnc.Network(gl), mem_cap_bytes=int(full["peak_bytes"] * 0.3), max_group_log2=2)
+    # one candidate tree, so that the cap cannot be met by another tree unsliced
+    one = dict(n_starts=1, embedding="collapsed")
+    full = tnc.Plan(tnc.Network(gl), **one).report
+    p = tnc.Plan(tnc.Network(gl), mem_cap_bytes=int(full["peak_bytes"] * 0.3), max_group_log2=2, **one)
     e = p.export()
     assert len(e["sliced_serial"]) + len(e["sliced_par"]) >= 1
     assert O.rel_error(emulate_program(e, bits), ref, 12).max() < 1e-5

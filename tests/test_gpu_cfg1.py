@@ -2,13 +2,15 @@
 workload: Haar single-qubit gates, CZ on brick patterns A, B, C, D) contracted
 along its separator tree on the GPU, against the stored amplitude that the
 FP64 side-wise oracle computed (tests/golden/make_golden.py, which calls only
-the oracle).  36 qubits put this beyond the state-vector oracle; the separator
-tree costs about 2.3e13 real flops, with the largest nodes on the tensor cores.
+the oracle).  36 qubits put this beyond the state-vector oracle; the refined
+separator tree costs about 1.4e12 real flops, with the largest nodes on the
+tensor cores.
 
 Error measure |a - a_ref| / max(|a_ref|, 2^{-n/2}) with n = 36: at most 1e-5
-for the FP32 and 3xTF32 forms, 1e-4 for split-BF16.  With a 64 GB memory cap
-the planner slices two labels (four slices), so the serial slice loop and the
-FP64 accumulation run at full size too.
+for the FP32 and 3xTF32 forms, 1e-4 for split-BF16.  Unsliced the refined
+tree needs about 1 GB; with a 256 MiB memory cap the planner slices two to four
+labels, so the serial slice loop and the FP64 accumulation run at full size
+too.
 """
 import json
 import os
@@ -18,6 +20,7 @@ import pytest
 
 import circuits as C
 import oracle as O
+from plan_cases import CFG1_REDUCED_CAP
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -45,8 +48,8 @@ def case():
 @pytest.mark.parametrize("form", ["fp32", "split_bf16", "3xtf32"])
 def test_cfg1_6x6_depth16_against_sidewise_oracle(case, form):
     tnc, gl, bits, ref = case
-    p = tnc.Plan(tnc.Network(gl), max_batch=1, form=form, mem_cap_bytes=64 << 30, ssa_trials=64)
-    assert p.ws_bytes < (64 << 30)
+    p = tnc.Plan(tnc.Network(gl), max_batch=1, form=form, mem_cap_bytes=CFG1_REDUCED_CAP, ssa_trials=64)
+    assert p.ws_bytes < 1.5 * CFG1_REDUCED_CAP
     assert p.report["n_sliced"] >= 1
     got = tnc.contract_amplitudes(p, bits).cpu().numpy()
     torch.cuda.synchronize()

@@ -13,6 +13,7 @@ import pytest
 import circuits as C
 import oracle as O
 from oracle.stabilizer import stabilizer_amplitudes
+from plan_cases import GROUPED_CASE, PARTIAL_CASE, SLICING_CAPS
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -116,7 +117,7 @@ def test_tree_order_independence(tnc):
     assert O.rel_error(vals[0], vals[2], 20).max() < 2e-5
 
 
-@pytest.mark.parametrize("cap,group", [(1 << 16, 0), (1 << 17, 3), (1 << 18, 6)])
+@pytest.mark.parametrize("cap,group", SLICING_CAPS)
 def test_slicing(tnc, cap, group):
     gl = C.random_2d(4, 5, 10, 2)
     bits = C.random_bitstrings(20, 2, 3)
@@ -127,10 +128,21 @@ def test_slicing(tnc, cap, group):
     _check(got, ref, 20)
 
 
+def test_grouped_and_serial_slices(tnc):
+    gl = C.random_2d(*GROUPED_CASE["shape"])
+    bits = C.random_bitstrings(20, GROUPED_CASE["batch"], 5)
+    ref = O.statevector_amplitudes(gl, bits)
+    got, p = _run(tnc, gl, bits, mem_cap_bytes=GROUPED_CASE["cap"], max_group_log2=GROUPED_CASE["max_group_log2"])
+    ex = p.export()
+    assert len(ex["sliced_par"]) >= 1 and len(ex["sliced_serial"]) >= 1
+    _check(got, ref, 20)
+
+
 def test_partial_slice_groups_add_up(tnc):
     gl = C.random_2d(4, 5, 10, 2)
     bits = C.random_bitstrings(20, 2, 3)
-    p = tnc.Plan(tnc.Network(gl), open_qubits=[1], max_batch=2, mem_cap_bytes=1 << 16, max_group_log2=0)
+    p = tnc.Plan(tnc.Network(gl), open_qubits=PARTIAL_CASE["open"], max_batch=PARTIAL_CASE["batch"],
+                 mem_cap_bytes=PARTIAL_CASE["cap"], max_group_log2=PARTIAL_CASE["max_group_log2"])
     ng = p.report["n_slice_groups"]
     assert ng >= 4
     db = torch.from_numpy(bits).cuda()
@@ -154,6 +166,26 @@ def test_config2_reduced(tnc):
     ref = O.statevector_amplitudes(gl, info["bits"], info["open"])
     got, _ = _run(tnc, gl, info["bits"], info["open"])
     _check(got, ref, 16)
+
+
+@pytest.fixture(scope="module")
+def config2_5x5():
+    """The Sycamore-type rules on a 5 x 5 grid (14 cycles of fSim(pi/2, pi/6)
+    on the staggered ABCD matchings, 6 seed-random open qubits, one
+    seed-random bitstring for the other 19): 25 qubits, within the state
+    vector (about two minutes on the host)."""
+    gl = C.sycamore(5, 14, 0)
+    bits = C.random_bitstrings(25, 1, 0)
+    oq = [int(q) for q in C.random_open_qubits(25, 6, 0)]
+    return gl, bits, oq, O.statevector_amplitudes(gl, bits, oq)
+
+
+@pytest.mark.parametrize("form", ["fp32", "split_bf16", "3xtf32"])
+def test_config2_reduced_5x5(tnc, config2_5x5, form):
+    gl, bits, oq, ref = config2_5x5
+    got, p = _run(tnc, gl, bits, oq, form=form)
+    assert got.shape == (1, 64)
+    _check(got, ref, 25, form)
 
 
 def test_config3_reduced_wht(tnc):

@@ -5,6 +5,7 @@ import pytest
 
 import circuits as C
 import oracle as O
+from plan_cases import TC_CASE
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -31,12 +32,14 @@ def _n_tc(p):
     return sum(1 for s in p.export()["steps"] if s["kind"] == 1 and s["kernel"] == 4)
 
 
+
+
 @pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
 def test_single_tensor_core_node(tnc, form):
-    gl = C.random_2d(4, 5, 10, 2)
-    bits = C.random_bitstrings(20, 16, 4)
-    ref = O.statevector_amplitudes(gl, bits)
-    got, p = _run(tnc, gl, bits, form)
+    gl = C.random_2d(*TC_CASE["shape"])
+    bits = C.random_bitstrings(20, TC_CASE["batch"], 4)
+    ref = O.statevector_amplitudes(gl, bits, TC_CASE["open"])
+    got, p = _run(tnc, gl, bits, form, oq=TC_CASE["open"])
     assert _n_tc(p) >= 1
     assert O.rel_error(got, ref, 20).max() <= TOL[form]
 
@@ -66,8 +69,9 @@ def test_dense_batched_nodes_random_2d(tnc, form):
 def test_tensor_core_error_flag_clear(tnc):
     """No bounded wait of the tcgen05 kernel timed out during the tests."""
     import ctypes
-    gl = C.random_2d(4, 5, 10, 2)
-    _run(tnc, gl, C.random_bitstrings(20, 16, 4), "split_bf16")
+    gl = C.random_2d(*TC_CASE["shape"])
+    _, p = _run(tnc, gl, C.random_bitstrings(20, TC_CASE["batch"], 4), "split_bf16", oq=TC_CASE["open"])
+    assert _n_tc(p) >= 1
     flag = ctypes.c_int(-1)
     assert tnc.lib.tnc_device_error(ctypes.byref(flag)) == 0
     assert flag.value == 0

@@ -19,6 +19,7 @@ import pytest
 
 import circuits as C
 import oracle as O
+from plan_cases import TC_CASE
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,9 +47,11 @@ def _free_bytes():
 # (circuit, open qubits, batch, form, kernel choice of the tensor-core steps, tolerance vs the oracle)
 CASES = {
     "fp32_4x4": (lambda: C.random_2d(4, 4, 8, 21), [1, 6], 4, "fp32", None, 1e-5),
-    "split_bf16_5x5": (lambda: C.random_2d(5, 5, 8, 1), [0, 3], 16, "split_bf16", None, 1e-4),
+    "split_bf16_4x5": (lambda: C.random_2d(*TC_CASE["shape"]), TC_CASE["open"], TC_CASE["batch"], "split_bf16", None,
+                       1e-4),
     # every tensor-core step on the plane-fed tile: its hi/lo planes are scratch inside the static array
-    "split_bf16_5x5_planes": (lambda: C.random_2d(5, 5, 8, 1), [0, 3], 16, "split_bf16", 1, 1e-4),
+    "split_bf16_4x5_planes": (lambda: C.random_2d(*TC_CASE["shape"]), TC_CASE["open"], TC_CASE["batch"], "split_bf16",
+                              1, 1e-4),
 }
 
 
