@@ -123,6 +123,32 @@ def _cpu_oracle(gl, bits, max_seconds: float = 20.0):
     return n_done / dt, n_done, dt
 
 
+def _oracle_chunk(job):
+    """One worker's share of the all-cores oracle timing (spawned process)."""
+    gl, bits = job
+    import oracle as O
+    O.iqp_transfer_amplitudes(gl, bits)
+    return bits.shape[0]
+
+
+def _cpu_oracle_all_cores(gl, bits, per_core: int = 32):
+    """The same oracle on every host core: a spawned process pool (the oracle
+    itself is elementwise NumPy, one thread), per_core bitstrings per
+    worker; returns amplitudes/s, workers, bitstrings, seconds."""
+    import multiprocessing as mp
+    ncores = os.cpu_count() or 1
+    flat = bits.reshape(-1, bits.shape[-1])
+    need = per_core * ncores
+    flat = np.concatenate([flat] * (need // flat.shape[0] + 1))[:need]
+    jobs = [(gl, flat[i * per_core:(i + 1) * per_core]) for i in range(ncores)]
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        pool.map(_oracle_chunk, jobs[:ncores])  # start-up and imports outside the timing
+        t0 = time.perf_counter()
+        n = sum(pool.map(_oracle_chunk, jobs))
+        dt = time.perf_counter() - t0
+    return n / dt, ncores, n, dt
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -152,70 +178,123 @@ def run_reference(args):
     return 0
 
 
-def serving_measure(tnc, torch, form: str, seed: int = 0, n_req: int = 240, cost_cap_log2: float = 36.0,
-                    ws_cap_bytes: int = 8 << 30):
-    """Poisson-arriving amplitude requests over the mixed pool (2D L x L
-    random circuits and (2+1)D layered circuits), 1-256 bitstrings each
-    (log-uniform), served by the continuous-batching loop; p50/p99 latency and
-    amplitudes/s at two arrival rates relative to the measured single-stream
-    capacity.  Instances planned above 2^cost_cap_log2 paper ops are excluded
-    and listed, as are those whose workspace exceeds ws_cap_bytes."""
+SERVING_RATES = (0.25, 0.5, 0.75, 0.9, 1.0, 1.2)
+SERVING_BUCKETS = (1, 16, 256)
+
+
+def _serve(tnc, torch, arena, reqs, gaps, n_streams):
+    """Submit the requests at their Poisson arrival times; latencies and span."""
+    srv = tnc.Server(arena, n_streams=n_streams)
+    tickets = []
+    start = time.perf_counter()
+    due = start
+    for (_, p, bits), gap in zip(reqs, gaps):
+        due += gap
+        while time.perf_counter() < due:
+            pass
+        out = torch.empty((bits.shape[0], 1 << p.n_open), dtype=torch.complex128, device="cuda")
+        tickets.append(srv.submit(p, bits, out))
+    lat = [srv.wait(t, 600000) for t in tickets]
+    span = time.perf_counter() - start
+    srv.close()
+    return np.asarray(lat), span
+
+
+def serving_measure(tnc, torch, forms=("split_bf16", "fp32"), seed: int = 0, n_req: int = 1000,
+                    cost_cap_flops: float = 2.0 ** 50, arena_bytes: int = 64 << 30, n_streams: int = 4,
+                    rates=SERVING_RATES):
+    """Poisson-arriving amplitude requests over the mixed pool (2D L x L random
+    circuits, L 4..10, depth 8..20, and (2+1)D layered circuits), 1-256
+    bitstrings each (log-uniform), served by the continuous-batching loop over
+    a device arena.  Every pool instance is planned under half the arena
+    (sliced where needed) and autotuned, per form and batch bucket; an
+    instance whose plan exceeds cost_cap_flops real flops (or cannot be
+    planned) is listed as excluded with its planned cost.  Per form: the
+    single-stream service time of the mix (the capacity), then n_req requests
+    at each rate factor of that capacity, p50/p99 latency and amplitudes/s;
+    and a serial queue (one stream, no overlap) at the same arrivals for
+    rate factors 0.9 and 1.2."""
     rng = np.random.default_rng(seed + 17)
-    buckets = [1, 16, 256]
     pool, excluded = [], []
     for gl in C.serving_pool(seed):
         net = tnc.Network(gl)
-        big = tnc.Plan(net, max_batch=buckets[-1], form=form)
-        if big.report["tree_cost_log2"] > cost_cap_log2 or big.ws_bytes > ws_cap_bytes:
-            excluded.append({"circuit": gl.name, "paper_ops_log2": round(big.report["tree_cost_log2"], 1),
-                             "ws_GB": round(big.ws_bytes / 1e9, 1)})
+        plans, why = {}, None
+        for f in forms:
+            try:
+                big = tnc.Plan(net, max_batch=SERVING_BUCKETS[-1], form=f, mem_cap_bytes=arena_bytes // 2)
+            except tnc.TncError as e:
+                why = f"{f}: {str(e)[:120]}"
+                break
+            if big.report["real_flops"] > cost_cap_flops:
+                why = f"planned {big.report['real_flops']:.3g} real flops > 2^{math.log2(cost_cap_flops):.0f}"
+                plans[f] = {SERVING_BUCKETS[-1]: big}
+                break
+            plans[f] = {b: (big if b == SERVING_BUCKETS[-1] else
+                            tnc.Plan(net, max_batch=b, form=f, mem_cap_bytes=arena_bytes // 2))
+                        for b in SERVING_BUCKETS}
+        if why:
+            r = next(iter(plans.values()))[SERVING_BUCKETS[-1]].report if plans else None
+            excluded.append({"circuit": gl.name, "reason": why,
+                             "real_flops": r["real_flops"] if r else None,
+                             "paper_ops_log2": round(r["tree_cost_log2"], 1) if r else None,
+                             "ws_GB": round(r["ws_bytes"] / 1e9, 2) if r else None})
             continue
-        pool.append((gl, {b: (big if b == buckets[-1] else tnc.Plan(net, max_batch=b, form=form))
-                          for b in buckets}))
+        pool.append((gl, plans))
+    result = {"pool": [{"circuit": gl.name, "qubits": gl.n_qubits,
+                        "real_flops_256": pl[forms[0]][SERVING_BUCKETS[-1]].report["real_flops"],
+                        "ws_GB_256": round(pl[forms[0]][SERVING_BUCKETS[-1]].ws_bytes / 1e9, 3)} for gl, pl in pool],
+              "excluded": excluded, "cost_cap_real_flops": cost_cap_flops, "arena_GB": arena_bytes / 1e9,
+              "requests_per_rate": n_req, "streams": n_streams, "forms": {}}
     if not pool:
-        return {"excluded": excluded}
-    reqs = []
+        return result
+    # one request sequence for every form and rate
+    seq = []
     for i in range(n_req):
-        gl, plans = pool[int(rng.integers(len(pool)))]
+        k = int(rng.integers(len(pool)))
         nb = int(round(float(np.exp(rng.uniform(0.0, np.log(256.0))))))
-        bucket = next(b for b in buckets if b >= nb)
-        reqs.append((gl, plans[bucket], C.random_bitstrings(gl.n_qubits, nb, 5000 + i)))
-    # single-stream service time of the mix (alone, warm)
-    ws = {id(p): tnc.alloc_workspace(p) for _, plans in pool for p in plans.values()}
-    for gl, p, bits in reqs[:len(pool) * 3]:
-        tnc.contract_amplitudes(p, bits, ws=ws[id(p)])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for gl, p, bits in reqs[:60]:
-        tnc.contract_amplitudes(p, bits, ws=ws[id(p)])
-        torch.cuda.synchronize()
-    service = (time.perf_counter() - t0) / 60
-    del ws
-    arena_bytes = (2 * max(p.ws_bytes for _, pl in pool for p in pl.values()) + (64 << 20)) // 256 * 256
+        seq.append((k, nb, C.random_bitstrings(pool[k][0].n_qubits, nb, 5000 + i)))
+    gaps_unit = rng.exponential(1.0, size=n_req)
     arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
-    result = {"pool": len(pool), "excluded": excluded, "requests": n_req, "streams": 4,
-              "single_stream_ms_per_request": 1e3 * service, "rates": []}
-    for factor in (0.5, 0.9):
-        rate = factor / service
-        gaps = rng.exponential(1.0 / rate, size=n_req)
-        srv = tnc.Server(arena, n_streams=4)
-        outs, tickets = [], []
-        start = time.perf_counter()
-        due = start
-        for (gl, p, bits), gap in zip(reqs, gaps):
-            due += gap
-            while time.perf_counter() < due:
-                pass
-            out = torch.empty((bits.shape[0], 1 << p.n_open), dtype=torch.complex128, device="cuda")
-            outs.append(out)
-            tickets.append(srv.submit(p, bits, out))
-        lat = [srv.wait(t, 120000) for t in tickets]
-        span = time.perf_counter() - start
+    for f in forms:
+        # autotune every plan of this form in the arena (outside any timing)
+        for _, plans in pool:
+            for p in plans[f].values():
+                p.autotune(arena[:p.ws_bytes // 256 * 256 + 256] if p.ws_bytes < arena_bytes else None, reps=2)
+        reqs = []
+        for k, nb, bits in seq:
+            bucket = next(b for b in SERVING_BUCKETS if b >= nb)
+            reqs.append((k, pool[k][1][f][bucket], bits))
+        # single-stream service time of the mix (one request at a time through
+        # the serving loop, warm): the capacity
+        srv = tnc.Server(arena, n_streams=1)
+
+        def one_by_one(rs):
+            for _, p, bits in rs:
+                out = torch.empty((bits.shape[0], 1 << p.n_open), dtype=torch.complex128, device="cuda")
+                srv.wait(srv.submit(p, bits, out), 600000)
+
+        one_by_one(reqs[:3 * len(pool)])
+        timed = reqs[:min(200, n_req)]
+        t0 = time.perf_counter()
+        one_by_one(timed)
+        service = (time.perf_counter() - t0) / len(timed)
         srv.close()
         amps = sum(b.shape[0] for _, _, b in reqs)
-        result["rates"].append({"rate_factor": factor, "requests_per_s": rate,
-                                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                                "amplitudes_per_s": amps / span})
+        fr = {"single_stream_ms_per_request": 1e3 * service, "capacity_requests_per_s": 1.0 / service,
+              "rates": [], "serial_queue": []}
+        for factor in rates:
+            rate = factor / service
+            lat, span = _serve(tnc, torch, arena, reqs, gaps_unit / rate, n_streams)
+            fr["rates"].append({"rate_factor": factor, "requests_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
+                                "p99_ms": float(np.percentile(lat, 99)), "amplitudes_per_s": amps / span})
+            if factor in (0.9, 1.2):
+                lat1, span1 = _serve(tnc, torch, arena, reqs, gaps_unit / rate, 1)
+                fr["serial_queue"].append({"rate_factor": factor, "p50_ms": float(np.percentile(lat1, 50)),
+                                           "p99_ms": float(np.percentile(lat1, 99)),
+                                           "amplitudes_per_s": amps / span1})
+        result["forms"][f] = fr
+    del arena
+    torch.cuda.empty_cache()
     return result
 
 
@@ -347,6 +426,52 @@ def _tune(plan, ws, stream, cache_path, key):
     return changed
 
 
+def _form_peaks(torch):
+    """TF32 and FP32 GEMM rates of this GPU measured in the run: cuBLAS through
+    torch.matmul on 8192^3 fp32 operands with TF32 allowed (tensor cores) and
+    not allowed (CUDA cores), CUDA events after warm-up."""
+    n, reps = 8192, 10
+    a = torch.randn(n, n, device="cuda")
+    b = torch.randn(n, n, device="cuda")
+    prev = torch.backends.cuda.matmul.allow_tf32
+    res = {}
+    try:
+        for name, tf32 in (("tf32_tflops", True), ("fp32_tflops", False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            for _ in range(3):
+                a @ b
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    del a, b
+    torch.cuda.empty_cache()
+    return res
+
+
+WORKLOADS = ("iqp_5x8", "rand2d_8x8_d16")
+
+
+def _make_workload(args, rank):
+    """(name, gate list, bitstrings [steps][batch][n], plan options) of the
+    benchmark workload: the 5 x 8 IQP circuit with 256 bitstrings per request,
+    or the 8 x 8 depth-16 random circuit with one seed-random bitstring per
+    request, sliced under 180 GB."""
+    nsteps = args.warmup + args.steps
+    if args.workload == "rand2d_8x8_d16":
+        gl, _ = C.config_circuit(1, args.seed + rank)
+        bits = np.stack([C.random_bitstrings(gl.n_qubits, 1, 7919 * (args.seed + rank) + i) for i in range(nsteps)])
+        return "rand2d_8x8_d16_1amp", gl, bits, dict(max_batch=1, mem_cap_bytes=180 * 10**9)
+    gl, bits = _workload(args.seed + rank, nsteps, args.rows, args.cols)
+    return workload_name(args.rows, args.cols), gl, bits, dict(max_batch=REQ_BATCH)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -360,16 +485,19 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    gl, bits = _workload(args.seed + rank, args.warmup + args.steps, args.rows, args.cols)
+    wname, gl, bits, popts = _make_workload(args, rank)
+    batch = bits.shape[1]
     net = tnc.Network(gl)
-    plan = tnc.Plan(net, max_batch=REQ_BATCH, form=args.form, seed=1, ssa_trials=64)
+    t_plan = time.perf_counter()
+    plan = tnc.Plan(net, form=args.form, seed=1, ssa_trials=64, **popts)
+    plan_s = time.perf_counter() - t_plan
     rep = plan.report
     ws = tnc.alloc_workspace(plan)
-    out = torch.empty((REQ_BATCH, 1), dtype=torch.complex128, device=dev)
+    out = torch.empty((batch, 1), dtype=torch.complex128, device=dev)
     d_bits = torch.from_numpy(bits).to(dev)
     stream = torch.cuda.current_stream()
     plan.upload(stream)
-    tuned = _tune(plan, ws, stream, args.tune_cache, f"{workload_name(args.rows, args.cols)}:{args.form}:{rank}")
+    tuned = _tune(plan, ws, stream, args.tune_cache, f"{wname}:{args.form}:{rank}") if args.autotune else 0
     rep = plan.report
 
     for w in range(args.warmup):
@@ -395,9 +523,10 @@ def run_ours(args):
     t_ms = e0.elapsed_time(e1)
     # ---- the same requests again with CUDA events around every step on the
     # launch stream (eager launches): per-kernel durations for the roofline
+    prof_steps = args.steps if args.workload == "iqp_5x8" else 1
     plan.set_profiling(True)
     torch.cuda.synchronize()
-    for k in range(args.steps):
+    for k in range(prof_steps):
         tnc.contract_amplitudes_dbits(plan, d_bits[args.warmup + k], out=out, ws=ws, stream=stream)
     torch.cuda.synchronize()
     prof = plan.profile()
@@ -406,43 +535,54 @@ def run_ours(args):
         t = torch.tensor([t_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_ms = float(t.item())
-    amps = world * args.steps * REQ_BATCH
+    amps = world * args.steps * batch
     value = amps / (t_ms / 1e3)
 
     last_out = out.clone()
 
     # ---- the FP32 CUDA-core form on the same requests (the metric's reference form)
     fp32_form = None
-    if args.form != "fp32":
-        p32 = tnc.Plan(net, max_batch=REQ_BATCH, form="fp32", seed=1, ssa_trials=64)
-        ws32 = tnc.alloc_workspace(p32)
-        _tune(p32, ws32, stream, args.tune_cache, f"{workload_name(args.rows, args.cols)}:fp32:{rank}")
+    if args.form != "fp32" and (args.workload == "iqp_5x8" or args.compare_forms):
+        p32 = tnc.Plan(net, form="fp32", seed=1, ssa_trials=64, **popts)
+        ws32 = tnc.alloc_workspace(p32) if args.workload == "iqp_5x8" else None
+        if ws32 is None:  # the 8 x 8 workload: one workspace at a time
+            del ws
+            torch.cuda.empty_cache()
+            ws32 = tnc.alloc_workspace(p32)
+        if args.autotune:
+            _tune(p32, ws32, stream, args.tune_cache, f"{wname}:fp32:{rank}")
         out32 = torch.empty_like(out)
-        for w in range(args.warmup):
+        n32 = args.steps if args.workload == "iqp_5x8" else 1
+        for w in range(args.warmup if args.workload == "iqp_5x8" else 0):
             tnc.contract_amplitudes_dbits(p32, d_bits[w], out=out32, ws=ws32, stream=stream)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for k in range(args.steps):
-            tnc.contract_amplitudes_dbits(p32, d_bits[args.warmup + k], out=out32, ws=ws32, stream=stream)
+        for k in range(n32):
+            tnc.contract_amplitudes_dbits(p32, d_bits[args.warmup + args.steps - n32 + k], out=out32, ws=ws32,
+                                          stream=stream)
         f1.record(stream)
         torch.cuda.synchronize()
         t32 = f0.elapsed_time(f1)
         a, r = last_out.cpu().numpy(), out32.cpu().numpy()
         floor = 2.0 ** (-gl.n_qubits / 2)
         rel = float(np.max(np.abs(a - r) / np.maximum(np.abs(r), floor)))
-        fp32_form = {"value": world * args.steps * REQ_BATCH / (t32 / 1e3), "unit": "amplitudes/s",
-                     "ms_per_step": t32 / args.steps, "max_rel_err_vs_fp32": rel}
-        del ws32
+        fp32_form = {"value": world * n32 * batch / (t32 / 1e3), "unit": "amplitudes/s",
+                     "ms_per_step": t32 / n32, "steps": n32, "max_rel_err_vs_fp32": rel}
+        del ws32, p32
+        torch.cuda.empty_cache()
+        if args.workload != "iqp_5x8":
+            ws = tnc.alloc_workspace(plan)
 
     # ---- end to end through the host-buffer API
     pinned = torch.from_numpy(bits).pin_memory()
-    res = torch.empty((REQ_BATCH, 1), dtype=torch.complex128).pin_memory()
+    res = torch.empty((batch, 1), dtype=torch.complex128).pin_memory()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    n_e2e = args.steps
     t0 = time.perf_counter()
-    for k in range(args.steps):
+    for k in range(n_e2e):
         tnc.contract_amplitudes(plan, pinned[args.warmup + k].numpy(), out=out, ws=ws, stream=stream)
         res.copy_(out, non_blocking=True)
         stream.synchronize()
@@ -451,11 +591,14 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = {"value": amps / e2e_s, "unit": "amplitudes/s", "h2d_bytes_per_step": int(REQ_BATCH * gl.n_qubits),
-           "d2h_bytes_per_step": int(REQ_BATCH * 16)}
+    e2e = {"value": world * n_e2e * batch / e2e_s, "unit": "amplitudes/s",
+           "h2d_bytes_per_step": int(batch * gl.n_qubits), "d2h_bytes_per_step": int(batch * 16)}
+    del ws
+    torch.cuda.empty_cache()
 
     # ---- roofline of the dominant step (largest share of the live CUDA-event time)
     peaks, src = _peaks()
+    fpk = _form_peaks(torch)
     names = {0: "cgemm_simt_128x64", 1: "cgemm_simt_64x32", 2: "cgemm_narrow", 3: "cgemm_dot",
              4: "cgemm_tc", 5: "cgemm_simt_32x128", 100: "permute", 101: "grouped_narrow"}
     kinds = {}
@@ -475,17 +618,21 @@ def run_ours(args):
     avg_s = float(prof["ms"][di]) / druns / 1e3
     fl, by = float(prof["flops"][di]), float(prof["bytes"][di])
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # three bf16 (tf32) products per useful product; tf32 peak = half the bf16 peak
-    tc_peak = float(peaks["bf16_tflops"]) * (1.0 if args.form == "split_bf16" else 0.5)
+    # the MMA peak of the form's operand type: bf16 measured; tf32 measured in
+    # this run (cuBLAS through torch), else the nominal tf32 / bf16 ratio
+    tf32_peak = fpk.get("tf32_tflops") or float(peaks["bf16_tflops"]) * 1.1 / 2.25
+    tc_peak = float(peaks["bf16_tflops"]) if args.form == "split_bf16" else tf32_peak
     hbm = float(peaks["hbm_gbs"])
+    fp32_peak = fpk.get("fp32_tflops") or 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    # useful peak of the form: three MMA products per useful product on the tensor cores
+    form_peak = fp32_peak if args.form == "fp32" else tc_peak / 3.0
     if dkind in (100, 101, 2) or (dkind == 4 and by / hbm / 1e9 > 3.0 * fl / tc_peak / 1e12):
         # tensor-core nodes whose algorithmic bytes take longer than their MMAs at peak are HBM-bound
         roof = {"bound": "hbm", "achieved": by / avg_s / 1e9, "peak": hbm, "unit": "GB/s"}
     elif dkind == 4:
         roof = {"bound": "tensor", "achieved": 3.0 * fl / avg_s / 1e12, "peak": tc_peak, "unit": "TFLOP/s"}
     else:
-        pk = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock
-        roof = {"bound": "alu", "achieved": fl / avg_s / 1e12, "peak": pk, "unit": "TFLOP/s"}
+        roof = {"bound": "alu", "achieved": fl / avg_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     choices = plan.get_kernels()
     dtile = int(choices[di][1]) if dkind == 4 else 0
@@ -499,28 +646,44 @@ def run_ours(args):
     roof["algorithmic_bytes_per_launch"] = by
     roof["algorithmic_flops_per_launch"] = fl
     roof["share_of_device_time"] = float(prof["ms"][di]) / total_ms if total_ms else None
-    roof["peak_source"] = src + (" burst" if dkind == 4 else "")
+    roof["peak_source"] = (src + " burst") if (dkind == 4 and args.form == "split_bf16") else \
+        ("measured in this run (cuBLAS tf32)" if dkind == 4 else
+         ("measured in this run (cuBLAS fp32)" if dkind in (0, 1, 3, 5) else src))
+    # request-level roofline: sum over the steps of max(flops / form peak,
+    # bytes / HBM) against the measured time per request
+    bound_ms_req = 0.0
+    rows = []
+    for i, (ms, runs, kind, fl_i, by_i) in enumerate(zip(prof["ms"], prof["runs"], prof["kind"], prof["flops"],
+                                                          prof["bytes"])):
+        if runs == 0:
+            continue
+        b_i = max(float(by_i) / hbm / 1e6, float(fl_i) / form_peak / 1e9)  # ms per launch
+        bound_ms_req += b_i * int(runs) / prof_steps
+        st_i = steps_all[i]
+        t_launch = float(ms) / int(runs)
+        mult = 3.0 if int(kind) == 4 else 1.0
+        kb_ms = max(float(by_i) / hbm / 1e6, mult * float(fl_i) / (tc_peak if int(kind) == 4 else fp32_peak) / 1e9)
+        rows.append({"step": i, "kernel": names.get(int(kind), str(int(kind))), "tile": int(choices[i][1]),
+                     "shape": {k: st_i.get(k) for k in ("batch", "M", "N", "K")}, "launches": int(runs),
+                     "ms": t_launch, "flops": float(fl_i), "bytes": float(by_i), "form_bound_ms": b_i,
+                     "kernel_bound_ms": kb_ms, "x_over_kernel_bound": t_launch / kb_ms if kb_ms else None})
+    roof["request_bound_ms"] = bound_ms_req
+    roof["request_frac"] = bound_ms_req / (t_ms / args.steps)
+    roof["request_peak"] = {"form_peak_tflops": form_peak, "hbm_gbs": hbm,
+                            "note": "sum over steps of max(flops / form peak, bytes / HBM), form peak = tensor "
+                                    "peak / 3 products (fp32 form: cuBLAS fp32), over ms_per_step"}
     if args.steps_detail and rank == 0:
-        rows = []
-        for i, (ms, runs, kind, fl_i, by_i) in enumerate(zip(prof["ms"], prof["runs"], prof["kind"], prof["flops"],
-                                                              prof["bytes"])):
-            if runs == 0:
-                continue
-            st_i = steps_all[i]
-            t_launch = float(ms) / int(runs)
-            mult = 3.0 if int(kind) == 4 else 1.0
-            bound_ms = max(float(by_i) / hbm / 1e6, mult * float(fl_i) / tc_peak / 1e9)
-            rows.append({"step": i, "kernel": names.get(int(kind), str(int(kind))),
-                         "tile": int(choices[i][1]), "shape": {k: st_i.get(k) for k in ("batch", "M", "N", "K")},
-                         "ms": t_launch, "bound_ms": bound_ms, "x_over_bound": t_launch / bound_ms if bound_ms else None})
-        rows.sort(key=lambda r: -r["ms"])
+        rows.sort(key=lambda r: -r["ms"] * r["launches"])
         with open(args.steps_detail, "w") as f:
-            json.dump(rows, f, indent=1)
+            json.dump({"workload": wname, "form": args.form, "ms_per_step": t_ms / args.steps,
+                       "request_bound_ms": bound_ms_req, "request_frac": roof["request_frac"],
+                       "form_peak_tflops": form_peak, "tc_peak_tflops": tc_peak, "fp32_peak_tflops": fp32_peak,
+                       "hbm_gbs": hbm, "steps": rows}, f, indent=1)
     breakdown = {}
     for kd, v in sorted(kinds.items(), key=lambda kv: -kv[1]["ms"]):
-        s = v["ms"] / 1e3
+        sec = v["ms"] / 1e3
         breakdown[names.get(kd, str(kd))] = {"share": v["ms"] / total_ms, "launches": v["launches"],
-                                              "GB/s": v["bytes"] / s / 1e9, "TFLOP/s": v["flops"] / s / 1e12}
+                                              "GB/s": v["bytes"] / sec / 1e9, "TFLOP/s": v["flops"] / sec / 1e12}
 
     line = {
         "metric": "amplitudes/s", "value": value, "unit": "amplitudes/s", "n_gpus": world,
@@ -528,19 +691,24 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "c64", "3xtf32": "tf32x3 (fp32 acc)", "split_bf16": "bf16x3 (fp32 acc)"}[args.form],
         "data": "synthetic",
-        "config": {"workload": workload_name(args.rows, args.cols), "form": args.form, "bitstrings_per_request": REQ_BATCH,
+        "config": {"workload": wname, "form": args.form, "bitstrings_per_request": batch,
                    "seed": args.seed, "real_tflop_per_request": rep["real_flops"] / 1e12,
-                   "paper_ops_log2": rep["tree_cost_log2"], "ws_bytes": rep["ws_bytes"],
+                   "paper_ops_log2": math.log2(rep["paper_ops"]), "tree_cost_log2": rep["tree_cost_log2"],
+                   "separator_tree_cost_log2": rep["sep_cost_log2"], "n_sliced": rep["n_sliced"],
+                   "slice_groups": rep["n_slice_groups"], "ws_bytes": rep["ws_bytes"],
+                   "embedding": {1: "time collapsed", 2: "space-time"}.get(rep["embedding_used"]),
+                   "plan_s": plan_s,
                    "paper_bounds_log2": {k: (round(v, 1) if math.isfinite(v) else None)
                                          for k, v in net.bounds().items()
                                          if k in ("thm2_log2", "thm2_pst_log2", "sidewise_log2", "explicit_log2")},
-                   "l2": f"working set {rep['ws_bytes'] / 1e9:.1f} GB per request > 129 MB L2",
+                   "l2": f"working set {rep['ws_bytes'] / 1e9:.2f} GB per request > 129 MB L2",
                    "parallelism": f"dp{world} (independent requests)", "autotuned_steps": tuned,
                    "timing": "value: CUDA events around the K steps, device-resident bitstrings, CUDA-graph "
-                             "replay per slice group; roofline and kernel_breakdown: a second pass over the same "
-                             "K requests with CUDA events around every step (eager launches); e2e: host buffers "
-                             "through tnc_contract_amplitudes, wall clock"},
+                             "replay per slice group; roofline and kernel_breakdown: a second pass with CUDA events "
+                             "around every step (eager launches); e2e: host buffers through "
+                             "tnc_contract_amplitudes, wall clock"},
         "effective_tflops": world * args.steps * rep["real_flops"] / (t_ms / 1e3) / 1e12,
+        "measured_peaks": dict(fpk, hbm_gbs=hbm, bf16_tflops=float(peaks["bf16_tflops"]), source=src),
         "roofline": roof,
         "kernel_breakdown": breakdown,
         "fp32_form": fp32_form,
@@ -548,21 +716,48 @@ def run_ours(args):
         "clocks": ck,
         "gpu_launches": int(args.steps * rep["n_launches"]),
     }
-    if rank == 0 and not args.no_serving:
-        line["serving"] = serving_measure(tnc, torch, args.form, args.seed)
-    if rank == 0 and not args.no_expectation:
-        line["expectation"] = expectation_measure(tnc, torch, args.form, args.seed)
-    if rank == 0 and not args.no_cpu_baseline:
-        v, n_done, dt = _cpu_oracle(gl, bits[args.warmup:args.warmup + 1])
-        line["cpu_baseline"] = {"value": v, "unit": "amplitudes/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{n_done} bitstrings (one request) of the same workload by the IQP "
-                                          f"transfer-matrix closed form, {dt:.1f} s, numpy single thread "
-                                          f"(host has {os.cpu_count()} cores)"}
+    if args.workload == "iqp_5x8":
+        if rank == 0 and not args.no_serving:
+            forms = tuple(dict.fromkeys((args.form, "fp32")))
+            line["serving"] = serving_measure(tnc, torch, forms=forms, seed=args.seed,
+                                              n_req=args.serving_requests)
+        if rank == 0 and not args.no_expectation:
+            line["expectation"] = expectation_measure(tnc, torch, args.form, args.seed)
+        if rank == 0 and not args.no_cpu_baseline:
+            v, n_done, dt = _cpu_oracle(gl, bits[args.warmup:args.warmup + 1])
+            va, ncores, na, dta = _cpu_oracle_all_cores(gl, bits[args.warmup:args.warmup + 1])
+            line["cpu_baseline"] = {
+                "value": v, "unit": "amplitudes/s", "cores": 1, "kind": "oracle",
+                "sample": f"{n_done} bitstrings (one request) of the same workload by the IQP transfer-matrix "
+                          f"closed form, {dt:.1f} s, numpy on one thread (elementwise, no BLAS calls; host has "
+                          f"{os.cpu_count()} cores)",
+                "all_cores": {"value": va, "unit": "amplitudes/s", "cores": ncores,
+                              "sample": f"{na} bitstrings over {ncores} spawned processes (one thread each), "
+                                        f"{dta:.1f} s"}}
+    elif rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_oracle_cfg1_reduction()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _cpu_oracle_cfg1_reduction():
+    """No CPU oracle reaches a random 64-qubit amplitude; the reported baseline
+    is the oracle's CH form on the workload's Clifford twin (same 8 x 8 layout
+    and depth-16 schedule, Clifford single-qubit gates), one thread, on a
+    bounded sample of seed-random bitstrings."""
+    from oracle.stabilizer import stabilizer_amplitudes
+    gl, _ = C.config_circuit(1, 0, clifford=True)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < 10.0 and n < 256:
+        stabilizer_amplitudes(gl, C.random_bitstrings(64, 1, 1000 + n))
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "amplitudes/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} amplitudes of the workload's Clifford twin by the CH form, {dt:.1f} s, one thread; "
+                      f"no CPU oracle reaches a random 64-qubit amplitude"}
 
 
 def main():
@@ -584,6 +779,14 @@ def main():
     ap.add_argument("--cols", type=int, default=8)
     ap.add_argument("--steps-detail", default=None,
                     help="write a JSON table of every program step (shape, kernel, ms per launch, roofline ms)")
+    ap.add_argument("--workload", choices=WORKLOADS, default="iqp_5x8",
+                    help="iqp_5x8: 5 x 8 IQP, 256 bitstrings per request (default); rand2d_8x8_d16: 8 x 8 "
+                         "depth-16 random circuit, one amplitude per request, sliced under 180 GB")
+    ap.add_argument("--compare-forms", action="store_true",
+                    help="rand2d_8x8_d16: also time one amplitude in the FP32 form")
+    ap.add_argument("--serving-requests", type=int, default=1000, help="requests per arrival rate")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the compiler's default kernel per step")
     args = ap.parse_args()
     if args.op_counts:
         print(json.dumps(op_counts()), flush=True)

@@ -135,6 +135,21 @@ const char* tnc_last_error(void);
 int tnc_load_network(const tnc_network_desc* desc, tnc_network_t** out);
 void tnc_free_network(tnc_network_t* net);
 
+/* Same as tnc_load_network, with build options.  TNC_NET_HYPEREDGES: every
+ * gate that is diagonal in the computational basis (CZ, the Z and ZZ phases
+ * of IQP circuits, any exactly diagonal 2x2 or 4x4 matrix) reads its wire
+ * without changing it, D|z> = d(z)|z>, so it becomes a tensor of its diagonal
+ * d on the wire labels (rank 1 or 2), and all diagonal gates between two
+ * non-diagonal gates of a qubit share one wire label: a hyper-edge (copy
+ * tensor) of the Classical Simulation section's network, as the bitstring
+ * batch index is.  The pending non-diagonal single-qubit product of a qubit
+ * becomes a rank-2 tensor of its own before such a label (or the vector
+ * P|0> before the first one); non-diagonal two-qubit gates are split as in
+ * tnc_load_network.  The amplitudes are the same; the plans differ.
+ * TNC_EINVAL for unknown flags or an invalid desc. */
+#define TNC_NET_HYPEREDGES 1
+int tnc_load_network_opts(const tnc_network_desc* desc, int flags, tnc_network_t** out);
+
 /* Fill *opts with defaults (no open qubits, batch 1, no cap, FP32, 32
  * trials, leaf size 8, group log2 6, CUDA graphs on). */
 void tnc_plan_opts_default(tnc_plan_opts* opts);

@@ -31,7 +31,7 @@ extern "C" int tnc_circuit_bounds_eval(const tnc_network_desc* desc, tnc_circuit
   }
   {
     tnc::Network check;  // same validation as tnc_load_network
-    const int rc = tnc::build_network(desc, &check);
+    const int rc = tnc::build_network(desc, &check, 0);
     if (rc != TNC_OK) return rc;
   }
   const double nan = std::numeric_limits<double>::quiet_NaN();

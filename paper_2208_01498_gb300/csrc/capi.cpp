@@ -154,13 +154,21 @@ const char* tnc_status_string(int s) {
 const char* tnc_last_error(void) { return g_err.c_str(); }
 
 int tnc_load_network(const tnc_network_desc* desc, tnc_network_t** out) {
+  return tnc_load_network_opts(desc, 0, out);
+}
+
+int tnc_load_network_opts(const tnc_network_desc* desc, int flags, tnc_network_t** out) {
   if (!out) {
     set_error("tnc_load_network: out is NULL");
     return TNC_EINVAL;
   }
   *out = nullptr;
+  if (flags & ~TNC_NET_HYPEREDGES) {
+    set_error("tnc_load_network_opts: unknown flags 0x%x", flags);
+    return TNC_EINVAL;
+  }
   auto* n = new tnc_network();
-  int rc = build_network(desc, &n->net);
+  int rc = build_network(desc, &n->net, flags);
   if (rc != TNC_OK) {
     delete n;
     return rc;

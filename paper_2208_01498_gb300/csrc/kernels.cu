@@ -283,6 +283,72 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ------------------------------------------------------------------ narrow, tiled
+// The narrow node again (N, K <= 16), for powers of two and a K-major A: one
+// CTA per tile of R = 2^r rows of one batch entry.  The tile's A rows are one
+// contiguous block of R K complex values, loaded with 16-byte coalesced loads
+// into shared memory (rows padded by one element, so that threads of a warp
+// reading different rows hit different banks).  One thread per output
+// element, n fastest.  A scattered output tile is staged in shared memory in
+// the order of its output addresses (each tile bit at the rank of its output
+// position among the tile's) and stored by consecutive threads to increasing
+// addresses, so every run of consecutive output positions that the tile
+// covers is written by consecutive threads; an identity layout is one
+// contiguous block and is stored directly.
+constexpr int kNarrowTile = 1024;  // R * max(K, N)
+
+__global__ void __launch_bounds__(256)
+    cgemm_narrow_tile_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
+                             int64_t M, int N, int K, int r, int nN, int64_t b0,
+                             const __grid_constant__ OutMap om, const __grid_constant__ TileRank tr) {
+  __shared__ __align__(16) float2 As[2 * kNarrowTile];  // R rows of K + 1 elements
+  __shared__ float2 Bs[16 * 16];
+  __shared__ float2 S[kNarrowTile];
+  const int R = 1 << r;
+  const int64_t bz = b0 + blockIdx.y;
+  const int64_t m0 = (int64_t)blockIdx.x << r;
+  const float2* Ab = A + (bz * M + m0) * K;
+  const float2* Bb = B + bz * (int64_t)K * N;
+  for (int e = threadIdx.x; e < K * N; e += blockDim.x) Bs[(e % K) * N + e / K] = Bb[e];  // B stored [N][K]
+  const int kp = K + 1;
+  if (K >= 2) {
+    const float4* A4 = (const float4*)Ab;
+    for (int i = threadIdx.x; i < (R * K) >> 1; i += blockDim.x) {
+      const float4 v = A4[i];
+      const int row = (2 * i) / K, k = (2 * i) % K;
+      As[row * kp + k] = make_float2(v.x, v.y);
+      As[row * kp + k + 1] = make_float2(v.z, v.w);
+    }
+  } else {
+    for (int i = threadIdx.x; i < R; i += blockDim.x) As[i * kp] = Ab[i];
+  }
+  __syncthreads();
+  const int bits = nN + r, total = R << nN;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int m = e >> nN, n = e & (N - 1);
+    const float2* a = As + m * kp;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = 0; k < K; ++k) acc = cmul_add(acc, a[k], Bs[k * N + n]);
+    if (om.ident) {
+      C[(bz * M + m0) * N + e] = acc;
+    } else {
+      uint32_t x = 0;
+      for (int b = 0; b < bits; ++b) x |= ((uint32_t)(e >> b) & 1u) << tr.rank[b];
+      S[tile_swz(x)] = acc;
+    }
+  }
+  if (om.ident) return;
+  __syncthreads();
+  // staging index x holds tile bit b at bit rank[b]; tile bit b is output
+  // bit om.pos[b] (n bits, then the tile's m bits)
+  float2* dst = C + om.row(bz, m0, M, N);
+  for (int x = threadIdx.x; x < total; x += blockDim.x) {
+    uint64_t o = 0;
+    for (int b = 0; b < bits; ++b) o |= (uint64_t)((x >> tr.rank[b]) & 1) << om.pos[b];
+    dst[o] = S[tile_swz((uint32_t)x)];
+  }
+}
+
 // ------------------------------------------------------------------ grouped narrow
 // Many independent narrow nodes in one launch: block -> (problem, batch,
 // row chunk) by binary search over the problems' first blocks.
@@ -340,6 +406,9 @@ __global__ void __launch_bounds__(kGroupThreads)
 // FP64; per-block partials reduced by a second pass.
 constexpr int kDotThreads = 256;
 
+// VEC: both operands K-major ([m][K], [n][K]), K even, 16-byte aligned: each
+// thread takes two consecutive k per 16-byte load of every row.
+template <bool VEC>
 __global__ void __launch_bounds__(kDotThreads)
     cgemm_dot_kernel(const float2* __restrict__ A, const float2* __restrict__ B, double2* __restrict__ part,
                      int M, int N, int64_t K, int transA, int transB, int64_t b0) {
@@ -353,6 +422,38 @@ __global__ void __launch_bounds__(kDotThreads)
   for (int i = 0; i < 16; ++i) acc64[i] = make_double2(0, 0), acc[i] = make_float2(0.f, 0.f);
   int run = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if constexpr (VEC) {
+    const float4* A4 = (const float4*)A;
+    const float4* B4 = (const float4*)B;
+    const int64_t K2 = K >> 1;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < K2; j += stride) {
+      float4 a[4], b[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        if (m < M) a[m] = A4[(int64_t)m * K2 + j];
+#pragma unroll
+      for (int n = 0; n < 4; ++n)
+        if (n < N) b[n] = B4[(int64_t)n * K2 + j];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        if (m >= M) break;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          if (n >= N || m * N + n >= 16) break;
+          float2 t = cmul_add(acc[m * N + n], make_float2(a[m].x, a[m].y), make_float2(b[n].x, b[n].y));
+          acc[m * N + n] = cmul_add(t, make_float2(a[m].z, a[m].w), make_float2(b[n].z, b[n].w));
+        }
+      }
+      if (++run == 16) {
+        run = 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          acc64[i].x += acc[i].x, acc64[i].y += acc[i].y;
+          acc[i] = make_float2(0.f, 0.f);
+        }
+      }
+    }
+  } else
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += stride) {
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -682,6 +783,29 @@ int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp,
       return run_simt<32, 128, 8, 4, 4>(d, A, B, C, (float2*)ws, st);
     case KG_NARROW: {
       if (d.N > 16 || d.K > 16) return (int)cudaErrorInvalidValue;
+      auto lg = [](int64_t v) { int r = 0; while (((int64_t)1 << r) < v) ++r; return ((int64_t)1 << r) == v ? r : -1; };
+      const int lM = lg(d.M), lN = lg(d.N), lK = lg(d.K);
+      if (lM >= 0 && lN >= 0 && lK >= 0 && !d.transA && d.transB && ((uintptr_t)A & 15) == 0 &&
+          (d.c_ident || (d.nN == lN && d.nM == lM))) {
+        int r = 0;
+        const int wide = lK > lN ? lK : lN;
+        while (r < lM && ((1 << (r + 1)) << wide) <= kNarrowTile) ++r;
+        TileRank tr;
+        std::memset(&tr, 0, sizeof(tr));
+        if (!d.c_ident)
+          for (int b = 0; b < lN + r; ++b) {
+            int rk = 0;
+            for (int q = 0; q < lN + r; ++q) rk += d.c_pos[q] < d.c_pos[b];
+            tr.rank[b] = (int8_t)rk;
+          }
+        const OutMap om = out_map(d);
+        for (int64_t b0 = 0; b0 < d.batch; b0 += 65535) {
+          int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
+          dim3 grid((unsigned)(d.M >> r), (unsigned)nb);
+          cgemm_narrow_tile_kernel<<<grid, 256, 0, st>>>(A, B, C, d.M, (int)d.N, (int)d.K, r, lN, b0, om, tr);
+        }
+        return (int)cudaGetLastError();
+      }
       int64_t blocks = (d.M + 255) / 256;
       if (blocks > (int64_t)sm_count() * 16) blocks = (int64_t)sm_count() * 16;
       for (int64_t b0 = 0; b0 < d.batch; b0 += 65535) {
@@ -696,7 +820,11 @@ int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp,
       if (d.M * d.N > 16 || d.M > 4 || d.N > 4) return run_simt<64, 32, 8, 4, 4>(d, A, B, C, (float2*)ws, st);
       double2* part = (double2*)ws;
       const int MN = (int)(d.M * d.N);
-      int64_t nblk = (d.K + kDotThreads * 32 - 1) / (kDotThreads * 32);
+      const bool vec = MN > 1 && !d.transA && d.transB && d.K % 2 == 0 && ((uintptr_t)A & 15) == 0 &&
+                       ((uintptr_t)B & 15) == 0;
+      // vectorised: about 8 k per thread; otherwise about 32
+      const int64_t per_blk = vec ? kDotThreads * 8 : kDotThreads * 32;
+      int64_t nblk = (d.K + per_blk - 1) / per_blk;
       if (nblk > 1024) nblk = 1024;
       if (nblk < 1) nblk = 1;
       if ((uint64_t)d.batch * nblk * MN * 2 > d.scratch_elems) return (int)cudaErrorInvalidValue;
@@ -709,8 +837,12 @@ int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp,
       for (int64_t b0 = 0; b0 < d.batch && !vec11; b0 += 65535) {
         int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
         dim3 grid((unsigned)nblk, (unsigned)nb);
-        cgemm_dot_kernel<<<grid, kDotThreads, 0, st>>>(A, B, part, (int)d.M, (int)d.N, d.K, d.transA, d.transB,
-                                                        b0);
+        if (vec)
+          cgemm_dot_kernel<true><<<grid, kDotThreads, 0, st>>>(A, B, part, (int)d.M, (int)d.N, d.K, d.transA,
+                                                                d.transB, b0);
+        else
+          cgemm_dot_kernel<false><<<grid, kDotThreads, 0, st>>>(A, B, part, (int)d.M, (int)d.N, d.K, d.transA,
+                                                                 d.transB, b0);
       }
       int64_t tot = d.batch * MN;
       dot_finish_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, C, (int)nblk, (int)d.M, (int)d.N,
@@ -753,8 +885,10 @@ int preload_kernels_core() {
       (const void*)cgemm_simt_kernel<64, 32, 8, 4, 4>,
       (const void*)cgemm_simt_kernel<32, 128, 8, 4, 4>,
       (const void*)cgemm_narrow_kernel,
+      (const void*)cgemm_narrow_tile_kernel,
       (const void*)grouped_narrow_kernel,
-      (const void*)cgemm_dot_kernel,
+      (const void*)cgemm_dot_kernel<false>,
+      (const void*)cgemm_dot_kernel<true>,
       (const void*)cgemm_dot11_kernel,
       (const void*)dot_finish_kernel,
       (const void*)accum_kernel,

@@ -92,7 +92,20 @@ static void apply_on_axis(Leaf& L, int label, const cd P[4]) {
   L.data.swap(out);
 }
 
-int build_network(const tnc_network_desc* d, Network* net) {
+static bool is_identity(const std::array<cd, 4>& P) {
+  return P[0] == cd(1) && P[1] == cd(0) && P[2] == cd(0) && P[3] == cd(1);
+}
+
+// A gate matrix (dim x dim, interleaved re/im, row-major) that is diagonal in
+// the computational basis, exactly: D|z> = d(z)|z>.
+static bool is_diagonal(const double* m, int dim) {
+  for (int r = 0; r < dim; ++r)
+    for (int c = 0; c < dim; ++c)
+      if (r != c && (m[2 * (r * dim + c)] != 0.0 || m[2 * (r * dim + c) + 1] != 0.0)) return false;
+  return true;
+}
+
+int build_network(const tnc_network_desc* d, Network* net, int flags) {
   if (!d || d->n_qubits < 1 || d->dim < 1 || d->dim > 3 || d->n_gates < 0 || !d->coords ||
       (d->n_gates > 0 && (!d->arity || !d->qubits || !d->mats))) {
     set_error("tnc_load_network: invalid descriptor");
@@ -161,11 +174,86 @@ int build_network(const tnc_network_desc* d, Network* net) {
   std::vector<std::array<cd, 4>> pend(n, {cd(1), cd(0), cd(0), cd(1)});
   std::vector<int> cur_label(n, -1), cur_holder(n, -1);
   std::vector<int> qlayer(n, 0);  // ASAP layer of the latest 2q gate on each qubit
+  std::vector<int> n_holders;     // per label (hyper-edge form)
+  const bool hyper = (flags & TNC_NET_HYPEREDGES) != 0;
+  auto hold = [&](int label) {
+    if ((int)n_holders.size() <= label) n_holders.resize(label + 1, 0);
+    n_holders[label]++;
+  };
   qoff = moff = 0;
   int g2 = 0;
+  // Hyper-edge form: the pending single-qubit product of qubit q becomes a
+  // tensor of its own, from the current wire label to a fresh one (or the
+  // vector P|0> on a fresh label when the qubit has none yet), so that the
+  // next diagonal gates can share the wire label it leaves.
+  auto flush = [&](int q, int layer) {
+    const std::array<cd, 4>& P = pend[q];
+    if (cur_label[q] >= 0 && is_identity(P)) return;
+    Leaf L;
+    const int nl = new_label(LK_WIRE);
+    L.labels.push_back(nl);
+    if (cur_label[q] >= 0) {
+      L.labels.push_back(cur_label[q]);
+      L.data = {P[0], P[1], P[2], P[3]};  // [w'][w]
+      hold(cur_label[q]);
+    } else {
+      L.data = {P[0], P[2]};  // P |0>
+    }
+    hold(nl);
+    for (int k = 0; k < dim; ++k) L.pos[k] = xq(q, k) + jdir[k] * jit * g2;
+    L.radius = 0.25 * l + eps;
+    L.qubit = q;
+    L.time = g2;
+    L.layer = layer;
+    net->leaves.push_back(std::move(L));
+    cur_label[q] = nl;
+    cur_holder[q] = (int)net->leaves.size() - 1;
+    pend[q] = {cd(1), cd(0), cd(0), cd(1)};
+  };
   for (int g = 0; g < d->n_gates; ++g) {
     int a = d->arity[g];
     const double* m = d->mats + moff;
+    if (hyper && a == 1 && is_diagonal(m, 2) && is_identity(pend[d->qubits[qoff]]) &&
+        cur_label[d->qubits[qoff]] >= 0) {
+      // a diagonal single-qubit gate right on a wire label: one more holder of it
+      const int q = d->qubits[qoff];
+      Leaf L;
+      L.labels = {cur_label[q]};
+      L.data = {cd(m[0], m[1]), cd(m[6], m[7])};
+      hold(cur_label[q]);
+      for (int k = 0; k < dim; ++k) L.pos[k] = xq(q, k) + jdir[k] * jit * g2;
+      L.radius = 0.25 * l + eps;
+      L.qubit = q;
+      L.time = g2;
+      L.layer = qlayer[q];
+      net->leaves.push_back(std::move(L));
+      qoff += a;
+      moff += 8;
+      continue;
+    }
+    if (hyper && a == 2 && is_diagonal(m, 4)) {
+      // a diagonal two-qubit gate: a rank-2 tensor d(z_a, z_b) on the two wire labels
+      const int qa = d->qubits[qoff], qb = d->qubits[qoff + 1];
+      const int layer = std::max(qlayer[qa], qlayer[qb]) + 1;
+      flush(qa, qlayer[qa]);
+      flush(qb, qlayer[qb]);
+      Leaf L;
+      L.labels = {cur_label[qa], cur_label[qb]};
+      for (int r = 0; r < 4; ++r) L.data.push_back(cd(m[2 * (r * 4 + r)], m[2 * (r * 4 + r) + 1]));
+      hold(cur_label[qa]);
+      hold(cur_label[qb]);
+      for (int k = 0; k < dim; ++k) L.pos[k] = 0.5 * (xq(qa, k) + xq(qb, k)) + jdir[k] * jit * g2;
+      L.radius = 0.5 * l + eps;
+      L.qubit = qa;
+      L.time = g2;
+      L.layer = layer;
+      net->leaves.push_back(std::move(L));
+      qlayer[qa] = qlayer[qb] = layer;
+      ++g2;
+      qoff += a;
+      moff += 32;
+      continue;
+    }
     if (a == 1) {
       int q = d->qubits[qoff];
       cd U[4] = {cd(m[0], m[1]), cd(m[2], m[3]), cd(m[4], m[5]), cd(m[6], m[7])};
@@ -241,6 +329,8 @@ int build_network(const tnc_network_desc* d, Network* net) {
       A.time = B.time = g2;
       A.layer = B.layer = std::max(qlayer[qa], qlayer[qb]) + 1;
       qlayer[qa] = qlayer[qb] = A.layer;
+      for (int x : A.labels) hold(x);
+      for (int x : B.labels) hold(x);
       net->leaves.push_back(std::move(A));
       net->leaves.push_back(std::move(B));
       const int ida = (int)net->leaves.size() - 2, idb = ida + 1;
@@ -258,6 +348,10 @@ int build_network(const tnc_network_desc* d, Network* net) {
   net->final_label.assign(n, -1);
   net->final_holder.assign(n, -1);
   for (int q = 0; q < n; ++q) {
+    // hyper-edge form: a wire label shared by several tensors cannot take the
+    // pending product on one holder's axis; it gets a tensor of its own
+    if (hyper && cur_holder[q] >= 0 && !is_identity(pend[q]) && n_holders[cur_label[q]] > 1)
+      flush(q, qlayer[q]);
     if (cur_holder[q] >= 0) {
       Leaf& L = net->leaves[cur_holder[q]];
       cd P[4] = {pend[q][0], pend[q][1], pend[q][2], pend[q][3]};

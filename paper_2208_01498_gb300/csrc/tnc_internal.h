@@ -42,7 +42,7 @@ struct Network {
   int n_gates_2q = 0;
 };
 
-int build_network(const tnc_network_desc* desc, Network* net);
+int build_network(const tnc_network_desc* desc, Network* net, int flags);
 
 // ------------------------------------------------------------------ planning
 // Planning view of the network: leaf label sets after the request-specific

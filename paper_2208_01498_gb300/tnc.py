@@ -23,6 +23,7 @@ TNC_ETIMEOUT = -4
 TNC_EBUSY = -5
 TNC_ESTATE = -6
 TNC_ENOTFOUND = -7
+TNC_NET_HYPEREDGES = 1
 
 FORMS = {"fp32": 0, "3xtf32": 1, "split_bf16": 2}
 EMBEDDINGS = {"auto": 0, "collapsed": 1, "spacetime": 2}
@@ -73,7 +74,7 @@ class PlanReport(C.Structure):
 
 
 EXPORTED = [
-    "tnc_status_string", "tnc_last_error", "tnc_load_network", "tnc_free_network",
+    "tnc_status_string", "tnc_last_error", "tnc_load_network", "tnc_load_network_opts", "tnc_free_network",
     "tnc_plan_opts_default", "tnc_plan", "tnc_free_plan", "tnc_plan_get_report",
     "tnc_plan_export_json", "tnc_plan_upload", "tnc_contract_amplitudes",
     "tnc_contract_amplitudes_dbits", "tnc_contract_partial", "tnc_server_create",
@@ -97,6 +98,7 @@ def _load():
         "tnc_status_string": (C.c_char_p, [i]),
         "tnc_last_error": (C.c_char_p, []),
         "tnc_load_network": (i, [C.POINTER(NetworkDesc), C.POINTER(vp)]),
+        "tnc_load_network_opts": (i, [C.POINTER(NetworkDesc), i, C.POINTER(vp)]),
         "tnc_free_network": (None, [vp]),
         "tnc_plan_opts_default": (None, [C.POINTER(PlanOpts)]),
         "tnc_plan": (i, [vp, C.POINTER(PlanOpts), C.POINTER(vp), C.POINTER(PlanReport)]),
@@ -155,7 +157,7 @@ class Network:
     """``tnc_load_network`` on a gate list (``circuits.GateList``) or on the
     flat arrays (coords, arity, qubits, mats)."""
 
-    def __init__(self, gatelist=None, *, arrays=None):
+    def __init__(self, gatelist=None, *, arrays=None, hyperedges: bool = False):
         if gatelist is not None:
             coords, arity, qubits, mats = gatelist.arrays()
             n = gatelist.n_qubits
@@ -168,7 +170,8 @@ class Network:
                       np.ascontiguousarray(qubits, np.int32), np.ascontiguousarray(mats, np.float64))
         desc = self.desc()
         h = C.c_void_p()
-        _check(lib.tnc_load_network(C.byref(desc), C.byref(h)), "tnc_load_network")
+        _check(lib.tnc_load_network_opts(C.byref(desc), TNC_NET_HYPEREDGES if hyperedges else 0, C.byref(h)),
+               "tnc_load_network_opts")
         self.handle = h
         self.n_qubits = int(n)
 

@@ -256,3 +256,41 @@ def test_cgemm_cuda_cores_split_k_small_grid(tnc, kernel, shape):
             addr |= ((m >> i) & 1) << int(c_pos[6 + i])
         placed = got[addr]
         _assert_close(placed, ref[0], "fp32", f"scattered {kernel}")
+
+
+NARROW_TILED = [  # batch, M, N, K: the tiled narrow kernel (powers of two, K-major A)
+    (256, 8192, 16, 16), (4, 2048, 8, 16), (2, 4096, 4, 4), (1, 1 << 16, 2, 2), (8, 512, 1, 16), (3, 256, 16, 1),
+    (16, 4, 16, 8), (2, 1, 4, 4), (5, 64, 8, 2),
+]
+
+
+@pytest.mark.parametrize("shape", NARROW_TILED, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("scatter", [False, True])
+def test_cgemm_narrow_tiled(tnc, shape, scatter):
+    """Narrow nodes on the tiled kernel (coalesced A tile in shared memory,
+    output staged in address order), identity and shuffled output bit
+    orders, element by element against NumPy."""
+    batch, M, N, K = shape
+    rng = np.random.default_rng(M + 3 * N + 7 * K + batch)
+    A = _crand(batch * M * K, rng)
+    B = _crand(batch * K * N, rng)
+    ref = _ref(A, B, batch, M, N, K, 0, 1)
+    nN, nM = N.bit_length() - 1, M.bit_length() - 1
+    if not scatter or batch & (batch - 1):
+        got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, 0, 1, "fp32",
+                        kernel="narrow")
+        _assert_close(got.cpu().numpy(), ref, "fp32", f"{shape}")
+        return
+    nB = batch.bit_length() - 1
+    c_pos = rng.permutation(nN + nM + nB)
+    got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, 0, 1, "fp32",
+                    kernel="narrow", c_pos=c_pos).reshape(-1).cpu().numpy()
+    b, m, n = np.meshgrid(np.arange(batch), np.arange(M), np.arange(N), indexing="ij")
+    addr = np.zeros(b.shape, np.int64)
+    for i in range(nN):
+        addr |= ((n >> i) & 1) << int(c_pos[i])
+    for i in range(nM):
+        addr |= ((m >> i) & 1) << int(c_pos[nN + i])
+    for i in range(nB):
+        addr |= ((b >> i) & 1) << int(c_pos[nN + nM + i])
+    _assert_close(got[addr], ref, "fp32", f"{shape} scattered")

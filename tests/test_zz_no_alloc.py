@@ -90,8 +90,8 @@ def test_static_workspace_limits(tnc):
     out = torch.empty((1, 1), dtype=torch.complex128, device="cuda")
     assert _call(tnc, p, np.zeros((1, 9), np.uint8), out) == tnc.TNC_ESTATE
     # a plan larger than the static workspace is refused with TNC_ENOMEM
-    big = tnc.Plan(tnc.Network(C.iqp(4, 6, 0)), max_batch=256)
+    big = tnc.Plan(tnc.Network(C.iqp(5, 8, 0)), max_batch=256)
     assert big.ws_bytes > 64 << 20
     out = torch.empty((256, 1), dtype=torch.complex128, device="cuda")
-    assert _call(tnc, big, np.zeros((256, 24), np.uint8), out) == tnc.TNC_ENOMEM
+    assert _call(tnc, big, np.zeros((256, 40), np.uint8), out) == tnc.TNC_ENOMEM
     assert b"static workspace" in tnc.lib.tnc_last_error()
