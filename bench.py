@@ -182,9 +182,10 @@ SERVING_RATES = (0.25, 0.5, 0.75, 0.9, 1.0, 1.2)
 SERVING_BUCKETS = (1, 16, 256)
 
 
-def _serve(tnc, torch, arena, reqs, gaps, n_streams):
+def _serve(tnc, torch, arena, reqs, gaps, n_streams, batching=1):
     """Submit the requests at their Poisson arrival times; latencies and span."""
     srv = tnc.Server(arena, n_streams=n_streams)
+    srv.set_batching(batching)
     tickets = []
     start = time.perf_counter()
     due = start
@@ -202,7 +203,7 @@ def _serve(tnc, torch, arena, reqs, gaps, n_streams):
 
 def serving_measure(tnc, torch, forms=("split_bf16", "fp32"), seed: int = 0, n_req: int = 1000,
                     cost_cap_flops: float = 2.0 ** 50, arena_bytes: int = 64 << 30, n_streams: int = 4,
-                    rates=SERVING_RATES):
+                    rates=SERVING_RATES, batching: int = 16):
     """Poisson-arriving amplitude requests over the mixed pool (2D L x L random
     circuits, L 4..10, depth 8..20, and (2+1)D layered circuits), 1-256
     bitstrings each (log-uniform), served by the continuous-batching loop over
@@ -211,9 +212,11 @@ def serving_measure(tnc, torch, forms=("split_bf16", "fp32"), seed: int = 0, n_r
     instance whose plan exceeds cost_cap_flops real flops (or cannot be
     planned) is listed as excluded with its planned cost.  Per form: the
     single-stream service time of the mix (the capacity), then n_req requests
-    at each rate factor of that capacity, p50/p99 latency and amplitudes/s;
-    and a serial queue (one stream, no overlap) at the same arrivals for
-    rate factors 0.9 and 1.2."""
+    at each rate factor of that capacity, p50/p99 latency and amplitudes/s,
+    with waiting requests admitted together up to `batching` at a time (their
+    nodes grouped across requests); for the first form also without
+    batching (each request its own launches, overlapped on the streams) and a
+    serial queue (one stream, no overlap) at rate factors 0.9 and 1.2."""
     rng = np.random.default_rng(seed + 17)
     pool, excluded = [], []
     for gl in C.serving_pool(seed):
@@ -281,17 +284,20 @@ def serving_measure(tnc, torch, forms=("split_bf16", "fp32"), seed: int = 0, n_r
         srv.close()
         amps = sum(b.shape[0] for _, _, b in reqs)
         fr = {"single_stream_ms_per_request": 1e3 * service, "capacity_requests_per_s": 1.0 / service,
-              "rates": [], "serial_queue": []}
+              "batching": batching, "rates": [], "no_batching": [], "serial_queue": []}
+
+        def point(factor, lat, span):
+            return {"rate_factor": factor, "requests_per_s": factor / service,
+                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "amplitudes_per_s": amps / span}
+
         for factor in rates:
             rate = factor / service
-            lat, span = _serve(tnc, torch, arena, reqs, gaps_unit / rate, n_streams)
-            fr["rates"].append({"rate_factor": factor, "requests_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
-                                "p99_ms": float(np.percentile(lat, 99)), "amplitudes_per_s": amps / span})
-            if factor in (0.9, 1.2):
-                lat1, span1 = _serve(tnc, torch, arena, reqs, gaps_unit / rate, 1)
-                fr["serial_queue"].append({"rate_factor": factor, "p50_ms": float(np.percentile(lat1, 50)),
-                                           "p99_ms": float(np.percentile(lat1, 99)),
-                                           "amplitudes_per_s": amps / span1})
+            fr["rates"].append(point(factor, *_serve(tnc, torch, arena, reqs, gaps_unit / rate, n_streams, batching)))
+            if f == forms[0]:
+                fr["no_batching"].append(point(factor, *_serve(tnc, torch, arena, reqs, gaps_unit / rate, n_streams)))
+                if factor in (0.9, 1.2):
+                    fr["serial_queue"].append(point(factor, *_serve(tnc, torch, arena, reqs, gaps_unit / rate, 1)))
         result["forms"][f] = fr
     del arena
     torch.cuda.empty_cache()
@@ -574,6 +580,35 @@ def run_ours(args):
         if args.workload != "iqp_5x8":
             ws = tnc.alloc_workspace(plan)
 
+    # ---- the same requests on the hyper-edge form of the network (diagonal
+    # gates on shared wire labels): another plan for the same amplitudes
+    hyper_form = None
+    if args.workload == "iqp_5x8" and args.hyperedges:
+        ph = tnc.Plan(tnc.Network(gl, hyperedges=True), form=args.form, seed=1, ssa_trials=64, **popts)
+        wsh = tnc.alloc_workspace(ph)
+        if args.autotune:
+            _tune(ph, wsh, stream, args.tune_cache, f"{wname}:{args.form}:hyper:{rank}")
+        outh = torch.empty_like(out)
+        for w in range(args.warmup):
+            tnc.contract_amplitudes_dbits(ph, d_bits[w], out=outh, ws=wsh, stream=stream)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for k in range(args.steps):
+            tnc.contract_amplitudes_dbits(ph, d_bits[args.warmup + k], out=outh, ws=wsh, stream=stream)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        th = h0.elapsed_time(h1)
+        a, r = last_out.cpu().numpy(), outh.cpu().numpy()
+        floor = 2.0 ** (-gl.n_qubits / 2)
+        hyper_form = {"value": world * args.steps * batch / (th / 1e3), "unit": "amplitudes/s",
+                      "ms_per_step": th / args.steps, "tree_cost_log2": ph.report["tree_cost_log2"],
+                      "real_tflop_per_request": ph.report["real_flops"] / 1e12, "ws_bytes": ph.report["ws_bytes"],
+                      "gpu_launches_per_step": ph.report["n_launches"],
+                      "max_rel_diff_vs_default_network": float(np.max(np.abs(a - r) / np.maximum(np.abs(r), floor)))}
+        del wsh, ph
+        torch.cuda.empty_cache()
+
     # ---- end to end through the host-buffer API
     pinned = torch.from_numpy(bits).pin_memory()
     res = torch.empty((batch, 1), dtype=torch.complex128).pin_memory()
@@ -712,6 +747,7 @@ def run_ours(args):
         "roofline": roof,
         "kernel_breakdown": breakdown,
         "fp32_form": fp32_form,
+        "hyperedge_form": hyper_form,
         "e2e": e2e,
         "clocks": ck,
         "gpu_launches": int(args.steps * rep["n_launches"]),
@@ -787,6 +823,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=1000, help="requests per arrival rate")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the compiler's default kernel per step")
+    ap.add_argument("--no-hyperedges", dest="hyperedges", action="store_false",
+                    help="skip timing the hyper-edge form of the network")
     args = ap.parse_args()
     if args.op_counts:
         print(json.dumps(op_counts()), flush=True)

@@ -370,6 +370,28 @@ int tnc_contract_amplitudes_dbits(tnc_plan_t* plan, const uint8_t* d_bits, int b
 int tnc_contract_amplitudes_static(tnc_plan_t* plan, const uint8_t* bits, int batch, void* d_out,
                                    void* cuda_stream);
 
+/* Several requests, possibly on different circuits, contracted together in
+ * one stream (the batching of small requests; north_star "Batching").  Their
+ * node programs advance in lockstep, in waves (wave w = step w of every
+ * request that has one); in each wave the narrow nodes of all requests run as
+ * one grouped launch and their CUDA-core cGEMM nodes as one grouped launch
+ * per tile shape, each problem with its own operands and output layout; the
+ * tensor-core, split-K and split-K-dot nodes run as launches of their own.
+ * Every node does the same arithmetic as when its request runs alone, so the
+ * results are those of tnc_contract_amplitudes per request.
+ * plans[n]: plans with one serial slice group each (else TNC_EINVAL), made
+ *   resident on the workspace's device by the call if needed; profiling off.
+ * bits[i]: HOST uint8 [batches[i]][n_qubits of plan i]; d_outs[i]: DEVICE
+ *   complex128 [batches[i]][2^n_open of plan i], caller-owned.
+ * d_ws: DEVICE workspace of ws_bytes >= tnc_batch_ws_bytes(n, plans),
+ *   256-byte aligned (descriptor tables, then one workspace per request).
+ * Enqueued on cuda_stream; the bitstrings and descriptor tables are copied
+ * before the call returns. */
+int tnc_contract_batch(int n, tnc_plan_t* const* plans, const uint8_t* const* bits, const int* batches,
+                       void* const* d_outs, void* d_ws, size_t ws_bytes, void* cuda_stream);
+/* Workspace bytes tnc_contract_batch needs for these n plans (0 on a NULL). */
+size_t tnc_batch_ws_bytes(int n, tnc_plan_t* const* plans);
+
 /* Partial sum over the serial slice groups [group_begin, group_end) only
  * (0 <= begin <= end <= n_slice_groups): the slice-sharded form used when
  * several processes each own a range of slices; the partial results add up
@@ -387,6 +409,15 @@ int tnc_contract_partial(tnc_plan_t* plan, const uint8_t* d_bits, int batch, int
  * arena_bytes, 256-byte aligned) stays owned by the caller and must outlive
  * the server. */
 int tnc_server_create(void* d_arena, size_t arena_bytes, int n_streams, tnc_server_t** out);
+/* Batching of admitted requests: with max_requests >= 2, whenever a stream is
+ * free and at least two requests with one serial slice group each wait at the
+ * head of the queue, up to max_requests of them (in arrival order, as many as
+ * fit the arena together, tnc_batch_ws_bytes) are admitted as one batch of
+ * tnc_contract_batch on that stream: their nodes run in grouped launches
+ * across requests, wave by wave.  1 (the default): every request runs its own
+ * launches.  A request's result does not depend on the setting.
+ * TNC_EINVAL outside 1..1024. */
+int tnc_server_set_batching(tnc_server_t* srv, int max_requests);
 /* Submit a request.  bits (HOST, [batch][n_qubits]) are copied before
  * returning.  d_out (DEVICE complex128 [batch][2^n_open]) must stay valid
  * until the request is done.  TNC_EBUSY if the request can never fit the

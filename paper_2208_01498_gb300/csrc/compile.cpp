@@ -158,7 +158,10 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
   add(KG_SIMT_128x64, 0);
   add(KG_SIMT_64x32, 0);
   add(KG_SIMT_32x128, 0);
-  if (g0.N <= 16 && g0.K <= 16) add(KG_NARROW, 0);
+  if (g0.N <= 16 && g0.K <= 16) {
+    add(KG_NARROW, 0);  // tiled (powers of two, K-major A), else one row per thread
+    add(KG_NARROW, 1);  // one row per thread
+  }
   if (g0.M <= 4 && g0.N <= 4 && g0.K >= 512) add(KG_DOT, 0);
   const bool pow2 = !(g0.M & (g0.M - 1)) && !(g0.N & (g0.N - 1)) && !(g0.K & (g0.K - 1));
   if (g0.form != TNC_FP32 && pow2 && g0.M >= 128 && g0.N >= 32 && g0.K >= 32) {

@@ -116,13 +116,14 @@ struct TileRank {
 
 __device__ __forceinline__ uint32_t tile_swz(uint32_t x) { return x ^ ((x >> 4) & 15u); }
 
+// One BM x BN output tile of batch entry bz (tile index `tile`, m-tiles
+// fastest) over the K range of split `split`: the body of the CUDA-core
+// cGEMM, shared by the per-node kernel and the grouped kernel.
 template <int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN),
-                                  (BM * BN >= 8192) ? 1 : ((BM / TM) * (BN / TN) >= 256 ? 3 : 4))
-    cgemm_simt_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
-                      int64_t M, int64_t N, int64_t K, int transA, int transB, int64_t b0, int64_t kchunk,
-                      int64_t part_stride, int staged, const __grid_constant__ OutMap om,
-                      const __grid_constant__ TileRank tr) {
+__device__ __forceinline__ void simt_tile(const float2* __restrict__ A, const float2* __restrict__ B,
+                                          float2* __restrict__ C, int64_t M, int64_t N, int64_t K, int transA,
+                                          int transB, int64_t bz, int64_t tile, int64_t split, int64_t kchunk,
+                                          int64_t part_stride, int staged, const OutMap& om, const TileRank& tr) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
   // rows padded by 16 bytes: the transposing tile stores spread over banks
@@ -130,14 +131,13 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN),
   __shared__ __align__(16) float2 Bs[BK][BN + 2];
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const int64_t bz = b0 + blockIdx.z;
   A += bz * M * K;
   B += bz * K * N;
-  C += (int64_t)blockIdx.y * part_stride;
-  const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
+  C += split * part_stride;
+  const int64_t kbeg = split * kchunk;
   const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
   const int64_t mt = (M + BM - 1) / BM;
-  const int64_t m0 = ((int64_t)blockIdx.x % mt) * BM, n0 = ((int64_t)blockIdx.x / mt) * BN;
+  const int64_t m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
   float2 acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -250,6 +250,49 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN),
   }
 }
 
+template <int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN),
+                                  (BM * BN >= 8192) ? 1 : ((BM / TM) * (BN / TN) >= 256 ? 3 : 4))
+    cgemm_simt_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
+                      int64_t M, int64_t N, int64_t K, int transA, int transB, int64_t b0, int64_t kchunk,
+                      int64_t part_stride, int staged, const __grid_constant__ OutMap om,
+                      const __grid_constant__ TileRank tr) {
+  simt_tile<BM, BN, BK, TM, TN>(A, B, C, M, N, K, transA, transB, b0 + blockIdx.z, blockIdx.x, blockIdx.y, kchunk,
+                                part_stride, staged, om, tr);
+}
+
+// Many CUDA-core cGEMM problems in one launch (nodes of different requests,
+// each with its own operands and output layout): block -> (problem, batch
+// entry, tile) by binary search over the problems' first blocks; the
+// problem's descriptor is read into shared memory once per block.
+template <int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN),
+                                  (BM * BN >= 8192) ? 1 : ((BM / TM) * (BN / TN) >= 256 ? 3 : 4))
+    grouped_simt_kernel(const SimtProblem* __restrict__ probs, int n) {
+  __shared__ SimtProblem p;
+  __shared__ OutMap om;
+  __shared__ TileRank tr;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;
+    const int64_t blk = blockIdx.x;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (probs[mid].first_block <= blk)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    p = probs[lo];
+    om.ident = p.ident, om.nN = p.nN, om.nM = p.nM, om.nB = p.nB;
+    for (int i = 0; i < kMaxRank; ++i) om.pos[i] = p.c_pos[i], tr.rank[i] = p.rank[i];
+  }
+  __syncthreads();
+  const int64_t local = (int64_t)blockIdx.x - p.first_block;
+  const int64_t tiles = ((p.M + BM - 1) / BM) * ((p.N + BN - 1) / BN);
+  simt_tile<BM, BN, BK, TM, TN>((const float2*)p.A, (const float2*)p.B, (float2*)p.C, p.M, p.N, p.K, p.transA,
+                                p.transB, local / tiles, local % tiles, 0, p.K, 0, p.staged, om, tr);
+}
+
 // ------------------------------------------------------------------ narrow
 // one output row per thread; N, K <= 16; B of the batch in shared memory
 __global__ void __launch_bounds__(256)
@@ -288,29 +331,34 @@ __global__ void __launch_bounds__(256)
 // CTA per tile of R = 2^r rows of one batch entry.  The tile's A rows are one
 // contiguous block of R K complex values, loaded with 16-byte coalesced loads
 // into shared memory (rows padded by one element, so that threads of a warp
-// reading different rows hit different banks).  One thread per output
-// element, n fastest.  A scattered output tile is staged in shared memory in
-// the order of its output addresses (each tile bit at the rank of its output
-// position among the tile's) and stored by consecutive threads to increasing
-// addresses, so every run of consecutive output positions that the tile
-// covers is written by consecutive threads; an identity layout is one
-// contiguous block and is stored directly.
-constexpr int kNarrowTile = 1024;  // R * max(K, N)
+// reading different rows hit different banks).  Thread t takes row t mod R
+// and a contiguous share of its N outputs: its A row goes to registers once,
+// B is read as broadcasts.  A scattered output tile is staged in shared
+// memory in the order of its output addresses (each tile bit at the rank of
+// its output position among the tile's; row and column parts from tables)
+// and stored by consecutive threads to increasing addresses (offsets from a
+// table of the high staging bits plus one of the low five), so every run of
+// consecutive output positions that the tile covers is written by
+// consecutive threads; an identity layout is stored directly.
+constexpr int kNarrowTile = 1024;     // R * N outputs and R * K inputs per CTA at most
+constexpr int kNarrowThreads = 256;
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kNarrowThreads)
     cgemm_narrow_tile_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
                              int64_t M, int N, int K, int r, int nN, int64_t b0,
                              const __grid_constant__ OutMap om, const __grid_constant__ TileRank tr) {
-  __shared__ __align__(16) float2 As[2 * kNarrowTile];  // R rows of K + 1 elements
+  __shared__ __align__(16) float2 As[kNarrowTile + kNarrowTile / 2];  // R rows of K + 1 (K >= 2), or R (K = 1)
   __shared__ float2 Bs[16 * 16];
   __shared__ float2 S[kNarrowTile];
+  __shared__ uint16_t rowx[kNarrowTile], colx[16];
+  __shared__ uint64_t hi_off[kNarrowTile / 32], lo_off[32];
   const int R = 1 << r;
   const int64_t bz = b0 + blockIdx.y;
   const int64_t m0 = (int64_t)blockIdx.x << r;
   const float2* Ab = A + (bz * M + m0) * K;
   const float2* Bb = B + bz * (int64_t)K * N;
   for (int e = threadIdx.x; e < K * N; e += blockDim.x) Bs[(e % K) * N + e / K] = Bb[e];  // B stored [N][K]
-  const int kp = K + 1;
+  const int kp = K >= 2 ? K + 1 : 1;
   if (K >= 2) {
     const float4* A4 = (const float4*)Ab;
     for (int i = threadIdx.x; i < (R * K) >> 1; i += blockDim.x) {
@@ -320,33 +368,59 @@ __global__ void __launch_bounds__(256)
       As[row * kp + k + 1] = make_float2(v.z, v.w);
     }
   } else {
-    for (int i = threadIdx.x; i < R; i += blockDim.x) As[i * kp] = Ab[i];
+    for (int i = threadIdx.x; i < R; i += blockDim.x) As[i] = Ab[i];
+  }
+  const int bits = nN + r, total = R << nN;
+  if (!om.ident) {
+    // staging index of (m, n) = rowx[m] | colx[n]: tile bit b (n bits, then m
+    // bits) at bit rank[b]; output offset of staging index x = hi_off[x >> 5]
+    // + lo_off[x & 31] (tile bit b is output bit om.pos[b])
+    for (int m = threadIdx.x; m < R; m += blockDim.x) {
+      uint32_t x = 0;
+      for (int b = 0; b < r; ++b) x |= ((uint32_t)(m >> b) & 1u) << tr.rank[nN + b];
+      rowx[m] = (uint16_t)x;
+    }
+    if (threadIdx.x < N) {
+      uint32_t x = 0;
+      for (int b = 0; b < nN; ++b) x |= ((uint32_t)(threadIdx.x >> b) & 1u) << tr.rank[b];
+      colx[threadIdx.x] = (uint16_t)x;
+    }
+    auto offset_of = [&](uint32_t x) {
+      uint64_t o = 0;
+      for (int b = 0; b < bits; ++b) o |= (uint64_t)((x >> tr.rank[b]) & 1u) << om.pos[b];
+      return o;
+    };
+    for (int h = threadIdx.x; h < (total + 31) / 32; h += blockDim.x) hi_off[h] = offset_of((uint32_t)h << 5);
+    if (threadIdx.x < 32) lo_off[threadIdx.x] = offset_of(threadIdx.x & (total - 1) & 31);
   }
   __syncthreads();
-  const int bits = nN + r, total = R << nN;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int m = e >> nN, n = e & (N - 1);
-    const float2* a = As + m * kp;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int k = 0; k < K; ++k) acc = cmul_add(acc, a[k], Bs[k * N + n]);
-    if (om.ident) {
-      C[(bz * M + m0) * N + e] = acc;
-    } else {
-      uint32_t x = 0;
-      for (int b = 0; b < bits; ++b) x |= ((uint32_t)(e >> b) & 1u) << tr.rank[b];
-      S[tile_swz(x)] = acc;
+  // thread -> (row, share of the columns)
+  const int per_row = blockDim.x / R > 0 ? blockDim.x / R : 1;  // threads per row
+  const int share = (N + per_row - 1) / per_row;
+  for (int t = threadIdx.x; t < R * per_row; t += blockDim.x) {
+    const int m = t % R, n0 = (t / R) * share;
+    if (n0 >= N) continue;
+    float2 a[16];
+    const float2* ar = As + m * kp;
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k < K) a[k] = ar[k];
+    const int n1 = n0 + share < N ? n0 + share : N;
+    for (int n = n0; n < n1; ++n) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (k < K) acc = cmul_add(acc, a[k], Bs[k * N + n]);
+      if (om.ident)
+        C[(bz * M + m0 + m) * N + n] = acc;
+      else
+        S[tile_swz((uint32_t)rowx[m] | colx[n])] = acc;
     }
   }
   if (om.ident) return;
   __syncthreads();
-  // staging index x holds tile bit b at bit rank[b]; tile bit b is output
-  // bit om.pos[b] (n bits, then the tile's m bits)
   float2* dst = C + om.row(bz, m0, M, N);
-  for (int x = threadIdx.x; x < total; x += blockDim.x) {
-    uint64_t o = 0;
-    for (int b = 0; b < bits; ++b) o |= (uint64_t)((x >> tr.rank[b]) & 1) << om.pos[b];
-    dst[o] = S[tile_swz((uint32_t)x)];
-  }
+  for (int x = threadIdx.x; x < total; x += blockDim.x) dst[hi_off[x >> 5] + lo_off[x & 31]] = S[tile_swz((uint32_t)x)];
 }
 
 // ------------------------------------------------------------------ grouped narrow
@@ -373,9 +447,12 @@ __global__ void __launch_bounds__(kGroupThreads)
   const int64_t bz = local / d.blocks_per_batch;
   const int64_t chunk = local % d.blocks_per_batch;
   const int N = d.N, K = d.K;
-  const float2* A = (d.a_buf ? base : ws) + d.a + bz * d.M * K;
-  const float2* B = (d.b_buf ? base : ws) + d.b + bz * (int64_t)K * N;
-  float2* C = ws + d.c;
+  // a problem of another request carries its own buffers
+  const float2* bb = d.base_ptr ? (const float2*)d.base_ptr : base;
+  float2* wb = d.ws_ptr ? (float2*)d.ws_ptr : ws;
+  const float2* A = (d.a_buf ? bb : wb) + d.a + bz * d.M * K;
+  const float2* B = (d.b_buf ? bb : wb) + d.b + bz * (int64_t)K * N;
+  float2* C = wb + d.c;
   for (int e = threadIdx.x; e < K * N; e += blockDim.x) {
     int kk = e / N, nn = e % N;
     Bs[e] = B[(int64_t)nn * K + kk];  // B stored [N][K]
@@ -785,8 +862,9 @@ int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp,
       if (d.N > 16 || d.K > 16) return (int)cudaErrorInvalidValue;
       auto lg = [](int64_t v) { int r = 0; while (((int64_t)1 << r) < v) ++r; return ((int64_t)1 << r) == v ? r : -1; };
       const int lM = lg(d.M), lN = lg(d.N), lK = lg(d.K);
-      if (lM >= 0 && lN >= 0 && lK >= 0 && !d.transA && d.transB && ((uintptr_t)A & 15) == 0 &&
+      if (d.tile != 1 && lM >= 0 && lN >= 0 && lK >= 0 && !d.transA && d.transB && ((uintptr_t)A & 15) == 0 &&
           (d.c_ident || (d.nN == lN && d.nM == lM))) {
+        // R rows: R * max(K, N) <= kNarrowTile, R <= M
         int r = 0;
         const int wide = lK > lN ? lK : lN;
         while (r < lM && ((1 << (r + 1)) << wide) <= kNarrowTile) ++r;
@@ -802,7 +880,8 @@ int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp,
         for (int64_t b0 = 0; b0 < d.batch; b0 += 65535) {
           int64_t nb = d.batch - b0 < 65535 ? d.batch - b0 : 65535;
           dim3 grid((unsigned)(d.M >> r), (unsigned)nb);
-          cgemm_narrow_tile_kernel<<<grid, 256, 0, st>>>(A, B, C, d.M, (int)d.N, (int)d.K, r, lN, b0, om, tr);
+          cgemm_narrow_tile_kernel<<<grid, kNarrowThreads, 0, st>>>(A, B, C, d.M, (int)d.N, (int)d.K, r, lN, b0, om,
+                                                                   tr);
         }
         return (int)cudaGetLastError();
       }
@@ -822,8 +901,8 @@ int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp,
       const int MN = (int)(d.M * d.N);
       const bool vec = MN > 1 && !d.transA && d.transB && d.K % 2 == 0 && ((uintptr_t)A & 15) == 0 &&
                        ((uintptr_t)B & 15) == 0;
-      // vectorised: about 8 k per thread; otherwise about 32
-      const int64_t per_blk = vec ? kDotThreads * 8 : kDotThreads * 32;
+      // about 32 k per thread (the partials of each block are summed in FP64)
+      const int64_t per_blk = kDotThreads * 32;
       int64_t nblk = (d.K + per_blk - 1) / per_blk;
       if (nblk > 1024) nblk = 1024;
       if (nblk < 1) nblk = 1;
@@ -865,6 +944,54 @@ int launch_grouped_narrow(const GroupedDesc* d_descs, int n, int64_t total_block
   return (int)cudaGetLastError();
 }
 
+// tile shapes of the CUDA-core cGEMM by kernel variant
+template <int V>
+struct SimtShape;
+template <>
+struct SimtShape<KG_SIMT_128x64> {
+  static constexpr int BM = 128, BN = 64, BK = 8, TM = 8, TN = 4;
+};
+template <>
+struct SimtShape<KG_SIMT_64x32> {
+  static constexpr int BM = 64, BN = 32, BK = 8, TM = 4, TN = 4;
+};
+template <>
+struct SimtShape<KG_SIMT_32x128> {
+  static constexpr int BM = 32, BN = 128, BK = 8, TM = 4, TN = 4;
+};
+
+template <int V>
+int launch_grouped_simt_v(const SimtProblem* d_probs, int n, int64_t total_blocks, cudaStream_t st) {
+  using S = SimtShape<V>;
+  constexpr int NT = (S::BM / S::TM) * (S::BN / S::TN);
+  const size_t dyn = (size_t)S::BM * S::BN * 8 + (size_t)S::BM * S::BN / 32 * 8 + (size_t)(S::BM + S::BN) * 4;
+  static std::atomic<int> attr_done[kMaxDevices];
+  if (int e = smem_attr_once(attr_done, grouped_simt_kernel<S::BM, S::BN, S::BK, S::TM, S::TN>, (int)dyn)) return e;
+  grouped_simt_kernel<S::BM, S::BN, S::BK, S::TM, S::TN><<<(unsigned)total_blocks, NT, dyn, st>>>(d_probs, n);
+  return (int)cudaGetLastError();
+}
+
+int simt_tile_shape(int kernel, int* bm, int* bn) {
+  switch (kernel) {
+    case KG_SIMT_128x64: *bm = 128, *bn = 64; return 0;
+    case KG_SIMT_64x32: *bm = 64, *bn = 32; return 0;
+    case KG_SIMT_32x128: *bm = 32, *bn = 128; return 0;
+    default: return -1;
+  }
+}
+
+int launch_grouped_simt(const SimtProblem* d_probs, int n, int64_t total_blocks, int kernel, void* stream) {
+  if (n <= 0 || total_blocks <= 0) return 0;
+  if (total_blocks > 0x7fffffff) return (int)cudaErrorInvalidConfiguration;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (kernel) {
+    case KG_SIMT_128x64: return launch_grouped_simt_v<KG_SIMT_128x64>(d_probs, n, total_blocks, st);
+    case KG_SIMT_64x32: return launch_grouped_simt_v<KG_SIMT_64x32>(d_probs, n, total_blocks, st);
+    case KG_SIMT_32x128: return launch_grouped_simt_v<KG_SIMT_32x128>(d_probs, n, total_blocks, st);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
 int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, void* stream) {
   int64_t total = (int64_t)batch << d.n_open;
   unsigned blocks = (unsigned)((total + 255) / 256);
@@ -893,6 +1020,9 @@ int preload_kernels_core() {
       (const void*)dot_finish_kernel,
       (const void*)accum_kernel,
       (const void*)splitk_reduce_kernel,
+      (const void*)grouped_simt_kernel<128, 64, 8, 8, 4>,
+      (const void*)grouped_simt_kernel<64, 32, 8, 4, 4>,
+      (const void*)grouped_simt_kernel<32, 128, 8, 4, 4>,
   };
   cudaFuncAttributes fa;
   for (const void* f : fns) {

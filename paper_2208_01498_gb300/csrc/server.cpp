@@ -6,6 +6,10 @@
 // (first-fit sub-allocation), so requests that arrive while others run start
 // as slots and memory free up, and their kernels overlap on the device.  A
 // finished request (cudaEvent) frees its bytes and stream for the next one.
+// With batching on (tnc_server_set_batching), the waiting requests at the head
+// of the queue are admitted together, up to the set number, as one batch of
+// tnc_contract_batch (their nodes grouped across requests, wave by wave) on
+// one stream; plans with several serial slice groups run alone.
 // Every host wait is bounded; device work is plain kernels with no spin.
 #include <cuda_runtime_api.h>
 
@@ -21,6 +25,9 @@
 namespace tnc {
 int run_request(tnc_plan_t* plan, const uint8_t* host_bits, int batch, void* d_out, void* d_ws,
                 size_t ws_bytes, void* stream);
+int run_batch(int n, tnc_plan_t* const* plans, const uint8_t* const* bits, const int* batches, void* const* d_outs,
+              void* d_ws, size_t ws_bytes, void* stream);
+uint64_t batch_ws_bytes(int n, tnc_plan_t* const* plans);
 }
 
 using namespace tnc;
@@ -40,6 +47,8 @@ struct Request {
   int stream = -1;
   uint64_t arena_off = 0;
   cudaEvent_t done_ev = nullptr;
+  uint64_t group = 0;  // batch id shared by the requests of one batch (0: alone)
+  bool owner = true;   // holds the stream, the arena block and the event
 };
 
 struct Done {
@@ -63,6 +72,8 @@ struct tnc_server {
   std::condition_variable cv_work, cv_done;
   bool stop = false;
   uint64_t next_ticket = 1;
+  int batching = 1;          // requests admitted together at most
+  uint64_t next_group = 1;
   size_t max_queue = 1 << 16;
   std::thread worker;
 
@@ -78,25 +89,85 @@ struct tnc_server {
     return true;
   }
 
+  static bool batchable(const Request& r) { return r.plan->p.rep.n_slice_groups == 1 && !r.plan->p.profiling; }
+
+  // Admit the batchable requests at the head of the queue (at least two, at
+  // most `batching`, as many as fit the arena together) as one batch on
+  // stream s; false if that does not apply.
+  bool admit_batch(int s) {
+    if (batching < 2 || queue.size() < 2) return false;
+    std::vector<tnc_plan_t*> plans;
+    for (size_t i = 0; i < queue.size() && (int)plans.size() < batching && batchable(queue[i]); ++i)
+      plans.push_back(queue[i].plan);
+    uint64_t off = 0;
+    while (plans.size() >= 2 && !alloc(batch_ws_bytes((int)plans.size(), plans.data()), &off)) plans.pop_back();
+    if (plans.size() < 2) return false;
+    const size_t n = plans.size();
+    const uint64_t need = batch_ws_bytes((int)n, plans.data());
+    std::vector<Request> grp;
+    for (size_t i = 0; i < n; ++i) {
+      grp.push_back(std::move(queue.front()));
+      queue.pop_front();
+    }
+    std::vector<const uint8_t*> bits(n);
+    std::vector<int> batches(n);
+    std::vector<void*> outs(n);
+    for (size_t i = 0; i < n; ++i) bits[i] = grp[i].bits.data(), batches[i] = grp[i].batch, outs[i] = grp[i].d_out;
+    const uint64_t gid = next_group++;
+    stream_busy[s] = 1;
+    int rc = run_batch((int)n, plans.data(), bits.data(), batches.data(), outs.data(), arena + off, need, streams[s]);
+    cudaEvent_t ev = nullptr;
+    if (rc == TNC_OK) rc = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess ? TNC_OK : TNC_ECUDA;
+    if (rc == TNC_OK) rc = cudaEventRecord(ev, streams[s]) == cudaSuccess ? TNC_OK : TNC_ECUDA;
+    if (rc != TNC_OK) {
+      if (ev) cudaEventDestroy(ev);
+      const auto now = Clock::now();
+      for (auto& r : grp) done[r.ticket] = {rc, std::chrono::duration<double, std::milli>(now - r.t_submit).count()};
+      used.erase(off);
+      stream_busy[s] = 0;
+      cv_done.notify_all();
+      return true;
+    }
+    for (size_t i = 0; i < n; ++i) {
+      grp[i].stream = s;
+      grp[i].arena_off = off;
+      grp[i].done_ev = ev;
+      grp[i].group = gid;
+      grp[i].owner = i == 0;
+      running.push_back(std::move(grp[i]));
+    }
+    return true;
+  }
+
   void loop() {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
     while (true) {
-      // completions
-      for (size_t i = 0; i < running.size();) {
+      // completions: the owner of each finished launch sequence (a request
+      // alone, or the first request of a batch) frees its resources, every
+      // request of it is done
+      for (size_t i = 0; i < running.size(); ++i) {
         Request& r = running[i];
+        if (!r.owner) continue;
         cudaError_t q = cudaEventQuery(r.done_ev);
-        if (q == cudaErrorNotReady) {
-          ++i;
-          continue;
-        }
-        double ms = std::chrono::duration<double, std::milli>(Clock::now() - r.t_submit).count();
-        done[r.ticket] = {q == cudaSuccess ? TNC_OK : TNC_ECUDA, ms};
+        if (q == cudaErrorNotReady) continue;
+        const int status = q == cudaSuccess ? TNC_OK : TNC_ECUDA;
+        const auto now = Clock::now();
+        const uint64_t grp = r.group, tk = r.ticket;
         used.erase(r.arena_off);
         stream_busy[r.stream] = 0;
         cudaEventDestroy(r.done_ev);
-        running.erase(running.begin() + i);
+        for (size_t j = 0; j < running.size();) {
+          Request& m = running[j];
+          if ((grp && m.group == grp) || (!grp && m.ticket == tk)) {
+            done[m.ticket] = {status, std::chrono::duration<double, std::milli>(now - m.t_submit).count()};
+            running.erase(running.begin() + j);
+          } else {
+            ++j;
+          }
+        }
         cv_done.notify_all();
+        i = (size_t)-1;  // the vector changed: scan again
       }
       // admissions, in arrival order
       while (!queue.empty() && !stop) {
@@ -108,6 +179,7 @@ struct tnc_server {
           }
         if (s < 0) break;
         uint64_t off;
+        if (admit_batch(s)) continue;
         Request& r = queue.front();
         if (!alloc(r.need, &off)) break;
         Request req = std::move(queue.front());
@@ -217,6 +289,16 @@ int tnc_server_submit(tnc_server_t* s, tnc_plan_t* plan, const uint8_t* bits, in
   *ticket = r.ticket;
   s->queue.push_back(std::move(r));
   s->cv_work.notify_one();
+  return TNC_OK;
+}
+
+int tnc_server_set_batching(tnc_server_t* s, int max_requests) {
+  if (!s || max_requests < 1 || max_requests > 1024) {
+    set_error("tnc_server_set_batching: invalid argument");
+    return TNC_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->batching = max_requests;
   return TNC_OK;
 }
 

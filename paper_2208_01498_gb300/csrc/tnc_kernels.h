@@ -67,7 +67,9 @@ struct GemmDesc {
                         // (K <= 256), 10 N = 128, 11 N = 256 with 64-byte rows, 12 N = 64:
                         // persistent from the planes (9-12 also for K = 4..16); 13 N = 256
                         // (K <= 256): A split on chip, B' from its planes; 14, 15 N = 256 split
-                        // on chip for any K (one TMEM slot + running sum; 15: with prefetch)
+                        // on chip for any K (one TMEM slot + running sum; 15: with prefetch).
+                        // Narrow kernel: 0 tiled (powers of two, K-major A; else as 1), 1 one row
+                        // per thread
 };
 
 // One problem of a grouped launch of narrow nodes (N, K <= 16): the same
@@ -81,6 +83,26 @@ struct GroupedDesc {
   int c_ident, nN, nM, nB;
   int blocks_per_batch;
   int8_t c_pos[kMaxRank];
+  int64_t first_block;
+  // buffers of this problem when it belongs to another request than the
+  // launch's (cross-request grouping); NULL: the launch's ws / leaf buffer
+  const void* ws_ptr;
+  const void* base_ptr;
+};
+
+// One problem of a grouped CUDA-core cGEMM launch (grouped_simt_kernel): a
+// node of any request, by absolute pointers, without split-K.
+// first_block: prefix sum of the blocks (tiles x batch) of the earlier problems.
+struct SimtProblem {
+  const void* A;
+  const void* B;
+  void* C;
+  int64_t M, N, K;
+  int transA, transB;
+  int staged;            // full tiles of a scattered output: staged epilogue (rank below)
+  int ident, nN, nM, nB;
+  int8_t c_pos[kMaxRank];
+  int8_t rank[kMaxRank]; // staged epilogue: rank of each tile bit's output position
   int64_t first_block;
 };
 
@@ -116,6 +138,10 @@ int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, voi
 int launch_grouped_narrow(const GroupedDesc* d_descs, int n, int64_t total_blocks, const void* base, void* ws,
                           void* stream);
 int launch_zero(void* ptr, size_t bytes, void* stream);
+// grouped CUDA-core cGEMM over problems of one tile shape (kernel = KG_SIMT_*)
+int launch_grouped_simt(const SimtProblem* d_probs, int n, int64_t total_blocks, int kernel, void* stream);
+// BM x BN tile of a CUDA-core kernel variant (-1 if not one)
+int simt_tile_shape(int kernel, int* bm, int* bn);
 // SM count of the current device (152, a GB300's, when there is none)
 int sm_count();
 int launch_set_counter(uint64_t* d_ctr, uint64_t value, void* stream);

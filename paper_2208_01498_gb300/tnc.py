@@ -83,6 +83,7 @@ EXPORTED = [
     "tnc_contract_amplitudes_static", "tnc_permute", "tnc_cgemm_scratch_bytes", "tnc_cgemm",
     "tnc_ssa_separate", "tnc_centerpoint", "tnc_plan_autotune", "tnc_plan_get_kernels",
     "tnc_plan_set_kernels", "tnc_cgemm_variant", "tnc_selftest_bounded_wait", "tnc_circuit_bounds_eval",
+    "tnc_contract_batch", "tnc_batch_ws_bytes", "tnc_server_set_batching",
 ]
 
 # kernel variants of a contraction step (TNC_KG_* in tnc.h)
@@ -109,6 +110,9 @@ def _load():
         "tnc_contract_amplitudes": (i, [vp, vp, i, vp, vp, sz, vp]),
         "tnc_contract_amplitudes_dbits": (i, [vp, vp, i, vp, vp, sz, vp]),
         "tnc_contract_partial": (i, [vp, vp, i, i, i, vp, vp, sz, vp]),
+        "tnc_contract_batch": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(i), C.POINTER(vp), vp, sz, vp]),
+        "tnc_batch_ws_bytes": (sz, [i, C.POINTER(vp)]),
+        "tnc_server_set_batching": (i, [vp, i]),
         "tnc_server_create": (i, [vp, sz, i, C.POINTER(vp)]),
         "tnc_server_submit": (i, [vp, vp, vp, i, vp, C.POINTER(u64)]),
         "tnc_server_poll": (i, [vp, u64, C.POINTER(i)]),
@@ -375,6 +379,33 @@ def contract_partial(p: Plan, d_bits, group_begin: int, group_end: int, out=None
     return out
 
 
+def batch_ws_bytes(plans) -> int:
+    """``tnc_batch_ws_bytes``: workspace of ``contract_batch`` for these plans."""
+    arr = (C.c_void_p * len(plans))(*[p.handle.value for p in plans])
+    return int(lib.tnc_batch_ws_bytes(len(plans), arr))
+
+
+def contract_batch(plans, bits_list, outs=None, ws=None, stream=None):
+    """``tnc_contract_batch``: several requests (plan, host bitstrings) in one
+    go, their nodes grouped across requests wave by wave.  Returns (or fills)
+    one complex128 CUDA tensor [batch][2^n_open] per request."""
+    import torch
+    n = len(plans)
+    bl = [np.ascontiguousarray(np.atleast_2d(b), dtype=np.uint8) for b in bits_list]
+    if outs is None:
+        outs = [torch.empty((b.shape[0], 1 << p.n_open), dtype=torch.complex128, device="cuda")
+                for p, b in zip(plans, bl)]
+    if ws is None:
+        ws = torch.empty(max(batch_ws_bytes(plans), 256), dtype=torch.uint8, device="cuda")
+    ph = (C.c_void_p * n)(*[p.handle.value for p in plans])
+    bp = (C.c_void_p * n)(*[b.ctypes.data for b in bl])
+    nb = (C.c_int * n)(*[b.shape[0] for b in bl])
+    op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    _check(lib.tnc_contract_batch(n, ph, bp, nb, op, C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)),
+           "tnc_contract_batch")
+    return outs
+
+
 def contract_amplitudes_static(p: Plan, bits, out, stream=None):
     """``tnc_contract_amplitudes_static``: same result as
     :func:`contract_amplitudes` with the library's static 64 MiB workspace;
@@ -453,6 +484,11 @@ class Server:
                "tnc_server_create")
         self.handle = h
         self._keep = {}
+
+    def set_batching(self, max_requests: int):
+        """``tnc_server_set_batching``: admit up to this many waiting requests
+        together, their nodes grouped across requests (1: each alone)."""
+        _check(lib.tnc_server_set_batching(self.handle, int(max_requests)), "tnc_server_set_batching")
 
     def submit(self, plan: Plan, bits, out) -> int:
         bits = np.ascontiguousarray(np.atleast_2d(bits), dtype=np.uint8)

@@ -193,3 +193,10 @@ def test_every_leaf_and_label_is_used_once():
             count[x] = count.get(x, 0) + 1
     assert all(c == 2 for x, c in count.items() if x not in finals)
     assert all(count[x] == 1 for x in finals)
+
+
+def test_batch_workspace_covers_every_request():
+    plans = [tnc.Plan(tnc.Network(C.random_2d(3, 4, 8, s)), max_batch=4) for s in range(3)]
+    need = tnc.batch_ws_bytes(plans)
+    assert need >= sum((p.ws_bytes + 255) // 256 * 256 for p in plans)
+    assert need % 256 == 0

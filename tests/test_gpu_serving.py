@@ -31,7 +31,10 @@ def _pool(tnc):
     return plans
 
 
-def test_alone_and_in_the_mix_agree(tnc):
+@pytest.mark.parametrize("batching", [1, 8])
+def test_alone_and_in_the_mix_agree(tnc, batching):
+    """batching 8: waiting requests are admitted together and their nodes run
+    in grouped launches across requests (tnc_contract_batch)."""
     plans = _pool(tnc)
     rng = np.random.default_rng(0)
     reqs = []
@@ -42,6 +45,7 @@ def test_alone_and_in_the_mix_agree(tnc):
     alone = [tnc.contract_amplitudes(p, bits).cpu().numpy() for gl, p, bits in reqs]
     arena = torch.empty(max(p.ws_bytes for _, p in plans) * 3 + (1 << 20), dtype=torch.uint8, device="cuda")
     srv = tnc.Server(arena, n_streams=4)
+    srv.set_batching(batching)
     outs, tickets = [], []
     for gl, p, bits in reqs:
         out = torch.full((bits.shape[0], 1 << p.n_open), complex(np.nan, np.nan), dtype=torch.complex128,
