@@ -507,7 +507,11 @@ def run_ours(args):
     rep = plan.report
 
     for w in range(args.warmup):
-        tnc.contract_amplitudes_dbits(plan, d_bits[w], out=out, ws=ws, stream=stream)
+        if args.shard_slices and args.workload == "rand2d_8x8_d16" and world > 1:
+            from paper_2208_01498_gb300 import shard as shard_w
+            shard_w.contract_amplitudes_sharded(plan, d_bits[w], out=out, ws=ws, stream=stream)
+        else:
+            tnc.contract_amplitudes_dbits(plan, d_bits[w], out=out, ws=ws, stream=stream)
     torch.cuda.synchronize()
 
     # ---- timed region: device-resident inputs, the library's default launch
@@ -517,10 +521,22 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    # slice sharding: every rank contracts its range of the serial slice
+    # groups of the same request, one FP64 all-reduce of the amplitudes
+    sharded = args.shard_slices and args.workload == "rand2d_8x8_d16"
+    if sharded:
+        from paper_2208_01498_gb300 import shard as shard_mod
+
+    def one_step(k):
+        if sharded:
+            out.copy_(shard_mod.contract_amplitudes_sharded(plan, d_bits[k], out=out, ws=ws, stream=stream))
+        else:
+            tnc.contract_amplitudes_dbits(plan, d_bits[k], out=out, ws=ws, stream=stream)
+
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
-        tnc.contract_amplitudes_dbits(plan, d_bits[args.warmup + k], out=out, ws=ws, stream=stream)
+        one_step(args.warmup + k)
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -541,7 +557,7 @@ def run_ours(args):
         t = torch.tensor([t_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_ms = float(t.item())
-    amps = world * args.steps * batch
+    amps = (1 if sharded else world) * args.steps * batch
     value = amps / (t_ms / 1e3)
 
     last_out = out.clone()
@@ -618,15 +634,21 @@ def run_ours(args):
     n_e2e = args.steps
     t0 = time.perf_counter()
     for k in range(n_e2e):
-        tnc.contract_amplitudes(plan, pinned[args.warmup + k].numpy(), out=out, ws=ws, stream=stream)
-        res.copy_(out, non_blocking=True)
+        if sharded:
+            # host bitstrings in, this rank's slice groups, the FP64 all-reduce, the amplitudes out
+            db = pinned[args.warmup + k].to(dev, non_blocking=True)
+            res.copy_(shard_mod.contract_amplitudes_sharded(plan, db, out=out, ws=ws, stream=stream),
+                      non_blocking=True)
+        else:
+            tnc.contract_amplitudes(plan, pinned[args.warmup + k].numpy(), out=out, ws=ws, stream=stream)
+            res.copy_(out, non_blocking=True)
         stream.synchronize()
     e2e_s = time.perf_counter() - t0
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = {"value": world * n_e2e * batch / e2e_s, "unit": "amplitudes/s",
+    e2e = {"value": (1 if sharded else world) * n_e2e * batch / e2e_s, "unit": "amplitudes/s",
            "h2d_bytes_per_step": int(batch * gl.n_qubits), "d2h_bytes_per_step": int(batch * 16)}
     del ws
     torch.cuda.empty_cache()
@@ -723,7 +745,7 @@ def run_ours(args):
     line = {
         "metric": "amplitudes/s", "value": value, "unit": "amplitudes/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong" if sharded else "weak", "vs_baseline": None,
         "dtype": {"fp32": "c64", "3xtf32": "tf32x3 (fp32 acc)", "split_bf16": "bf16x3 (fp32 acc)"}[args.form],
         "data": "synthetic",
         "config": {"workload": wname, "form": args.form, "bitstrings_per_request": batch,
@@ -737,7 +759,8 @@ def run_ours(args):
                                          for k, v in net.bounds().items()
                                          if k in ("thm2_log2", "thm2_pst_log2", "sidewise_log2", "explicit_log2")},
                    "l2": f"working set {rep['ws_bytes'] / 1e9:.2f} GB per request > 129 MB L2",
-                   "parallelism": f"dp{world} (independent requests)", "autotuned_steps": tuned,
+                   "parallelism": (f"slice groups of one request over {world} ranks, one FP64 all-reduce" if sharded
+                                   else f"dp{world} (independent requests)"), "autotuned_steps": tuned,
                    "timing": "value: CUDA events around the K steps, device-resident bitstrings, CUDA-graph "
                              "replay per slice group; roofline and kernel_breakdown: a second pass with CUDA events "
                              "around every step (eager launches); e2e: host buffers through "
@@ -825,6 +848,9 @@ def main():
                     help="keep the compiler's default kernel per step")
     ap.add_argument("--no-hyperedges", dest="hyperedges", action="store_false",
                     help="skip timing the hyper-edge form of the network")
+    ap.add_argument("--shard-slices", action="store_true",
+                    help="rand2d_8x8_d16 under torchrun: split each request's slice groups over the ranks "
+                         "(strong scaling, one FP64 all-reduce) instead of independent requests per rank")
     args = ap.parse_args()
     if args.op_counts:
         print(json.dumps(op_counts()), flush=True)

@@ -13,8 +13,10 @@
 // Schmidt rank of 3 would be padded with a zero singular value.  The final
 // wire of every qubit is left as a label of kind LK_FINAL; the plan decides
 // whether it stays open or is projected onto the requested bit values.
+#include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
 
 #include "tnc_internal.h"
 
@@ -103,6 +105,88 @@ static bool is_diagonal(const double* m, int dim) {
     for (int c = 0; c < dim; ++c)
       if (r != c && (m[2 * (r * dim + c)] != 0.0 || m[2 * (r * dim + c) + 1] != 0.0)) return false;
   return true;
+}
+
+// Hyper-edge form: diagonal tensors on the same wire labels commute and
+// multiply elementwise, so they are merged on the host in FP64 (fewer
+// tensors, and no long chains of FP32 products of phases on the device):
+// all rank-2 diagonal tensors on one pair of labels become one, and every
+// rank-1 diagonal tensor joins a rank-2 one on its label where there is one
+// (otherwise all rank-1 ones on a label become one).  The merged tensor sits
+// at the mean position and layer of its parts.
+static void merge_diagonals(Network* net) {
+  std::vector<Leaf>& L = net->leaves;
+  std::map<std::pair<int, int>, int> pair_of;  // (x < y) -> merged leaf
+  std::map<int, int> single_of;                  // x -> merged rank-1 leaf
+  std::vector<Leaf> merged;
+  std::vector<int> parts;
+  std::vector<int> keep_index(L.size(), -1);
+  std::vector<Leaf> out;
+  for (size_t i = 0; i < L.size(); ++i) {
+    if (!L[i].diag || L[i].labels.size() != 2) continue;
+    int x = L[i].labels[0], y = L[i].labels[1];
+    std::array<cd, 4> d = {L[i].data[0], L[i].data[1], L[i].data[2], L[i].data[3]};
+    if (x > y) {  // transpose to (min, max) order
+      std::swap(x, y);
+      std::swap(d[1], d[2]);
+    }
+    auto it = pair_of.find({x, y});
+    if (it == pair_of.end()) {
+      Leaf m = L[i];
+      m.labels = {x, y};
+      m.data.assign(d.begin(), d.end());
+      pair_of[{x, y}] = (int)merged.size();
+      merged.push_back(std::move(m));
+      parts.push_back(1);
+    } else {
+      Leaf& m = merged[it->second];
+      for (int k = 0; k < 4; ++k) m.data[k] *= d[k];
+      for (int k = 0; k < 3; ++k) m.pos[k] += L[i].pos[k];
+      m.layer += L[i].layer;
+      parts[it->second]++;
+    }
+  }
+  // rank-1 diagonals: into a rank-2 diagonal on their label, else merged per label
+  std::map<int, int> pair_with;  // label -> a merged rank-2 diagonal holding it
+  for (size_t j = 0; j < merged.size(); ++j)
+    for (int x : merged[j].labels) pair_with.emplace(x, (int)j);
+  for (size_t i = 0; i < L.size(); ++i) {
+    if (!L[i].diag || L[i].labels.size() != 1) continue;
+    const int x = L[i].labels[0];
+    auto pw = pair_with.find(x);
+    if (pw != pair_with.end()) {
+      Leaf& m = merged[pw->second];
+      const bool first = m.labels[0] == x;  // the axis of x: bit 1 (first label) or bit 0
+      for (int k = 0; k < 4; ++k) m.data[k] *= L[i].data[first ? (k >> 1) : (k & 1)];
+      continue;
+    }
+    auto it = single_of.find(x);
+    if (it == single_of.end()) {
+      single_of[x] = (int)merged.size();
+      merged.push_back(L[i]);
+      parts.push_back(1);
+    } else {
+      Leaf& m = merged[it->second];
+      m.data[0] *= L[i].data[0];
+      m.data[1] *= L[i].data[1];
+      for (int k = 0; k < 3; ++k) m.pos[k] += L[i].pos[k];
+      m.layer += L[i].layer;
+      parts[it->second]++;
+    }
+  }
+  for (size_t j = 0; j < merged.size(); ++j) {
+    for (int k = 0; k < 3; ++k) merged[j].pos[k] /= parts[j];
+    merged[j].layer = (int)std::lround((double)merged[j].layer / parts[j]);
+  }
+  for (size_t i = 0; i < L.size(); ++i)
+    if (!L[i].diag) {
+      keep_index[i] = (int)out.size();
+      out.push_back(std::move(L[i]));
+    }
+  for (auto& m : merged) out.push_back(std::move(m));
+  for (int& h : net->final_holder)
+    if (h >= 0) h = keep_index[h];  // final wires are never held by a diagonal tensor alone
+  L.swap(out);
 }
 
 int build_network(const tnc_network_desc* d, Network* net, int flags) {
@@ -220,6 +304,7 @@ int build_network(const tnc_network_desc* d, Network* net, int flags) {
       Leaf L;
       L.labels = {cur_label[q]};
       L.data = {cd(m[0], m[1]), cd(m[6], m[7])};
+      L.diag = true;
       hold(cur_label[q]);
       for (int k = 0; k < dim; ++k) L.pos[k] = xq(q, k) + jdir[k] * jit * g2;
       L.radius = 0.25 * l + eps;
@@ -240,6 +325,7 @@ int build_network(const tnc_network_desc* d, Network* net, int flags) {
       Leaf L;
       L.labels = {cur_label[qa], cur_label[qb]};
       for (int r = 0; r < 4; ++r) L.data.push_back(cd(m[2 * (r * 4 + r)], m[2 * (r * 4 + r) + 1]));
+      L.diag = true;
       hold(cur_label[qa]);
       hold(cur_label[qb]);
       for (int k = 0; k < dim; ++k) L.pos[k] = 0.5 * (xq(qa, k) + xq(qb, k)) + jdir[k] * jit * g2;
@@ -373,6 +459,7 @@ int build_network(const tnc_network_desc* d, Network* net, int flags) {
       net->final_holder[q] = (int)net->leaves.size() - 1;
     }
   }
+  if (hyper) merge_diagonals(net);
   return TNC_OK;
 }
 

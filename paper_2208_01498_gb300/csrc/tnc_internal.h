@@ -29,6 +29,7 @@ struct Leaf {
   int qubit = -1;
   int time = 0;   // index of the 2q gate among the circuit's 2q gates
   int layer = 0;  // ASAP layer: 1 + the latest layer on either of its qubits (0 for a bare wire)
+  bool diag = false;  // hyper-edge form: the diagonal of a diagonal gate on its wire labels
 };
 
 struct Network {
