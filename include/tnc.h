@@ -410,14 +410,18 @@ int tnc_contract_partial(tnc_plan_t* plan, const uint8_t* d_bits, int batch, int
  * the server. */
 int tnc_server_create(void* d_arena, size_t arena_bytes, int n_streams, tnc_server_t** out);
 /* Batching of admitted requests: with max_requests >= 2, whenever a stream is
- * free and at least two requests with one serial slice group each wait at the
- * head of the queue, up to max_requests of them (in arrival order, as many as
- * fit the arena together, tnc_batch_ws_bytes) are admitted as one batch of
- * tnc_contract_batch on that stream: their nodes run in grouped launches
- * across requests, wave by wave.  1 (the default): every request runs its own
- * launches.  A request's result does not depend on the setting.
- * TNC_EINVAL outside 1..1024. */
-int tnc_server_set_batching(tnc_server_t* srv, int max_requests);
+ * free and at least two small requests wait at the head of the queue, up to
+ * max_requests of them (in arrival order, as many as fit the arena together,
+ * tnc_batch_ws_bytes) are admitted as one batch of tnc_contract_batch on that
+ * stream: their nodes run in grouped launches across requests, wave by wave.
+ * Small: one serial slice group, and planned real flops and bytes (report
+ * real_flops, bytes) at most max_request_flops and max_request_bytes (0: no
+ * limit) -- a batch finishes with its slowest request, so large requests run
+ * alone.  max_requests 1 (the default): every request runs its own launches.
+ * A request's result does not depend on the setting.  TNC_EINVAL for
+ * max_requests outside 1..1024 or a negative limit. */
+int tnc_server_set_batching(tnc_server_t* srv, int max_requests, double max_request_flops,
+                            double max_request_bytes);
 /* Submit a request.  bits (HOST, [batch][n_qubits]) are copied before
  * returning.  d_out (DEVICE complex128 [batch][2^n_open]) must stay valid
  * until the request is done.  TNC_EBUSY if the request can never fit the

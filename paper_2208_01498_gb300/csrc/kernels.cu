@@ -326,6 +326,123 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ------------------------------------------------------------------ narrow, unrolled
+// The narrow node with K and N known at compile time (powers of two <= 16), A
+// K-major: one row per thread, its A row read with 16-byte loads and kept in
+// registers as the packed pairs (a.x, a.x) and (-a.y, a.y); B in shared memory
+// as (b.x, b.y, b.y, b.x), read with one 16-byte broadcast per (k, n); every
+// complex multiply-add is two packed FP32 FMAs (__ffma2_rn), which compute per
+// component exactly the two FMAs of cmul_add in its order.  Fully unrolled:
+// no index arithmetic or predicates in the inner loops.
+template <int K, int N>
+__global__ void __launch_bounds__(256)
+    cgemm_narrow_unrolled_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
+                                 int64_t M, int64_t b0, const __grid_constant__ OutMap om) {
+  __shared__ float4 Bp[K * N];
+  __shared__ uint64_t coff[N];
+  const int64_t bz = b0 + blockIdx.y;
+  A += bz * M * K;
+  B += bz * (int64_t)K * N;
+  for (int e = threadIdx.x; e < K * N; e += blockDim.x) {
+    const float2 b = B[e];  // B stored [N][K]: e = n K + k
+    Bp[(e % K) * N + e / K] = make_float4(b.x, b.y, b.y, b.x);
+  }
+  if (threadIdx.x < N) coff[threadIdx.x] = om.col(threadIdx.x);
+  __syncthreads();
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+    float2 ax[K], ay[K];
+    if constexpr (K >= 2) {
+      const float4* row = (const float4*)(A + m * K);
+#pragma unroll
+      for (int k = 0; k < K / 2; ++k) {
+        const float4 v = row[k];
+        ax[2 * k] = make_float2(v.x, v.x);
+        ay[2 * k] = make_float2(-v.y, v.y);
+        ax[2 * k + 1] = make_float2(v.z, v.z);
+        ay[2 * k + 1] = make_float2(-v.w, v.w);
+      }
+    } else {
+      const float2 v = A[m];
+      ax[0] = make_float2(v.x, v.x);
+      ay[0] = make_float2(-v.y, v.y);
+    }
+    const uint64_t roff = om.row(bz, m, M, N);
+    // two columns at a time: two independent FMA chains, B loads bounded
+#pragma unroll 1
+    for (int n = 0; n < N; n += (N >= 2 ? 2 : 1)) {
+      float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float4 b0 = Bp[k * N + n];
+        acc0 = __ffma2_rn(ax[k], make_float2(b0.x, b0.y), acc0);
+        acc0 = __ffma2_rn(ay[k], make_float2(b0.z, b0.w), acc0);
+        if constexpr (N >= 2) {
+          const float4 b1 = Bp[k * N + n + 1];
+          acc1 = __ffma2_rn(ax[k], make_float2(b1.x, b1.y), acc1);
+          acc1 = __ffma2_rn(ay[k], make_float2(b1.z, b1.w), acc1);
+        }
+      }
+      C[roff + coff[n]] = acc0;
+      if constexpr (N >= 2) C[roff + coff[n + 1]] = acc1;
+    }
+  }
+}
+
+template <int K, int N>
+void launch_narrow_unrolled(const float2* A, const float2* B, float2* C, int64_t M, int64_t batch, const OutMap& om,
+                            cudaStream_t st) {
+  int64_t blocks = (M + 255) / 256;
+  if (blocks > (int64_t)sm_count() * 16) blocks = (int64_t)sm_count() * 16;
+  for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
+    const int64_t nb = batch - b0 < 65535 ? batch - b0 : 65535;
+    cgemm_narrow_unrolled_kernel<K, N><<<dim3((unsigned)blocks, (unsigned)nb), 256, 0, st>>>(A, B, C, M, b0, om);
+  }
+}
+
+template <int K>
+bool launch_narrow_unrolled_n(int N, const float2* A, const float2* B, float2* C, int64_t M, int64_t batch,
+                              const OutMap& om, cudaStream_t st) {
+  switch (N) {
+    case 1: launch_narrow_unrolled<K, 1>(A, B, C, M, batch, om, st); return true;
+    case 2: launch_narrow_unrolled<K, 2>(A, B, C, M, batch, om, st); return true;
+    case 4: launch_narrow_unrolled<K, 4>(A, B, C, M, batch, om, st); return true;
+    case 8: launch_narrow_unrolled<K, 8>(A, B, C, M, batch, om, st); return true;
+    case 16: launch_narrow_unrolled<K, 16>(A, B, C, M, batch, om, st); return true;
+    default: return false;
+  }
+}
+
+template <int K>
+void narrow_unrolled_fns_n(const void** out) {
+  out[0] = (const void*)cgemm_narrow_unrolled_kernel<K, 1>;
+  out[1] = (const void*)cgemm_narrow_unrolled_kernel<K, 2>;
+  out[2] = (const void*)cgemm_narrow_unrolled_kernel<K, 4>;
+  out[3] = (const void*)cgemm_narrow_unrolled_kernel<K, 8>;
+  out[4] = (const void*)cgemm_narrow_unrolled_kernel<K, 16>;
+}
+
+// the 25 instances (for preloading)
+void narrow_unrolled_fns(const void** out) {
+  narrow_unrolled_fns_n<1>(out);
+  narrow_unrolled_fns_n<2>(out + 5);
+  narrow_unrolled_fns_n<4>(out + 10);
+  narrow_unrolled_fns_n<8>(out + 15);
+  narrow_unrolled_fns_n<16>(out + 20);
+}
+
+// false if (K, N) has no unrolled instance
+bool launch_narrow_unrolled_kn(int K, int N, const float2* A, const float2* B, float2* C, int64_t M, int64_t batch,
+                               const OutMap& om, cudaStream_t st) {
+  switch (K) {
+    case 1: return launch_narrow_unrolled_n<1>(N, A, B, C, M, batch, om, st);
+    case 2: return launch_narrow_unrolled_n<2>(N, A, B, C, M, batch, om, st);
+    case 4: return launch_narrow_unrolled_n<4>(N, A, B, C, M, batch, om, st);
+    case 8: return launch_narrow_unrolled_n<8>(N, A, B, C, M, batch, om, st);
+    case 16: return launch_narrow_unrolled_n<16>(N, A, B, C, M, batch, om, st);
+    default: return false;
+  }
+}
+
 // ------------------------------------------------------------------ narrow, tiled
 // The narrow node again (N, K <= 16), for powers of two and a K-major A: one
 // CTA per tile of R = 2^r rows of one batch entry.  The tile's A rows are one
@@ -500,9 +617,17 @@ __global__ void __launch_bounds__(kDotThreads)
   int run = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if constexpr (VEC) {
+    // FP32 over the thread's k (16 products; more only when K exceeds the
+    // 1024 blocks of 4096 k), an FP32 tree over the warp's 32 lanes, FP64
+    // over the warps and blocks; accumulators indexed statically (registers)
     const float4* A4 = (const float4*)A;
     const float4* B4 = (const float4*)B;
     const int64_t K2 = K >> 1;
+    float2 c[4][4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int n = 0; n < 4; ++n) c[m][n] = make_float2(0.f, 0.f);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < K2; j += stride) {
       float4 a[4], b[4];
 #pragma unroll
@@ -512,24 +637,35 @@ __global__ void __launch_bounds__(kDotThreads)
       for (int n = 0; n < 4; ++n)
         if (n < N) b[n] = B4[(int64_t)n * K2 + j];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        if (m >= M) break;
+      for (int m = 0; m < 4; ++m)
 #pragma unroll
-        for (int n = 0; n < 4; ++n) {
-          if (n >= N || m * N + n >= 16) break;
-          float2 t = cmul_add(acc[m * N + n], make_float2(a[m].x, a[m].y), make_float2(b[n].x, b[n].y));
-          acc[m * N + n] = cmul_add(t, make_float2(a[m].z, a[m].w), make_float2(b[n].z, b[n].w));
-        }
-      }
-      if (++run == 16) {
-        run = 0;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          acc64[i].x += acc[i].x, acc64[i].y += acc[i].y;
-          acc[i] = make_float2(0.f, 0.f);
-        }
-      }
+        for (int n = 0; n < 4; ++n)
+          if (m < M && n < N) {
+            const float2 t = cmul_add(c[m][n], make_float2(a[m].x, a[m].y), make_float2(b[n].x, b[n].y));
+            c[m][n] = cmul_add(t, make_float2(a[m].z, a[m].w), make_float2(b[n].z, b[n].w));
+          }
     }
+    __shared__ float2 red32[kDotThreads / 32][16];
+    const int lane32 = threadIdx.x & 31, wid32 = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        if (m >= M || n >= N) continue;  // uniform over the block
+        float x = c[m][n].x, y = c[m][n].y;
+        for (int off = 16; off; off >>= 1) {
+          x += __shfl_xor_sync(0xffffffffu, x, off);
+          y += __shfl_xor_sync(0xffffffffu, y, off);
+        }
+        if (lane32 == 0) red32[wid32][m * N + n] = make_float2(x, y);
+      }
+    __syncthreads();
+    if (threadIdx.x < MN) {
+      double2 sum = make_double2(0, 0);
+      for (int w = 0; w < kDotThreads / 32; ++w) sum.x += red32[w][threadIdx.x].x, sum.y += red32[w][threadIdx.x].y;
+      part[(bz * gridDim.x + blockIdx.x) * MN + threadIdx.x] = sum;
+    }
+    return;
   } else
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += stride) {
 #pragma unroll
@@ -862,8 +998,11 @@ int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp,
       if (d.N > 16 || d.K > 16) return (int)cudaErrorInvalidValue;
       auto lg = [](int64_t v) { int r = 0; while (((int64_t)1 << r) < v) ++r; return ((int64_t)1 << r) == v ? r : -1; };
       const int lM = lg(d.M), lN = lg(d.N), lK = lg(d.K);
-      if (d.tile != 1 && lM >= 0 && lN >= 0 && lK >= 0 && !d.transA && d.transB && ((uintptr_t)A & 15) == 0 &&
-          (d.c_ident || (d.nN == lN && d.nM == lM))) {
+      const bool kmajor = !d.transA && d.transB && ((uintptr_t)A & 15) == 0;
+      if (d.tile == 0 && kmajor && lN >= 0 && lK >= 0 &&
+          launch_narrow_unrolled_kn((int)d.K, (int)d.N, A, B, C, d.M, d.batch, out_map(d), st))
+        return (int)cudaGetLastError();
+      if (d.tile == 2 && lM >= 0 && lN >= 0 && lK >= 0 && kmajor && (d.c_ident || (d.nN == lN && d.nM == lM))) {
         // R rows: R * max(K, N) <= kNarrowTile, R <= M
         int r = 0;
         const int wide = lK > lN ? lK : lN;
@@ -901,8 +1040,8 @@ int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp,
       const int MN = (int)(d.M * d.N);
       const bool vec = MN > 1 && !d.transA && d.transB && d.K % 2 == 0 && ((uintptr_t)A & 15) == 0 &&
                        ((uintptr_t)B & 15) == 0;
-      // about 32 k per thread (the partials of each block are summed in FP64)
-      const int64_t per_blk = kDotThreads * 32;
+      // vectorised: 16 k per thread (FP32), else about 32 (FP32 runs of 32 summed in FP64)
+      const int64_t per_blk = vec ? kDotThreads * 16 : kDotThreads * 32;
       int64_t nblk = (d.K + per_blk - 1) / per_blk;
       if (nblk > 1024) nblk = 1024;
       if (nblk < 1) nblk = 1;
@@ -1026,6 +1165,12 @@ int preload_kernels_core() {
   };
   cudaFuncAttributes fa;
   for (const void* f : fns) {
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return (int)e;
+  }
+  const void* unrolled[25];
+  narrow_unrolled_fns(unrolled);
+  for (const void* f : unrolled) {
     cudaError_t e = cudaFuncGetAttributes(&fa, f);
     if (e != cudaSuccess) return (int)e;
   }

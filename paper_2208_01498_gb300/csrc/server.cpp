@@ -73,6 +73,7 @@ struct tnc_server {
   bool stop = false;
   uint64_t next_ticket = 1;
   int batching = 1;          // requests admitted together at most
+  double batch_max_flops = 0, batch_max_bytes = 0;  // plans batched at most this large (0: any)
   uint64_t next_group = 1;
   size_t max_queue = 1 << 16;
   std::thread worker;
@@ -89,7 +90,12 @@ struct tnc_server {
     return true;
   }
 
-  static bool batchable(const Request& r) { return r.plan->p.rep.n_slice_groups == 1 && !r.plan->p.profiling; }
+  // small requests only: their launches, not their work, set their time
+  bool batchable(const Request& r) const {
+    const tnc_plan_report& rp = r.plan->p.rep;
+    return rp.n_slice_groups == 1 && !r.plan->p.profiling && (batch_max_flops <= 0 || rp.real_flops <= batch_max_flops) &&
+           (batch_max_bytes <= 0 || rp.bytes <= batch_max_bytes);
+  }
 
   // Admit the batchable requests at the head of the queue (at least two, at
   // most `batching`, as many as fit the arena together) as one batch on
@@ -292,13 +298,15 @@ int tnc_server_submit(tnc_server_t* s, tnc_plan_t* plan, const uint8_t* bits, in
   return TNC_OK;
 }
 
-int tnc_server_set_batching(tnc_server_t* s, int max_requests) {
-  if (!s || max_requests < 1 || max_requests > 1024) {
+int tnc_server_set_batching(tnc_server_t* s, int max_requests, double max_request_flops, double max_request_bytes) {
+  if (!s || max_requests < 1 || max_requests > 1024 || !(max_request_flops >= 0) || !(max_request_bytes >= 0)) {
     set_error("tnc_server_set_batching: invalid argument");
     return TNC_EINVAL;
   }
   std::lock_guard<std::mutex> lk(s->mu);
   s->batching = max_requests;
+  s->batch_max_flops = max_request_flops;
+  s->batch_max_bytes = max_request_bytes;
   return TNC_OK;
 }
 

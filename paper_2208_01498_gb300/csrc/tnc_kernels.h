@@ -68,8 +68,9 @@ struct GemmDesc {
                         // persistent from the planes (9-12 also for K = 4..16); 13 N = 256
                         // (K <= 256): A split on chip, B' from its planes; 14, 15 N = 256 split
                         // on chip for any K (one TMEM slot + running sum; 15: with prefetch).
-                        // Narrow kernel: 0 tiled (powers of two, K-major A; else as 1), 1 one row
-                        // per thread
+                        // Narrow kernel: 0 unrolled for K, N in {1, 2, 4, 8, 16} with packed FP32
+                        // FMAs (K-major A; else as 1), 1 one row per thread, 2 tiled with the output
+                        // staged in address order (powers of two, K-major A; else as 1)
 };
 
 // One problem of a grouped launch of narrow nodes (N, K <= 16): the same

@@ -112,7 +112,7 @@ def _load():
         "tnc_contract_partial": (i, [vp, vp, i, i, i, vp, vp, sz, vp]),
         "tnc_contract_batch": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(i), C.POINTER(vp), vp, sz, vp]),
         "tnc_batch_ws_bytes": (sz, [i, C.POINTER(vp)]),
-        "tnc_server_set_batching": (i, [vp, i]),
+        "tnc_server_set_batching": (i, [vp, i, C.c_double, C.c_double]),
         "tnc_server_create": (i, [vp, sz, i, C.POINTER(vp)]),
         "tnc_server_submit": (i, [vp, vp, vp, i, vp, C.POINTER(u64)]),
         "tnc_server_poll": (i, [vp, u64, C.POINTER(i)]),
@@ -485,10 +485,13 @@ class Server:
         self.handle = h
         self._keep = {}
 
-    def set_batching(self, max_requests: int):
-        """``tnc_server_set_batching``: admit up to this many waiting requests
-        together, their nodes grouped across requests (1: each alone)."""
-        _check(lib.tnc_server_set_batching(self.handle, int(max_requests)), "tnc_server_set_batching")
+    def set_batching(self, max_requests: int, max_request_flops: float = 2.0 ** 34,
+                     max_request_bytes: float = 2.0 ** 28):
+        """``tnc_server_set_batching``: admit up to this many waiting small
+        requests together (planned real flops and bytes at most the limits;
+        0: no limit), their nodes grouped across requests (1: each alone)."""
+        _check(lib.tnc_server_set_batching(self.handle, int(max_requests), float(max_request_flops),
+                                           float(max_request_bytes)), "tnc_server_set_batching")
 
     def submit(self, plan: Plan, bits, out) -> int:
         bits = np.ascontiguousarray(np.atleast_2d(bits), dtype=np.uint8)

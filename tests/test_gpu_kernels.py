@@ -71,6 +71,8 @@ SHAPES = [  # batch, M, N, K, transA, transB
     (1, 1000, 4, 2, 0, 1), (4, 513, 16, 16, 1, 1), (1, 2, 2, 100000, 0, 1), (2, 8, 8, 20000, 1, 0),
     (1, 4, 4, 3000, 0, 0), (8, 16, 256, 8, 0, 1), (3, 1, 1, 70000, 0, 1), (2, 1, 1, 4099, 1, 0),
     (5, 1, 1, 1 << 16, 0, 1),
+    # split-K dot with 16-byte loads (K-major operands): FP32 per thread and warp, FP64 across
+    (256, 4, 4, 16384, 0, 1), (3, 2, 4, 1000, 0, 1), (2, 4, 1, 1 << 20, 0, 1), (1, 3, 3, 70000, 0, 1),
 ]
 TC_SHAPES = [(4, 128, 64, 64, 0, 1), (2, 256, 128, 512, 0, 1), (1, 512, 256, 4096, 0, 1),
              (2, 128, 32, 64, 0, 1), (1, 1024, 512, 8192, 0, 1),

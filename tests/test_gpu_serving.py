@@ -45,7 +45,7 @@ def test_alone_and_in_the_mix_agree(tnc, batching):
     alone = [tnc.contract_amplitudes(p, bits).cpu().numpy() for gl, p, bits in reqs]
     arena = torch.empty(max(p.ws_bytes for _, p in plans) * 3 + (1 << 20), dtype=torch.uint8, device="cuda")
     srv = tnc.Server(arena, n_streams=4)
-    srv.set_batching(batching)
+    srv.set_batching(batching, 0, 0)  # every request of this pool may join a batch
     outs, tickets = [], []
     for gl, p, bits in reqs:
         out = torch.full((bits.shape[0], 1 << p.n_open), complex(np.nan, np.nan), dtype=torch.complex128,
