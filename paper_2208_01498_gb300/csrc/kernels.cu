@@ -330,22 +330,27 @@ __global__ void __launch_bounds__(256)
 // The narrow node with K and N known at compile time (powers of two <= 16), A
 // K-major: one row per thread, its A row read with 16-byte loads and kept in
 // registers as the packed pairs (a.x, a.x) and (-a.y, a.y); B in shared memory
-// as (b.x, b.y, b.y, b.x), read with one 16-byte broadcast per (k, n); every
-// complex multiply-add is two packed FP32 FMAs (__ffma2_rn), which compute per
-// component exactly the two FMAs of cmul_add in its order.  Fully unrolled:
-// no index arithmetic or predicates in the inner loops.
+// with the values of two columns in each 16-byte word, so that one broadcast
+// per (k, column pair) feeds both columns (the swapped pairs (b.y, b.x) are
+// register moves); every complex multiply-add is two packed FP32 FMAs
+// (__ffma2_rn), which compute per component exactly the two FMAs of cmul_add
+// in its order.  Fully unrolled over K: no index arithmetic or predicates in
+// the inner loop.
 template <int K, int N>
 __global__ void __launch_bounds__(256)
     cgemm_narrow_unrolled_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
                                  int64_t M, int64_t b0, const __grid_constant__ OutMap om) {
-  __shared__ float4 Bp[K * N];
+  constexpr int NP = N >= 2 ? N / 2 : 1;  // column pairs (N = 1: one column, second slot zero)
+  __shared__ float4 Bq[K * NP];           // Bq[k][p] = (b[k][2p], b[k][2p + 1])
   __shared__ uint64_t coff[N];
   const int64_t bz = b0 + blockIdx.y;
   A += bz * M * K;
   B += bz * (int64_t)K * N;
-  for (int e = threadIdx.x; e < K * N; e += blockDim.x) {
-    const float2 b = B[e];  // B stored [N][K]: e = n K + k
-    Bp[(e % K) * N + e / K] = make_float4(b.x, b.y, b.y, b.x);
+  for (int e = threadIdx.x; e < K * NP; e += blockDim.x) {
+    const int k = e / NP, p = e % NP;
+    const float2 x = B[(int64_t)(2 * p) * K + k];  // B stored [N][K]
+    const float2 y = N >= 2 ? B[(int64_t)(2 * p + 1) * K + k] : make_float2(0.f, 0.f);
+    Bq[e] = make_float4(x.x, x.y, y.x, y.y);
   }
   if (threadIdx.x < N) coff[threadIdx.x] = om.col(threadIdx.x);
   __syncthreads();
@@ -367,23 +372,21 @@ __global__ void __launch_bounds__(256)
       ay[0] = make_float2(-v.y, v.y);
     }
     const uint64_t roff = om.row(bz, m, M, N);
-    // two columns at a time: two independent FMA chains, B loads bounded
 #pragma unroll 1
-    for (int n = 0; n < N; n += (N >= 2 ? 2 : 1)) {
+    for (int p = 0; p < NP; ++p) {
       float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const float4 b0 = Bp[k * N + n];
-        acc0 = __ffma2_rn(ax[k], make_float2(b0.x, b0.y), acc0);
-        acc0 = __ffma2_rn(ay[k], make_float2(b0.z, b0.w), acc0);
+        const float4 b = Bq[k * NP + p];
+        acc0 = __ffma2_rn(ax[k], make_float2(b.x, b.y), acc0);
+        acc0 = __ffma2_rn(ay[k], make_float2(b.y, b.x), acc0);
         if constexpr (N >= 2) {
-          const float4 b1 = Bp[k * N + n + 1];
-          acc1 = __ffma2_rn(ax[k], make_float2(b1.x, b1.y), acc1);
-          acc1 = __ffma2_rn(ay[k], make_float2(b1.z, b1.w), acc1);
+          acc1 = __ffma2_rn(ax[k], make_float2(b.z, b.w), acc1);
+          acc1 = __ffma2_rn(ay[k], make_float2(b.w, b.z), acc1);
         }
       }
-      C[roff + coff[n]] = acc0;
-      if constexpr (N >= 2) C[roff + coff[n + 1]] = acc1;
+      C[roff + coff[2 * p]] = acc0;
+      if constexpr (N >= 2) C[roff + coff[2 * p + 1]] = acc1;
     }
   }
 }
