@@ -151,7 +151,8 @@ void tnc_free_network(tnc_network_t* net);
 int tnc_load_network_opts(const tnc_network_desc* desc, int flags, tnc_network_t** out);
 
 /* Fill *opts with defaults (no open qubits, batch 1, no cap, FP32, 32
- * trials, leaf size 8, group log2 6, CUDA graphs on). */
+ * trials, leaf size 8, group log2 6, CUDA graphs on, both embeddings, 4
+ * starts per embedding, refinement windows of 8 subtrees). */
 void tnc_plan_opts_default(tnc_plan_opts* opts);
 
 /* ------------------------------------------------- planner primitives (host)
@@ -195,11 +196,15 @@ typedef struct {
 } tnc_circuit_bounds;
 int tnc_circuit_bounds_eval(const tnc_network_desc* desc, tnc_circuit_bounds* out);
 
-/* Plan the contraction (host only, no GPU needed): separator hierarchy
- * (Thm. 1 proof, Algorithm 1), greedy leaves, index slicing to meet
- * mem_cap_bytes, and the compiled node program.  The plan keeps what it needs
- * from net; net may be freed afterwards.  rep may be NULL.
- * TNC_ENOMEM if no slicing meets the cap; TNC_EINVAL for bad options. */
+/* Plan the contraction (host only, no GPU needed): separator hierarchies
+ * (Thm. 1 proof, Algorithm 1) with greedy leaves over the embeddings and
+ * seeds of opts, each refined if opts->refine_window asks, the cheapest tree
+ * by Eq. 3 (with a cap: the cheapest after slicing among the four cheapest),
+ * index slicing to meet mem_cap_bytes, and the compiled node program.  The
+ * plan keeps what it needs from net; net may be freed afterwards.  rep may be
+ * NULL.  TNC_ENOMEM if no slicing meets the cap, or an intermediate needs
+ * more than the executor's 48 binary indices (set a cap to slice it);
+ * TNC_EINVAL for bad options. */
 int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** out,
              tnc_plan_report* rep);
 void tnc_free_plan(tnc_plan_t* plan);
