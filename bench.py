@@ -203,7 +203,7 @@ def _serve(tnc, torch, arena, reqs, gaps, n_streams, batching=1):
 
 def serving_measure(tnc, torch, forms=("split_bf16", "fp32"), seed: int = 0, n_req: int = 1000,
                     cost_cap_flops: float = 2.0 ** 50, arena_bytes: int = 64 << 30, n_streams: int = 4,
-                    rates=SERVING_RATES, batching: int = 16):
+                    rates=SERVING_RATES, batching: int = 16, n_req_by_form=None):
     """Poisson-arriving amplitude requests over the mixed pool (2D L x L random
     circuits, L 4..10, depth 8..20, and (2+1)D layered circuits), 1-256
     bitstrings each (log-uniform), served by the continuous-batching loop over
@@ -216,7 +216,10 @@ def serving_measure(tnc, torch, forms=("split_bf16", "fp32"), seed: int = 0, n_r
     with waiting requests admitted together up to `batching` at a time (their
     nodes grouped across requests); for the first form also without
     batching (each request its own launches, overlapped on the streams) and a
-    serial queue (one stream, no overlap) at rate factors 0.9 and 1.2."""
+    serial queue (one stream, no overlap) at rate factors 0.9 and 1.2.
+    n_req_by_form: fewer requests per rate for a form (a prefix of the same
+    sequence), e.g. the slower FP32 form."""
+    n_req_by_form = dict(n_req_by_form or {})
     rng = np.random.default_rng(seed + 17)
     pool, excluded = [], []
     for gl in C.serving_pool(seed):
@@ -263,8 +266,9 @@ def serving_measure(tnc, torch, forms=("split_bf16", "fp32"), seed: int = 0, n_r
         for _, plans in pool:
             for p in plans[f].values():
                 p.autotune(arena[:p.ws_bytes // 256 * 256 + 256] if p.ws_bytes < arena_bytes else None, reps=2)
+        n_f = min(n_req, int(n_req_by_form.get(f, n_req)))
         reqs = []
-        for k, nb, bits in seq:
+        for k, nb, bits in seq[:n_f]:
             bucket = next(b for b in SERVING_BUCKETS if b >= nb)
             reqs.append((k, pool[k][1][f][bucket], bits))
         # single-stream service time of the mix (one request at a time through
@@ -277,14 +281,14 @@ def serving_measure(tnc, torch, forms=("split_bf16", "fp32"), seed: int = 0, n_r
                 srv.wait(srv.submit(p, bits, out), 600000)
 
         one_by_one(reqs[:3 * len(pool)])
-        timed = reqs[:min(200, n_req)]
+        timed = reqs[:min(200, n_f)]
         t0 = time.perf_counter()
         one_by_one(timed)
         service = (time.perf_counter() - t0) / len(timed)
         srv.close()
         amps = sum(b.shape[0] for _, _, b in reqs)
         fr = {"single_stream_ms_per_request": 1e3 * service, "capacity_requests_per_s": 1.0 / service,
-              "batching": batching, "rates": [], "no_batching": [], "serial_queue": []}
+              "requests_per_rate": n_f, "batching": batching, "rates": [], "no_batching": [], "serial_queue": []}
 
         def point(factor, lat, span):
             return {"rate_factor": factor, "requests_per_s": factor / service,
@@ -293,15 +297,58 @@ def serving_measure(tnc, torch, forms=("split_bf16", "fp32"), seed: int = 0, n_r
 
         for factor in rates:
             rate = factor / service
-            fr["rates"].append(point(factor, *_serve(tnc, torch, arena, reqs, gaps_unit / rate, n_streams, batching)))
+            gaps = gaps_unit[:n_f] / rate
+            fr["rates"].append(point(factor, *_serve(tnc, torch, arena, reqs, gaps, n_streams, batching)))
             if f == forms[0]:
-                fr["no_batching"].append(point(factor, *_serve(tnc, torch, arena, reqs, gaps_unit / rate, n_streams)))
+                fr["no_batching"].append(point(factor, *_serve(tnc, torch, arena, reqs, gaps, n_streams)))
                 if factor in (0.9, 1.2):
-                    fr["serial_queue"].append(point(factor, *_serve(tnc, torch, arena, reqs, gaps_unit / rate, 1)))
+                    fr["serial_queue"].append(point(factor, *_serve(tnc, torch, arena, reqs, gaps, 1)))
+        if f == forms[0]:
+            fr["small_mix"] = _small_mix(tnc, torch, arena, pool, f, seed, n_f, n_streams, batching)
         result["forms"][f] = fr
     del arena
     torch.cuda.empty_cache()
     return result
+
+
+def _small_mix(tnc, torch, arena, pool, form, seed, n_req, n_streams, batching,
+               max_flops=2.0 ** 34, rates=(0.9, 1.5, 3.0)):
+    """The same serving loop on the pool's small instances only (planned at
+    most max_flops real flops for 256 bitstrings, the size cross-request
+    batching merges): n_req Poisson requests at each rate factor of their
+    single-stream capacity, with and without batching."""
+    small = [i for i, (_, pl) in enumerate(pool) if pl[form][SERVING_BUCKETS[-1]].report["real_flops"] <= max_flops]
+    if not small:
+        return None
+    rng = np.random.default_rng(seed + 29)
+    reqs = []
+    for i in range(n_req):
+        k = small[int(rng.integers(len(small)))]
+        nb = int(round(float(np.exp(rng.uniform(0.0, np.log(256.0))))))
+        bucket = next(b for b in SERVING_BUCKETS if b >= nb)
+        reqs.append((k, pool[k][1][form][bucket], C.random_bitstrings(pool[k][0].n_qubits, nb, 9000 + i)))
+    gaps_unit = rng.exponential(1.0, size=n_req)
+    srv = tnc.Server(arena, n_streams=1)
+    for _, p, bits in reqs[:3 * len(small)] + reqs[:min(200, n_req)]:
+        out = torch.empty((bits.shape[0], 1 << p.n_open), dtype=torch.complex128, device="cuda")
+        srv.wait(srv.submit(p, bits, out), 600000)
+    t0 = time.perf_counter()
+    for _, p, bits in reqs[:min(200, n_req)]:
+        out = torch.empty((bits.shape[0], 1 << p.n_open), dtype=torch.complex128, device="cuda")
+        srv.wait(srv.submit(p, bits, out), 600000)
+    service = (time.perf_counter() - t0) / min(200, n_req)
+    srv.close()
+    amps = sum(b.shape[0] for _, _, b in reqs)
+    res = {"circuits": [pool[i][0].name for i in small], "requests_per_rate": n_req,
+           "single_stream_ms_per_request": 1e3 * service, "batching": batching, "rates": [], "no_batching": []}
+    for factor in rates:
+        gaps = gaps_unit / (factor / service)
+        for key, b in (("rates", batching), ("no_batching", 1)):
+            lat, span = _serve(tnc, torch, arena, reqs, gaps, n_streams, b)
+            res[key].append({"rate_factor": factor, "requests_per_s": factor / service,
+                             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                             "amplitudes_per_s": amps / span})
+    return res
 
 
 def expectation_measure(tnc, torch, form: str, seed: int = 0, reps: int = 20, warmup: int = 3):
@@ -678,7 +725,11 @@ def run_ours(args):
     # the MMA peak of the form's operand type: bf16 measured; tf32 measured in
     # this run (cuBLAS through torch), else the nominal tf32 / bf16 ratio
     tf32_peak = fpk.get("tf32_tflops") or float(peaks["bf16_tflops"]) * 1.1 / 2.25
-    tc_peak = float(peaks["bf16_tflops"]) if args.form == "split_bf16" else tf32_peak
+    # a kernel timed inside a seconds-long step runs under the power cap: the
+    # sustained bf16 figure; the burst figure for the short steps
+    sustained = t_ms > 1000.0 and "bf16_tflops_sustained" in peaks
+    bf16_peak = float(peaks["bf16_tflops_sustained"] if sustained else peaks["bf16_tflops"])
+    tc_peak = bf16_peak if args.form == "split_bf16" else tf32_peak
     hbm = float(peaks["hbm_gbs"])
     fp32_peak = fpk.get("fp32_tflops") or 152 * 128 * 2 * sm_max * 1e6 / 1e12
     # useful peak of the form: three MMA products per useful product on the tensor cores
@@ -703,7 +754,7 @@ def run_ours(args):
     roof["algorithmic_bytes_per_launch"] = by
     roof["algorithmic_flops_per_launch"] = fl
     roof["share_of_device_time"] = float(prof["ms"][di]) / total_ms if total_ms else None
-    roof["peak_source"] = (src + " burst") if (dkind == 4 and args.form == "split_bf16") else \
+    roof["peak_source"] = (src + (" sustained" if sustained else " burst")) if (dkind == 4 and args.form == "split_bf16") else \
         ("measured in this run (cuBLAS tf32)" if dkind == 4 else
          ("measured in this run (cuBLAS fp32)" if dkind in (0, 1, 3, 5) else src))
     # request-level roofline: sum over the steps of max(flops / form peak,
@@ -766,7 +817,9 @@ def run_ours(args):
                              "around every step (eager launches); e2e: host buffers through "
                              "tnc_contract_amplitudes, wall clock"},
         "effective_tflops": world * args.steps * rep["real_flops"] / (t_ms / 1e3) / 1e12,
-        "measured_peaks": dict(fpk, hbm_gbs=hbm, bf16_tflops=float(peaks["bf16_tflops"]), source=src),
+        "measured_peaks": dict(fpk, hbm_gbs=hbm, bf16_tflops=float(peaks["bf16_tflops"]),
+                               bf16_tflops_sustained=float(peaks.get("bf16_tflops_sustained", 0.0)) or None,
+                               source=src),
         "roofline": roof,
         "kernel_breakdown": breakdown,
         "fp32_form": fp32_form,
@@ -779,7 +832,9 @@ def run_ours(args):
         if rank == 0 and not args.no_serving:
             forms = tuple(dict.fromkeys((args.form, "fp32")))
             line["serving"] = serving_measure(tnc, torch, forms=forms, seed=args.seed,
-                                              n_req=args.serving_requests)
+                                              n_req=max(args.serving_requests, args.serving_requests_fp32),
+                                              n_req_by_form={args.form: args.serving_requests,
+                                                             "fp32": args.serving_requests_fp32})
         if rank == 0 and not args.no_expectation:
             line["expectation"] = expectation_measure(tnc, torch, args.form, args.seed)
         if rank == 0 and not args.no_cpu_baseline:
@@ -844,6 +899,8 @@ def main():
     ap.add_argument("--compare-forms", action="store_true",
                     help="rand2d_8x8_d16: also time one amplitude in the FP32 form")
     ap.add_argument("--serving-requests", type=int, default=1000, help="requests per arrival rate")
+    ap.add_argument("--serving-requests-fp32", type=int, default=250,
+                    help="requests per arrival rate in the FP32 form (5.5x slower; 1000 takes three minutes)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the compiler's default kernel per step")
     ap.add_argument("--no-hyperedges", dest="hyperedges", action="store_false",
