@@ -162,6 +162,9 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
     add(KG_NARROW, 0);  // unrolled for K, N in {1, 2, 4, 8, 16} (K-major A), else one row per thread
     add(KG_NARROW, 1);  // one row per thread
     add(KG_NARROW, 2);  // tiled, output staged in address order (powers of two, K-major A)
+    if (!g0.transA && g0.transB && (g0.K == 8 || g0.K == 16) && g0.N >= 2 && !(g0.N & (g0.N - 1)) &&
+        g0.M >= 256 && g0.M % 256 == 0)
+      add(KG_NARROW, 3);  // A tiles staged in shared memory by TMA
   }
   if (g0.M <= 4 && g0.N <= 4 && g0.K >= 512) add(KG_DOT, 0);
   const bool pow2 = !(g0.M & (g0.M - 1)) && !(g0.N & (g0.N - 1)) && !(g0.K & (g0.K - 1));

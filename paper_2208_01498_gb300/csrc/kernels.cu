@@ -329,19 +329,20 @@ __global__ void __launch_bounds__(256)
 // ------------------------------------------------------------------ narrow, unrolled
 // The narrow node with K and N known at compile time (powers of two <= 16), A
 // K-major: one row per thread, its A row read with 16-byte loads and kept in
-// registers as the packed pairs (a.x, a.x) and (-a.y, a.y); B in shared memory
-// with the values of two columns in each 16-byte word, so that one broadcast
-// per (k, column pair) feeds both columns (the swapped pairs (b.y, b.x) are
-// register moves); every complex multiply-add is two packed FP32 FMAs
-// (__ffma2_rn), which compute per component exactly the two FMAs of cmul_add
+// registers as the packed pairs (a.x, a.x), (a.y, a.y) and (-a.y, -a.y); B in
+// shared memory with two columns in each 16-byte word as (b0.x, b1.x, b0.y,
+// b1.y), so that one broadcast per (k, column pair) feeds both columns and the
+// packed FP32 FMAs (__ffma2_rn) take their pairs straight from the loaded
+// word: the real parts of the two columns in one register pair, the imaginary
+// parts in another.  Per component these are exactly the two FMAs of cmul_add
 // in its order.  Fully unrolled over K: no index arithmetic or predicates in
-// the inner loop.
+// the inner loop.  (N = 1: one column, the second slot of each pair zero.)
 template <int K, int N>
 __global__ void __launch_bounds__(256)
     cgemm_narrow_unrolled_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
                                  int64_t M, int64_t b0, const __grid_constant__ OutMap om) {
-  constexpr int NP = N >= 2 ? N / 2 : 1;  // column pairs (N = 1: one column, second slot zero)
-  __shared__ float4 Bq[K * NP];           // Bq[k][p] = (b[k][2p], b[k][2p + 1])
+  constexpr int NP = N >= 2 ? N / 2 : 1;  // column pairs
+  __shared__ float4 Bq[K * NP];           // Bq[k][p] = (b[2p][k].x, b[2p+1][k].x, b[2p][k].y, b[2p+1][k].y)
   __shared__ uint64_t coff[N];
   const int64_t bz = b0 + blockIdx.y;
   A += bz * M * K;
@@ -350,43 +351,45 @@ __global__ void __launch_bounds__(256)
     const int k = e / NP, p = e % NP;
     const float2 x = B[(int64_t)(2 * p) * K + k];  // B stored [N][K]
     const float2 y = N >= 2 ? B[(int64_t)(2 * p + 1) * K + k] : make_float2(0.f, 0.f);
-    Bq[e] = make_float4(x.x, x.y, y.x, y.y);
+    Bq[e] = make_float4(x.x, y.x, x.y, y.y);
   }
   if (threadIdx.x < N) coff[threadIdx.x] = om.col(threadIdx.x);
   __syncthreads();
   for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
-    float2 ax[K], ay[K];
+    float2 ax[K], ay[K], an[K];
     if constexpr (K >= 2) {
       const float4* row = (const float4*)(A + m * K);
 #pragma unroll
       for (int k = 0; k < K / 2; ++k) {
         const float4 v = row[k];
         ax[2 * k] = make_float2(v.x, v.x);
-        ay[2 * k] = make_float2(-v.y, v.y);
+        ay[2 * k] = make_float2(v.y, v.y);
+        an[2 * k] = make_float2(-v.y, -v.y);
         ax[2 * k + 1] = make_float2(v.z, v.z);
-        ay[2 * k + 1] = make_float2(-v.w, v.w);
+        ay[2 * k + 1] = make_float2(v.w, v.w);
+        an[2 * k + 1] = make_float2(-v.w, -v.w);
       }
     } else {
       const float2 v = A[m];
       ax[0] = make_float2(v.x, v.x);
-      ay[0] = make_float2(-v.y, v.y);
+      ay[0] = make_float2(v.y, v.y);
+      an[0] = make_float2(-v.y, -v.y);
     }
     const uint64_t roff = om.row(bz, m, M, N);
 #pragma unroll 1
     for (int p = 0; p < NP; ++p) {
-      float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+      float2 re = make_float2(0.f, 0.f), im = make_float2(0.f, 0.f);  // columns 2p, 2p + 1
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const float4 b = Bq[k * NP + p];
-        acc0 = __ffma2_rn(ax[k], make_float2(b.x, b.y), acc0);
-        acc0 = __ffma2_rn(ay[k], make_float2(b.y, b.x), acc0);
-        if constexpr (N >= 2) {
-          acc1 = __ffma2_rn(ax[k], make_float2(b.z, b.w), acc1);
-          acc1 = __ffma2_rn(ay[k], make_float2(b.w, b.z), acc1);
-        }
+        const float2 bx = make_float2(b.x, b.y), by = make_float2(b.z, b.w);
+        re = __ffma2_rn(ax[k], bx, re);
+        re = __ffma2_rn(an[k], by, re);
+        im = __ffma2_rn(ax[k], by, im);
+        im = __ffma2_rn(ay[k], bx, im);
       }
-      C[roff + coff[2 * p]] = acc0;
-      if constexpr (N >= 2) C[roff + coff[2 * p + 1]] = acc1;
+      C[roff + coff[2 * p]] = make_float2(re.x, im.x);
+      if constexpr (N >= 2) C[roff + coff[2 * p + 1]] = make_float2(re.y, im.y);
     }
   }
 }
@@ -976,6 +979,7 @@ int launch_permute_ptr(const PermDesc& d, const void* in, void* out, void* strea
 }
 
 int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* C, void* scratch, cudaStream_t st);
+int launch_narrow_tma(const GemmDesc& d, const float2* A, const float2* B, float2* C, cudaStream_t st);
 
 int launch_gemm(const GemmDesc& d, const void* base, void* ws, void* stream) {
   const float2* A = (const float2*)(d.a_buf ? base : ws) + d.a;
@@ -1002,7 +1006,11 @@ int launch_gemm_ptr(const GemmDesc& d, const void* Ap, const void* Bp, void* Cp,
       auto lg = [](int64_t v) { int r = 0; while (((int64_t)1 << r) < v) ++r; return ((int64_t)1 << r) == v ? r : -1; };
       const int lM = lg(d.M), lN = lg(d.N), lK = lg(d.K);
       const bool kmajor = !d.transA && d.transB && ((uintptr_t)A & 15) == 0;
-      if (d.tile == 0 && kmajor && lN >= 0 && lK >= 0 &&
+      if (d.tile == 3) {
+        const int r = launch_narrow_tma(d, A, B, C, st);
+        if (r >= 0) return r;  // else (shape not eligible) as tile 0
+      }
+      if ((d.tile == 0 || d.tile == 3) && kmajor && lN >= 0 && lK >= 0 &&
           launch_narrow_unrolled_kn((int)d.K, (int)d.N, A, B, C, d.M, d.batch, out_map(d), st))
         return (int)cudaGetLastError();
       if (d.tile == 2 && lM >= 0 && lN >= 0 && lK >= 0 && kmajor && (d.c_ident || (d.nN == lN && d.nM == lM))) {

@@ -1397,6 +1397,175 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   return run_tc<false, 64, 4>(d, A, B, (float*)C, scratch, st);
 }
 
+// ------------------------------------------------------------------ narrow nodes staged by TMA
+// The narrow node (N <= 16 complex columns, K = 8 or 16, A K-major [b][M][K],
+// B [b][N][K], FP32 on the CUDA cores) with its A rows brought into shared
+// memory by TMA: one 256-row tile (64 or 128 bytes a row) per box, swizzled
+// (64- or 128-byte pattern) so that each thread's 16-byte reads of its own row
+// are free of bank conflicts, in a ring of stages refilled as soon as every
+// thread holds its row.  The loads of a warp then move whole contiguous tiles
+// instead of one scattered 16-byte piece of 32 rows each, which set the pace
+// of the kernel that reads its rows from global memory.  One thread a row; B
+// in shared memory with two columns per 16-byte word as (b0.x, b1.x, b0.y,
+// b1.y), so the packed FP32 FMAs take both column pairs straight from the
+// loaded word: per component they are exactly the FMAs of cmul_add in its
+// order (bit-identical to the other CUDA-core kernels).  Each CTA takes a
+// contiguous range of tiles (B reloaded when the batch changes); every wait is
+// bounded (a timeout sets tc_error_flag, all threads leave together after
+// thread 0 has waited, bounded, for the copies still in flight).
+constexpr int kNtRows = 256;  // rows per tile = threads per CTA
+
+template <int K>
+struct NtCfg {
+  static constexpr int kRowBytes = K * 8;  // 64 or 128
+  static constexpr int kStages = K == 16 ? 3 : 4;
+  static constexpr uint32_t kTileBytes = kNtRows * kRowBytes;
+  static constexpr int kSmem = kStages * (int)kTileBytes + 1024;  // + slack to align the swizzle atoms
+  static constexpr int kCtasPerSm = K == 16 ? 2 : 3;               // by shared memory (97 / 65 KB a CTA)
+};
+
+template <int K>
+__device__ __forceinline__ int nt_chunk(int row, int c) {
+  return K == 16 ? (c ^ (row & 7)) : (c ^ ((row >> 1) & 3));
+}
+
+template <int K, int N>
+__global__ void __launch_bounds__(kNtRows, 2)
+    cgemm_narrow_tma_kernel(const __grid_constant__ CUtensorMap mA, const float2* __restrict__ B,
+                            float2* __restrict__ C, int64_t M, int64_t n_tiles, const __grid_constant__ OutMap om) {
+  static_assert(K == 8 || K == 16, "K");
+  static_assert(N >= 2 && N <= 16, "N");
+  using Cfg = NtCfg<K>;
+  constexpr int NP = N / 2;
+  constexpr int S = Cfg::kStages;
+  extern __shared__ uint8_t nt_dyn[];
+  __shared__ float4 Bq[K * NP];  // Bq[k][p] = (b[2p][k].x, b[2p+1][k].x, b[2p][k].y, b[2p+1][k].y)
+  __shared__ uint64_t coff[N];
+  __shared__ __align__(8) uint64_t full[S];
+  uint8_t* tiles = nt_dyn + ((1024u - (smem_u32(nt_dyn) & 1023u)) & 1023u);
+  const int tid = threadIdx.x;
+  const int64_t tiles_m = M / kNtRows;
+  const int64_t per = n_tiles / gridDim.x, extra = n_tiles % gridDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * per + ((int64_t)blockIdx.x < extra ? blockIdx.x : extra);
+  const int64_t nt = per + ((int64_t)blockIdx.x < extra ? 1 : 0);
+  if (tid < N) coff[tid] = om.col(tid);
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int j = 0; j < S && j < nt; ++j) {
+      const int64_t t = t0 + j;
+      mbar_expect_tx(&full[j], Cfg::kTileBytes);
+      tma_load_3d(tiles + j * Cfg::kTileBytes, &mA, &full[j], 0, (int)((t % tiles_m) * kNtRows), (int)(t / tiles_m));
+    }
+  }
+  int64_t cur_b = -1;
+  int64_t failed_at = -1;
+  for (int64_t j = 0; j < nt; ++j) {
+    const int64_t t = t0 + j;
+    const int64_t bz = t / tiles_m;
+    if (bz != cur_b) {  // the same for every thread of the CTA
+      __syncthreads();  // (also orders the barrier set-up before the first waits)
+      const float2* Bb = B + bz * (int64_t)K * N;
+      for (int e = tid; e < K * NP; e += kNtRows) {
+        const int k = e / NP, p = e % NP;
+        const float2 x = Bb[(int64_t)(2 * p) * K + k];
+        const float2 y = Bb[(int64_t)(2 * p + 1) * K + k];
+        Bq[e] = make_float4(x.x, y.x, x.y, y.y);
+      }
+      __syncthreads();
+      cur_b = bz;
+    }
+    const int s = (int)(j % S);
+    const bool ok = mbar_wait(&full[s], (uint32_t)((j / S) & 1));
+    float2 ax[K], ay[K], an[K];  // (a.x, a.x), (a.y, a.y), (-a.y, -a.y)
+    if (ok) {
+      const uint8_t* rowp = tiles + s * Cfg::kTileBytes + tid * Cfg::kRowBytes;
+#pragma unroll
+      for (int c = 0; c < K / 2; ++c) {
+        const float4 v = *(const float4*)(rowp + (nt_chunk<K>(tid, c) << 4));
+        ax[2 * c] = make_float2(v.x, v.x);
+        ay[2 * c] = make_float2(v.y, v.y);
+        an[2 * c] = make_float2(-v.y, -v.y);
+        ax[2 * c + 1] = make_float2(v.z, v.z);
+        ay[2 * c + 1] = make_float2(v.w, v.w);
+        an[2 * c + 1] = make_float2(-v.w, -v.w);
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      failed_at = j;
+      break;
+    }
+    // every thread holds its row: refill the stage
+    if (tid == 0 && j + S < nt) {
+      const int64_t tn = t + S;
+      mbar_expect_tx(&full[s], Cfg::kTileBytes);
+      tma_load_3d(tiles + s * Cfg::kTileBytes, &mA, &full[s], 0, (int)((tn % tiles_m) * kNtRows), (int)(tn / tiles_m));
+    }
+    const int64_t m = (t % tiles_m) * kNtRows + tid;
+    const uint64_t roff = om.row(bz, m, M, N);
+#pragma unroll 1
+    for (int p = 0; p < NP; ++p) {
+      float2 re = make_float2(0.f, 0.f), im = make_float2(0.f, 0.f);  // columns 2p, 2p + 1
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float4 b = Bq[k * NP + p];
+        const float2 bx = make_float2(b.x, b.y), by = make_float2(b.z, b.w);
+        re = __ffma2_rn(ax[k], bx, re);
+        re = __ffma2_rn(an[k], by, re);
+        im = __ffma2_rn(ax[k], by, im);
+        im = __ffma2_rn(ay[k], bx, im);
+      }
+      C[roff + coff[2 * p]] = make_float2(re.x, im.x);
+      C[roff + coff[2 * p + 1]] = make_float2(re.y, im.y);
+    }
+  }
+  if (failed_at >= 0 && tid == 0) {
+    atomicExch(&tc_error_flag, 9);
+    // tiles failed_at .. failed_at + S - 1 were issued and not consumed
+    for (int64_t j = failed_at; j < failed_at + S && j < nt; ++j)
+      mbar_wait(&full[j % S], (uint32_t)((j / S) & 1));
+  }
+}
+
+// The TMA-staged narrow kernel for this node, or kNtNotEligible when its
+// shape or layout does not fit (A K-major and 16-byte aligned, B [b][N][K],
+// K in {8, 16}, N in {2, 4, 8, 16}, M a multiple of 256).
+constexpr int kNtNotEligible = -1;
+
+template <int K, int N>
+int launch_narrow_tma_kn(const GemmDesc& d, const float2* A, const float2* B, float2* C, cudaStream_t st) {
+  using Cfg = NtCfg<K>;
+  static std::atomic<int> attr_done[kMaxDevices];
+  if (int e = smem_attr_once(attr_done, cgemm_narrow_tma_kernel<K, N>, Cfg::kSmem)) return e;
+  CUtensorMap m;
+  if (int e = make_map(&m, (void*)A, true, 2 * K, d.M, d.batch, kNtRows, Cfg::kRowBytes)) return e;
+  const int64_t n_tiles = d.batch * (d.M / kNtRows);
+  int64_t grid = (int64_t)sm_count() * Cfg::kCtasPerSm;
+  if (grid > n_tiles) grid = n_tiles;
+  cgemm_narrow_tma_kernel<K, N><<<(unsigned)grid, kNtRows, Cfg::kSmem, st>>>(m, B, C, d.M, n_tiles, out_map(d));
+  return (int)cudaGetLastError();
+}
+
+template <int K>
+int launch_narrow_tma_k(const GemmDesc& d, const float2* A, const float2* B, float2* C, cudaStream_t st) {
+  switch (d.N) {
+    case 2: return launch_narrow_tma_kn<K, 2>(d, A, B, C, st);
+    case 4: return launch_narrow_tma_kn<K, 4>(d, A, B, C, st);
+    case 8: return launch_narrow_tma_kn<K, 8>(d, A, B, C, st);
+    case 16: return launch_narrow_tma_kn<K, 16>(d, A, B, C, st);
+    default: return kNtNotEligible;
+  }
+}
+
+int launch_narrow_tma(const GemmDesc& d, const float2* A, const float2* B, float2* C, cudaStream_t st) {
+  if (d.transA || !d.transB || ((uintptr_t)A & 15) || d.M < kNtRows || d.M % kNtRows || d.batch < 1 ||
+      d.M > ((int64_t)1 << 31) || d.batch > ((int64_t)1 << 31))
+    return kNtNotEligible;
+  if (d.K == 16) return launch_narrow_tma_k<16>(d, A, B, C, st);
+  if (d.K == 8) return launch_narrow_tma_k<8>(d, A, B, C, st);
+  return kNtNotEligible;
+}
+
 int read_tc_error(int* flag) {
   return (int)cudaMemcpyFromSymbol(flag, tc_error_flag, sizeof(int));
 }
@@ -1442,6 +1611,14 @@ int preload_kernels_tc() {
       (const void*)prep_a_vec_kernel<true>,
       (const void*)prep_b_vec_kernel<false>,
       (const void*)prep_b_vec_kernel<true>,
+      (const void*)cgemm_narrow_tma_kernel<16, 2>,
+      (const void*)cgemm_narrow_tma_kernel<16, 4>,
+      (const void*)cgemm_narrow_tma_kernel<16, 8>,
+      (const void*)cgemm_narrow_tma_kernel<16, 16>,
+      (const void*)cgemm_narrow_tma_kernel<8, 2>,
+      (const void*)cgemm_narrow_tma_kernel<8, 4>,
+      (const void*)cgemm_narrow_tma_kernel<8, 8>,
+      (const void*)cgemm_narrow_tma_kernel<8, 16>,
   };
   cudaFuncAttributes fa;
   for (const void* f : fns) {

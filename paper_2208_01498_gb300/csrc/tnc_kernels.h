@@ -70,7 +70,9 @@ struct GemmDesc {
                         // on chip for any K (one TMEM slot + running sum; 15: with prefetch).
                         // Narrow kernel: 0 unrolled for K, N in {1, 2, 4, 8, 16} with packed FP32
                         // FMAs (K-major A; else as 1), 1 one row per thread, 2 tiled with the output
-                        // staged in address order (powers of two, K-major A; else as 1)
+                        // staged in address order (powers of two, K-major A; else as 1), 3 A tiles
+                        // staged in shared memory by TMA (K in {8, 16}, N in {2, 4, 8, 16}, M a
+                        // multiple of 256, K-major A; else as 0)
 };
 
 // One problem of a grouped launch of narrow nodes (N, K <= 16): the same

@@ -260,39 +260,55 @@ def test_cgemm_cuda_cores_split_k_small_grid(tnc, kernel, shape):
         _assert_close(placed, ref[0], "fp32", f"scattered {kernel}")
 
 
-NARROW_TILED = [  # batch, M, N, K: the tiled narrow kernel (powers of two, K-major A)
+NARROW_CASES = [  # batch, M, N, K
     (256, 8192, 16, 16), (4, 2048, 8, 16), (2, 4096, 4, 4), (1, 1 << 16, 2, 2), (8, 512, 1, 16), (3, 256, 16, 1),
-    (16, 4, 16, 8), (2, 1, 4, 4), (5, 64, 8, 2),
+    (16, 4, 16, 8), (2, 1, 4, 4), (5, 64, 8, 2), (3, 768, 4, 8), (5, 1 << 16, 2, 16), (2, 4096, 16, 8),
 ]
+NARROW_TILES = (0, 1, 2, 3)  # unrolled; one row per thread; tiled, output staged; A tiles staged by TMA
 
 
-@pytest.mark.parametrize("shape", NARROW_TILED, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("shape", NARROW_CASES, ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("scatter", [False, True])
-def test_cgemm_narrow_tiled(tnc, shape, scatter):
-    """Narrow nodes on the tiled kernel (coalesced A tile in shared memory,
-    output staged in address order), identity and shuffled output bit
-    orders, element by element against NumPy."""
+def test_cgemm_narrow_tiles(tnc, shape, scatter):
+    """Narrow nodes on every narrow kernel that takes the shape (tile 0
+    unrolled, 1 one row per thread, 2 tiled with the output staged in address
+    order, 3 A tiles staged in shared memory by TMA: ranges of tiles per CTA
+    that cross batches, M not a power of two), identity and shuffled output bit
+    orders, element by element against NumPy.  All of them compute per
+    component the same FP32 FMAs in the same order, so they agree bit for bit."""
     batch, M, N, K = shape
     rng = np.random.default_rng(M + 3 * N + 7 * K + batch)
     A = _crand(batch * M * K, rng)
     B = _crand(batch * K * N, rng)
     ref = _ref(A, B, batch, M, N, K, 0, 1)
-    nN, nM = N.bit_length() - 1, M.bit_length() - 1
-    if not scatter or batch & (batch - 1):
-        got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, 0, 1, "fp32",
-                        kernel="narrow")
-        _assert_close(got.cpu().numpy(), ref, "fp32", f"{shape}")
-        return
-    nB = batch.bit_length() - 1
-    c_pos = rng.permutation(nN + nM + nB)
-    got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, 0, 1, "fp32",
-                    kernel="narrow", c_pos=c_pos).reshape(-1).cpu().numpy()
-    b, m, n = np.meshgrid(np.arange(batch), np.arange(M), np.arange(N), indexing="ij")
-    addr = np.zeros(b.shape, np.int64)
-    for i in range(nN):
-        addr |= ((n >> i) & 1) << int(c_pos[i])
-    for i in range(nM):
-        addr |= ((m >> i) & 1) << int(c_pos[nN + i])
-    for i in range(nB):
-        addr |= ((b >> i) & 1) << int(c_pos[nN + nM + i])
-    _assert_close(got[addr], ref, "fp32", f"{shape} scattered")
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    c_pos, addr = None, None
+    if scatter and not batch & (batch - 1) and not M & (M - 1):
+        nN, nM, nB = N.bit_length() - 1, M.bit_length() - 1, batch.bit_length() - 1
+        c_pos = rng.permutation(nN + nM + nB)
+        b, m, n = np.meshgrid(np.arange(batch), np.arange(M), np.arange(N), indexing="ij")
+        addr = np.zeros(b.shape, np.int64)
+        for i in range(nN):
+            addr |= ((n >> i) & 1) << int(c_pos[i])
+        for i in range(nM):
+            addr |= ((m >> i) & 1) << int(c_pos[nN + i])
+        for i in range(nB):
+            addr |= ((b >> i) & 1) << int(c_pos[nN + nM + i])
+    elif scatter:
+        pytest.skip("scattered output needs power-of-two batch and M")
+    outs = {}
+    for tile in NARROW_TILES:
+        try:
+            got = tnc.cgemm(dA, dB, batch, M, N, K, 0, 1, "fp32", kernel="narrow", tile=tile, c_pos=c_pos)
+        except tnc.TncError as e:
+            assert e.status == tnc.TNC_EINVAL  # the tile does not take this shape
+            continue
+        got = got.reshape(-1).cpu().numpy()
+        got = got[addr] if addr is not None else got.reshape(batch, M, N)
+        _assert_close(got, ref, "fp32", f"{shape} tile {tile}")
+        outs[tile] = got
+    assert 0 in outs and 1 in outs
+    if K in (8, 16) and N >= 2 and M % 256 == 0:
+        assert 3 in outs, "the TMA-staged kernel takes this shape"
+    for tile, got in outs.items():
+        assert np.array_equal(got.view(np.uint64), outs[0].view(np.uint64)), f"tile {tile} differs from tile 0 in bits"
