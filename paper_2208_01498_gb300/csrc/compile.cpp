@@ -184,6 +184,9 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
         add(KG_TC, 14);
         add(KG_TC, 15);
       }
+      add(KG_TC, 16);  // split on chip from FP32 tiles brought by TMA
+      if (g0.N >= 64) add(KG_TC, 17);
+      if (g0.N >= 128 && g0.K <= 256) add(KG_TC, 18);
     }
     if (g0.form == TNC_SPLIT_BF16 && g0.N >= 64) add(KG_TC, 10);
     if (g0.form == TNC_SPLIT_BF16) add(KG_TC, 12);
@@ -202,13 +205,19 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
       if (g0.K >= 16 && !g0.transA) add(KG_TC, 13);
     }
   }
+  if (g0.form == TNC_SPLIT_BF16 && pow2 && g0.M >= 128 && g0.N >= 32 && g0.K >= 2 && g0.K < 32 && !g0.transA &&
+      g0.transB) {
+    add(KG_TC, 16);
+    if (g0.N >= 64) add(KG_TC, 17);
+    if (g0.N >= 128) add(KG_TC, 18);
+  }
   *n = k;
 }
 
 uint64_t gemm_scratch_bytes(const GemmDesc& g) {
   uint64_t bytes = 0;
   if (g.kernel == KG_DOT) bytes = (uint64_t)g.batch * g.M * g.N * 16 * 1024;
-  if (g.kernel == KG_TC) {
+  if (g.kernel == KG_TC && !(g.tile >= 16 && g.tile <= 18)) {  // 16-18 split on chip: no planes
     // hi/lo planes of A' (batch x M x 2K) and B'^T (batch x 2N x 2K), 2 or 4 bytes each
     const uint64_t es = g.form == TNC_SPLIT_BF16 ? 2 : 4;
     bytes = (uint64_t)g.batch * (g.M * 2 * g.K * 2 + 2 * g.N * 2 * g.K * 2) * es + 4096;

@@ -440,6 +440,7 @@ struct FzCfg {
   static constexpr int kBN = BN;
   static constexpr bool kPlanes = false;
   static constexpr bool kHybrid = false;
+  static constexpr bool kF32 = false;  // operands loaded by the converters themselves
   static constexpr int kSlots = 2;  // TMEM accumulator slots (alternating chunks / tiles)
   static constexpr int kRowBytes = BN == 256 ? 64 : 128;
   static constexpr int kChunks = kRowBytes / 16;              // 16-byte chunks per row
@@ -507,6 +508,7 @@ struct PlCfg {
   static constexpr int kBN = BN;
   static constexpr bool kPlanes = true;
   static constexpr bool kHybrid = false;
+  static constexpr bool kF32 = false;
   static constexpr int kSlots = 2;
   static constexpr int kRowBytes = ROW;  // 64-byte rows keep BN = 256 at two stages of 48 KB
   // staging blocks per epilogue step: two unless the shared memory is full
@@ -535,6 +537,7 @@ struct HyCfg {
   static constexpr int kBN = 256;
   static constexpr bool kPlanes = true;
   static constexpr bool kHybrid = true;
+  static constexpr bool kF32 = false;
   static constexpr int kSlots = 2;
   static constexpr int kRowBytes = 64;
   static constexpr int kChunks = kRowBytes / 16;
@@ -576,6 +579,67 @@ struct FzWideCfg : FzCfg<256> {
   static constexpr int kTmemCols = 512;
   static constexpr int kChunkKB = 1024 / (kRowBytes / 2);
 };
+
+// Split on chip from FP32 tiles that TMA brings into shared memory: a
+// producer warp streams each k-block's A tile (128 rows) and B tile (BN / 2
+// complex rows) of 16 complex k (128-byte rows, 128-byte swizzle) into a ring
+// of kF32Stages stages, several k-blocks ahead; the converters read their
+// tasks from there instead of from global memory, split them and store the
+// 64-byte-row A' and B'^T tiles as FzCfg does.  The converters of FzCfg hold
+// one k-block of loads in registers, so a CTA has about one k-block of DRAM
+// reads in flight and the short-K, output-heavy nodes ran at half the HBM
+// rate; the ring keeps several in flight without registers.  BN = 256 takes
+// K <= 256 (one accumulation chunk per tile, no running sum).
+template <int BN>
+struct FtCfg {
+  static constexpr int kBN = BN;
+  static constexpr bool kPlanes = false;
+  static constexpr bool kHybrid = false;
+  static constexpr bool kF32 = true;
+  static constexpr int kSlots = 2;
+  static constexpr int kRowBytes = 64;
+  static constexpr int kChunks = 4;
+  static constexpr int kKC = 16;
+  static constexpr int kKSteps = 2;
+  static constexpr int kChunkKB = 512 / (kRowBytes / 2);
+  static constexpr int kATasks = 128 * kChunks;
+  static constexpr int kTasks = kATasks + (BN / 2) * kChunks;
+  static constexpr int kTPT = 2;
+  static constexpr int kConvWarps = kTasks / (32 * kTPT);  // 10, 12 or 16
+  static constexpr int kConvThreads = 32 * kConvWarps;
+  static constexpr int kEpiWarps = BN == 256 ? 8 : 4;
+  // staging blocks per epilogue step: the 18-warp BN = 128 block has 96
+  // registers a thread, the 26-warp BN = 256 block 72 (as the hybrid tile)
+  static constexpr int kStageBlocks = BN == 128 ? 1 : 2;
+  static constexpr int kThreads = 32 * (kEpiWarps + 2 + kConvWarps);
+  static constexpr int kFullArrivals = kConvThreads;
+  static constexpr uint32_t kATileBytes = 128 * kRowBytes;
+  static constexpr uint32_t kBTileBytes = BN * kRowBytes;
+  static constexpr uint32_t kStageBytes = 2 * kATileBytes + 2 * kBTileBytes;
+  static constexpr bool kSum = BN != 256;
+  static constexpr int kTmemCols = BN == 256 ? 512 : (3 * BN <= 256 ? 256 : 512);
+  static constexpr int kF32Stages = BN == 256 ? 2 : 4;
+  static constexpr uint32_t kF32ABytes = 128 * 128;                 // 128 rows x 16 complex
+  static constexpr uint32_t kF32StageBytes = kF32ABytes + (BN / 2) * 128;
+  __device__ static uint32_t swz(int row, int chunk) { return (uint32_t)(row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4)); }
+  __device__ static uint64_t desc(uint32_t saddr) { return sw64_desc(saddr); }
+};
+
+// shared-memory bytes and stages of the FP32 ring (0 without one)
+template <class Cf>
+__host__ __device__ constexpr uint32_t f32_ring_bytes() {
+  if constexpr (Cf::kF32)
+    return Cf::kF32Stages * Cf::kF32StageBytes;
+  else
+    return 0;
+}
+template <class Cf>
+__host__ __device__ constexpr int f32_stages() {
+  if constexpr (Cf::kF32)
+    return Cf::kF32Stages;
+  else
+    return 0;
+}
 
 struct PlMaps {
   CUtensorMap ah, al, bh, bl;
@@ -685,6 +749,23 @@ __device__ __forceinline__ void fz_prefetch(const float2* __restrict__ A, const 
   }
 }
 
+// A converter thread's tasks of one k-block from the FP32 ring stage at
+// `stage` (A tile, then B tile; 128-byte rows, 16-byte chunk c of row r at
+// r * 128 + ((c ^ (r % 8)) * 16)): the same registers fz_load fills
+template <class Cf>
+__device__ __forceinline__ void ft_load(FzRegs<Cf::kTPT>& R, const uint8_t* stage, int ct) {
+  const int cc = ct % Cf::kChunks;
+#pragma unroll
+  for (int i = 0; i < Cf::kTPT; ++i) {
+    const int j = ct + Cf::kConvThreads * i;
+    const bool a = j < Cf::kATasks;
+    const int r = a ? j / Cf::kChunks : (j - Cf::kATasks) / Cf::kChunks;
+    const uint8_t* row = stage + (a ? 0u : Cf::kF32ABytes) + r * 128;
+    R.v[i][0] = *(const float4*)(row + (((2 * cc) ^ (r & 7)) << 4));
+    R.v[i][1] = *(const float4*)(row + (((2 * cc + 1) ^ (r & 7)) << 4));
+  }
+}
+
 template <class Cf>
 __device__ __forceinline__ void fz_store(const FzRegs<Cf::kTPT>& R, uint32_t st, int ct) {
   constexpr uint32_t kAl = Cf::kATileBytes, kB = 2 * Cf::kATileBytes, kBl = kB + Cf::kBTileBytes;
@@ -751,9 +832,12 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
   constexpr int CHUNK = Cf::kSum ? Cf::kChunkKB : (1 << 30);
   constexpr uint32_t IDESC = instr_desc<false, BN>();
   constexpr uint32_t kStageBytes = Cf::kStageBytes;
+  constexpr bool kProducer = Cf::kPlanes || Cf::kF32;  // warp E + 1 issues TMA loads
+  constexpr int SF = f32_stages<Cf>();                   // FP32 ring stages (kF32)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + kFzStages * kStageBytes);
+  uint8_t* ring = smem + kFzStages * kStageBytes;        // FP32 ring (kF32), 1024-byte aligned
+  uint64_t* full = (uint64_t*)(ring + f32_ring_bytes<Cf>());
   uint64_t* empty = full + kFzStages;
   uint64_t* acc_full = empty + kFzStages;  // [2]
   uint64_t* acc_empty = acc_full + 2;      // [2]
@@ -765,6 +849,8 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
                                                             // (coltab: [E warps][CW / 2], 4 BN / 2 in all)
   uint64_t* blk_dep = (uint64_t*)(blk_col + 8);               // [8] output offset of staging index bits 5..7
   float2* stage_out = (float2*)(blk_dep + 8);                 // [E warps][2][256]
+  uint64_t* ffull = (uint64_t*)(stage_out + Cf::kEpiWarps * Cf::kStageBlocks * 256);  // [SF] (kF32)
+  uint64_t* fempty = ffull + SF;                                                       // [SF]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int E = Cf::kEpiWarps;        // warps 0..E-1: epilogue; E: MMA; E+1..: producer / converters
@@ -784,6 +870,11 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
       mbar_init(&acc_empty[s], 32 * E);
     }
     mbar_init(done, 1);
+    if constexpr (Cf::kF32)
+      for (int f = 0; f < SF; ++f) {
+        mbar_init(&ffull[f], 1);
+        mbar_init(&fempty[f], Cf::kConvThreads);
+      }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -799,7 +890,43 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   int64_t tma_issued = 0;  // planes: k-blocks whose TMA loads were issued
-  if (Cf::kPlanes && warp == E + 1) {
+  if (Cf::kF32 && warp == E + 1) {
+    // producer: TMA loads of the FP32 A and B tiles of every k-block into the ring
+    if constexpr (Cf::kF32) {
+      if (lane == 0) {
+        int f = 0;
+        uint32_t fph = 0;
+        for (int64_t lt = 0; lt < my_tiles; ++lt) {
+          int bz, m0, n0;
+          fz_tile<BN>(geo, (int64_t)blockIdx.x + lt * gridDim.x, bz, m0, n0);
+          bool ok = true;
+          for (int kb = 0; kb < nk; ++kb) {
+            if (tma_issued >= SF && !mbar_wait(&fempty[f], fph ^ 1u)) {
+              atomicExch(&tc_error_flag, 10);
+              *(volatile int*)abort_flag = 1;
+              ok = false;
+              break;
+            }
+            if (*(volatile int*)abort_flag) {
+              ok = false;
+              break;
+            }
+            uint8_t* st = ring + f * Cf::kF32StageBytes;
+            const int kx = kb * (2 * Cf::kKC);  // first float of the k-block
+            mbar_expect_tx(&ffull[f], Cf::kF32StageBytes);
+            tma_load_3d(st, &maps.ah, &ffull[f], kx, m0, bz);
+            tma_load_3d(st + Cf::kF32ABytes, &maps.bh, &ffull[f], kx, n0 / 2, bz);
+            ++tma_issued;
+            if (++f == SF) {
+              f = 0;
+              fph ^= 1u;
+            }
+          }
+          if (!ok) break;
+        }
+      }
+    }
+  } else if (Cf::kPlanes && warp == E + 1) {
     // producer: TMA loads of the hi/lo plane tiles of every k-block
     if (lane == 0) {
       int s = 0;
@@ -839,8 +966,41 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
         if (!ok) break;
       }
     }
-  } else if (warp >= E + 1 + (Cf::kPlanes ? 1 : 0)) {
-   if constexpr (!Cf::kPlanes || Cf::kHybrid) {
+  } else if (warp >= E + 1 + (kProducer ? 1 : 0)) {
+   if constexpr (Cf::kF32) {
+    // converters fed by the FP32 ring: k-block q in ring stage q % SF
+    const int ct = threadIdx.x - 32 * (E + 2);
+    const int64_t total = my_tiles * nk;
+    FzRegs<Cf::kTPT> R;
+    int s = 0, f = 0;
+    uint32_t ph = 0, fph = 0;
+    for (int64_t q = 0; q < total; ++q) {
+      if (!mbar_wait(&ffull[f], fph)) {
+        atomicExch(&tc_error_flag, 11);
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      ft_load<Cf>(R, ring + f * Cf::kF32StageBytes, ct);
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&fempty[f])) : "memory");
+      if (++f == SF) {
+        f = 0;
+        fph ^= 1u;
+      }
+      if (q >= kFzStages && !mbar_wait(&empty[s], ph ^ 1u)) {
+        atomicExch(&tc_error_flag, 6);
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)abort_flag) break;
+      fz_store<Cf>(R, smem_u32(smem + s * kStageBytes), ct);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[s])) : "memory");
+      if (++s == kFzStages) {
+        s = 0;
+        ph ^= 1u;
+      }
+    }
+   } else if constexpr (!Cf::kPlanes || Cf::kHybrid) {
     // converters: global k-block q = (local tile) * nk + kb
     const int ct = threadIdx.x - 32 * (E + 1 + (Cf::kHybrid ? 1 : 0));
     const int64_t total = my_tiles * nk;
@@ -1037,6 +1197,10 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
     for (int64_t q = (tma_issued > kFzStages ? tma_issued - kFzStages : 0); q < tma_issued; ++q)
       mbar_wait(&full[q % kFzStages], (uint32_t)((q / kFzStages) & 1));
   }
+  if (Cf::kF32 && warp == E + 1 && lane == 0 && *(volatile int*)abort_flag) {
+    for (int64_t q = (tma_issued > SF ? tma_issued - SF : 0); q < tma_issued; ++q)
+      mbar_wait(&ffull[q % SF], (uint32_t)((q / SF) & 1));
+  }
   __syncthreads();
   if (warp == E) {
     tc_fence_after();
@@ -1065,8 +1229,9 @@ int launch_persistent(const GemmDesc& d, const float2* A, const float2* B, float
                       cudaStream_t st) {
   constexpr int BN = Cf::kBN;
   // at least 117 KB so that one CTA (and one TMEM allocation) holds an SM
-  const size_t need = 1024 + kFzStages * Cf::kStageBytes + (2 * kFzStages + 5) * 8 + 16 + 4 * BN / 2 * 8 + 8 * 4 +
-                      8 * 8 + Cf::kEpiWarps * Cf::kStageBlocks * 256 * 8;
+  const size_t need = 1024 + kFzStages * Cf::kStageBytes + f32_ring_bytes<Cf>() + (2 * kFzStages + 5) * 8 + 16 +
+                      4 * BN / 2 * 8 + 8 * 4 + 8 * 8 + Cf::kEpiWarps * Cf::kStageBlocks * 256 * 8 +
+                      2 * f32_stages<Cf>() * 8;
   const size_t smem = need > 117 * 1024 ? need : 117 * 1024;
   static std::atomic<int> attr_done[kMaxDevices];
   if (int e = smem_attr_once(attr_done, tc_fused_bf16_kernel<Cf, PREFETCH>, (int)smem)) return e;
@@ -1246,6 +1411,31 @@ int make_map(CUtensorMap* m, void* base, bool tf32, int64_t cols, int64_t rows, 
   return r == CUDA_SUCCESS ? 0 : (int)cudaErrorInvalidValue;
 }
 
+// split on chip from FP32 tiles brought by TMA (FtCfg): maps over A [b][M][K]
+// and B [b][N][K] as FP32 rows of 2K floats, boxes of 16 complex k x 128
+// (A) or BN / 2 (B) rows, 128-byte swizzle
+template <int BN>
+int run_tc_ft(const GemmDesc& d, const float2* A, const float2* B, float* C, cudaStream_t st) {
+  PlMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  if (int e = make_map(&maps.ah, (void*)A, true, 2 * d.K, d.M, d.batch, BM, 128)) return e;
+  if (int e = make_map(&maps.bh, (void*)B, true, 2 * d.K, d.N, d.batch, BN / 2, 128)) return e;
+  return launch_persistent<FtCfg<BN>, false>(d, A, B, C, maps, st);
+}
+
+template <int BN>
+bool ft_launchable() {
+  static std::atomic<int> ok{-1};
+  int v = ok.load(std::memory_order_acquire);
+  if (v < 0) {
+    cudaFuncAttributes fa;
+    v = cudaFuncGetAttributes(&fa, tc_fused_bf16_kernel<FtCfg<BN>, false>) == cudaSuccess &&
+        fa.maxThreadsPerBlock >= FtCfg<BN>::kThreads;
+    ok.store(v, std::memory_order_release);
+  }
+  return v == 1;
+}
+
 // hi/lo planes of A' and B'^T in the scratch and TMA maps over them (boxes
 // of 128-byte rows x 128 (A) or box_n (B) rows)
 template <bool kTF32>
@@ -1327,12 +1517,26 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
                    cudaStream_t st) {
   // the persistent plane tiles (9, 10) also take short K (a power of two
   // >= 4): TMA fills the k-block beyond the plane rows with zeros
-  const bool short_k = ((d.tile >= 9 && d.tile <= 12) || (d.tile == 13 && d.K >= 16)) && d.K >= 4 && d.K < 32 &&
-                       !(d.K & (d.K - 1));
+  const bool short_k = (((d.tile >= 9 && d.tile <= 12) || (d.tile == 13 && d.K >= 16)) && d.K >= 4 && d.K < 32 &&
+                        !(d.K & (d.K - 1))) ||
+                       (d.tile >= 16 && d.tile <= 18 && d.K >= 2 && d.K < 32 && !(d.K & 1));
   if (d.M < BM || d.N < 32 || (d.K < 32 && !short_k) || (d.M % BM) || (d.N % 32) || (d.K % 32 && !short_k) ||
       d.M > (1 << 30) || 2 * d.N > (1 << 30) || 2 * d.K > (1 << 30))
     return (int)cudaErrorInvalidValue;
   const bool tf32 = d.form == TNC_3XTF32;
+  const int tile = d.tile ? d.tile : (d.N >= 64 ? 2 : 1);
+  if (tile >= 16 && tile <= 18) {  // no scratch
+    // split on chip from FP32 tiles by TMA: K-major, 16-byte aligned, K even;
+    // 18: 256 columns, K <= 256
+    const int bn = tile == 16 ? 64 : (tile == 17 ? 128 : 256);
+    if (tf32 || d.transA || !d.transB || 2 * d.N < bn || (2 * d.N) % bn || (d.K & 1) || (tile == 18 && d.K > 256) ||
+        ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
+      return (int)cudaErrorInvalidValue;
+    if (tile == 16 && ft_launchable<64>()) return run_tc_ft<64>(d, A, B, (float*)C, st);
+    if (tile == 17 && ft_launchable<128>()) return run_tc_ft<128>(d, A, B, (float*)C, st);
+    if (tile == 18 && ft_launchable<256>()) return run_tc_ft<256>(d, A, B, (float*)C, st);
+    return (int)cudaErrorInvalidValue;
+  }
   const uint64_t es = tf32 ? 4 : 2;
   const uint64_t need = (uint64_t)d.batch * (d.M * 2 * d.K * 2 + 2 * d.N * 2 * d.K * 2) * es;
   if (need > d.scratch_elems * 8) return (int)cudaErrorInvalidValue;
@@ -1347,7 +1551,6 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   // 13: 128 x 256 (K <= 256) with A split on chip and B' from its planes;
   // 14, 15: 128 x 256 split on chip for any K (one TMEM slot + running sum),
   // 15 with the L2 prefetch
-  const int tile = d.tile ? d.tile : (d.N >= 64 ? 2 : 1);
   if (tile < 1 || tile > 15 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
       (tile >= 4 && tile <= 8 && (d.transA || !d.transB)) || (tile >= 4 && tf32) ||
       ((tile == 4 || tile == 5 || tile == 10) && d.N < 64) ||
@@ -1603,6 +1806,9 @@ int preload_kernels_tc() {
       (const void*)tc_fused_bf16_kernel<PlCfg<128, 128>, false>,
       (const void*)tc_fused_bf16_kernel<PlCfg<256, 64>, false>,
       (const void*)tc_fused_bf16_kernel<PlCfg<64, 128>, false>,
+      (const void*)tc_fused_bf16_kernel<FtCfg<64>, false>,
+      (const void*)tc_fused_bf16_kernel<FtCfg<128>, false>,
+      (const void*)tc_fused_bf16_kernel<FtCfg<256>, false>,
       (const void*)prep_a_kernel<false>,
       (const void*)prep_a_kernel<true>,
       (const void*)prep_b_kernel<false>,

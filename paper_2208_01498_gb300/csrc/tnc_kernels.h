@@ -67,7 +67,9 @@ struct GemmDesc {
                         // (K <= 256), 10 N = 128, 11 N = 256 with 64-byte rows, 12 N = 64:
                         // persistent from the planes (9-12 also for K = 4..16); 13 N = 256
                         // (K <= 256): A split on chip, B' from its planes; 14, 15 N = 256 split
-                        // on chip for any K (one TMEM slot + running sum; 15: with prefetch).
+                        // on chip for any K (one TMEM slot + running sum; 15: with prefetch);
+                        // 16 N = 64, 17 N = 128, 18 N = 256 (K <= 256): split on chip from FP32
+                        // tiles that TMA streams into a shared-memory ring (K even, also < 32).
                         // Narrow kernel: 0 unrolled for K, N in {1, 2, 4, 8, 16} with packed FP32
                         // FMAs (K-major A; else as 1), 1 one row per thread, 2 tiled with the output
                         // staged in address order (powers of two, K-major A; else as 1), 3 A tiles
@@ -136,7 +138,7 @@ void choose_gemm_kernel(GemmDesc& g);
 uint64_t gemm_scratch_bytes(const GemmDesc& g);
 // every kernel variant that can run this node (the default choice first)
 void gemm_candidates(const GemmDesc& g, GemmDesc* out, int* n);
-constexpr int kMaxCandidates = 20;
+constexpr int kMaxCandidates = 24;
 int launch_accum(const AccumDesc& d, const void* ws, void* d_out, int batch, void* stream);
 int launch_grouped_narrow(const GroupedDesc* d_descs, int n, int64_t total_blocks, const void* base, void* ws,
                           void* stream);

@@ -184,7 +184,9 @@ SCATTER_CASES = [  # batch, M, N, K, kernel, tile, form
     (4, 256, 128, 128, "tc", 13, "split_bf16"), (2, 512, 256, 16, "tc", 13, "split_bf16"),
     (2, 256, 128, 2048, "tc", 14, "split_bf16"), (2, 128, 256, 1024, "tc", 15, "split_bf16"),
     (2, 128, 64, 1024, "tc", 5, "split_bf16"), (2, 256, 64, 128, "tc", 10, "split_bf16"),
-    (4, 128, 64, 64, "tc", 2, "3xtf32"),
+    (4, 128, 64, 64, "tc", 2, "3xtf32"), (4, 256, 32, 32, "tc", 16, "split_bf16"),
+    (4, 256, 64, 128, "tc", 17, "split_bf16"), (2, 256, 128, 256, "tc", 18, "split_bf16"),
+    (4, 256, 64, 8, "tc", 17, "split_bf16"),
 ]
 
 
@@ -228,6 +230,25 @@ def test_cgemm_short_k_plane_tiles(tnc, shape, tile):
     B = _crand(batch * K * N, rng)
     ref = _ref(A, B, batch, M, N, K, tA, tB)
     got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, tA, tB, "split_bf16",
+                    kernel="tc", tile=tile)
+    _assert_close(got.cpu().numpy(), ref, "split_bf16", f"{shape} tile {tile}")
+
+
+@pytest.mark.parametrize("shape,tile", [((2, 256, 32, 2), 16), ((4, 128, 64, 8), 17), ((2, 256, 128, 4), 18),
+                                        ((1, 512, 64, 16), 16), ((8, 4096, 32, 32), 16), ((2, 2048, 64, 64), 17),
+                                        ((4, 1024, 128, 256), 18), ((2, 256, 64, 2048), 17),
+                                        ((1, 128, 32, 1024), 16), ((16, 512, 128, 32), 18)])
+def test_cgemm_f32_ring_tiles(tnc, shape, tile):
+    """The on-chip split fed by TMA from FP32 tiles (tiles 16-18): short K
+    (the k-block beyond K zero-filled by TMA), CTAs with several tiles, rings
+    that wrap many times, long K with several accumulation chunks, element by
+    element against NumPy."""
+    batch, M, N, K = shape
+    rng = np.random.default_rng(M + 3 * N + 5 * K + tile)
+    A = _crand(batch * M * K, rng)
+    B = _crand(batch * K * N, rng)
+    ref = _ref(A, B, batch, M, N, K, 0, 1)
+    got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, 0, 1, "split_bf16",
                     kernel="tc", tile=tile)
     _assert_close(got.cpu().numpy(), ref, "split_bf16", f"{shape} tile {tile}")
 
