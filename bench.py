@@ -743,12 +743,11 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": fl / avg_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     choices = plan.get_kernels()
-    dtile = int(choices[di][1]) if dkind == 4 else 0
+    dtile = int(choices[di][1]) if choices[di][1] >= 0 else 0
     roof["traffic"] = _traffic(step, names.get(dkind), args.form, dtile)
     roof["kernel"] = names.get(dkind, str(dkind))
     roof["step"] = {k: step.get(k) for k in ("batch", "M", "N", "K")}
-    if dkind == 4:
-        roof["step"]["tile"] = dtile
+    roof["step"]["tile"] = dtile
     roof["launches_timed"] = druns
     roof["avg_launch_ms"] = avg_s * 1e3
     roof["algorithmic_bytes_per_launch"] = by

@@ -604,13 +604,16 @@ struct FtCfg {
   static constexpr int kChunkKB = 512 / (kRowBytes / 2);
   static constexpr int kATasks = 128 * kChunks;
   static constexpr int kTasks = kATasks + (BN / 2) * kChunks;
-  static constexpr int kTPT = 2;
-  static constexpr int kConvWarps = kTasks / (32 * kTPT);  // 10, 12 or 16
+  // Converters only read shared memory here, so 4 tasks a thread keep up;
+  // the epilogue sets the pace of these output-heavy nodes, so 8 warps (two
+  // per TMEM lane quarter, half of the columns each) drain it: 4 -> 8 took
+  // the batch 256, M 2048, N 64, K 32 node from 0.157 to 0.114 ms.  15, 16
+  // or 18 warps: 128, 128 and 96 registers a thread.
+  static constexpr int kTPT = 4;
+  static constexpr int kConvWarps = kTasks / (32 * kTPT);  // 5, 6 or 8
   static constexpr int kConvThreads = 32 * kConvWarps;
-  static constexpr int kEpiWarps = BN == 256 ? 8 : 4;
-  // staging blocks per epilogue step: the 18-warp BN = 128 block has 96
-  // registers a thread, the 26-warp BN = 256 block 72 (as the hybrid tile)
-  static constexpr int kStageBlocks = BN == 128 ? 1 : 2;
+  static constexpr int kEpiWarps = 8;
+  static constexpr int kStageBlocks = 2;
   static constexpr int kThreads = 32 * (kEpiWarps + 2 + kConvWarps);
   static constexpr int kFullArrivals = kConvThreads;
   static constexpr uint32_t kATileBytes = 128 * kRowBytes;
@@ -688,6 +691,23 @@ struct BlockOrder {
     return o;
   }
 };
+
+// Direct epilogue stores of one warp's column blocks (v: NB blocks of 8
+// complex columns, real and imaginary parts interleaved; ctc: the output
+// offsets of those columns) when output bit 0 is column bit CB: the column
+// pair (j, j | 2^CB) is 16 contiguous bytes.
+template <int CB, int NB>
+__device__ __forceinline__ void store_pairs(float2* base, const uint64_t* ctc, const float* v) {
+#pragma unroll
+  for (int h = 0; h < NB; ++h)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (j & (1 << CB)) continue;
+      const int k = j | (1 << CB);
+      *(float4*)(base + ctc[8 * h + j]) =
+          make_float4(v[16 * h + 2 * j], v[16 * h + 2 * j + 1], v[16 * h + 2 * k], v[16 * h + 2 * k + 1]);
+    }
+}
 
 // bank spread of the staging block (8-byte elements): low 4 index bits XOR
 // the high 4, a bijection on 0..255
@@ -1107,10 +1127,41 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
     float2* so = stage_out + warp * 256 * Cf::kStageBlocks;
     uint32_t idx_row = 0;
     uint64_t dep_lane = 0;
+    // Direct stores, without the staging block, when the lowest output
+    // address bits are bits of this warp's 32 x 8 block (rows 0..4 from the
+    // lane, columns 0..2 from the register index): every store then fills
+    // whole 32-byte sectors or halves that the same thread completes next,
+    // and the re-ordering through shared memory would only add latency.
+    //   direct 1: positions 0 and 1 both row bits: 8-byte stores, aligned
+    //             groups of four lanes cover a sector;
+    //   direct 2: position 0 a column bit c: 16-byte stores of the column
+    //             pairs (j, j | 2^c).
+    // (A row bit at 0 and a column bit at 1, the pair exchanged between two
+    // lanes by a shuffle, was slower than the staging block: 0.101 -> 0.108 ms
+    // on batch 256, M 512, N 256, K 64.)
+    int direct = 0, dbit_c = 0;
+    uint64_t lane_off = 0;
     if (!om.ident) {
       const BlockOrder bo(om);
       idx_row = bo.index_row(lane);
       dep_lane = bo.offset_of((uint32_t)lane);
+      int r0 = -1, r1 = -1, c0 = -1;
+#pragma unroll
+      for (int b = 0; b < 5; ++b) {
+        if (om.pos[om.nN + b] == 0) r0 = b;
+        if (om.pos[om.nN + b] == 1) r1 = b;
+      }
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (om.pos[b] == 0) c0 = b;
+      }
+      if (r0 >= 0 && r1 >= 0) {
+        direct = 1;
+      } else if (c0 >= 0) {
+        direct = 2;
+        dbit_c = c0;
+      }
+      lane_off = om.row(0, lane, geo.M, geo.N);
     }
     int64_t gc = 0;
     bool ok = true;
@@ -1160,6 +1211,19 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
               float4* dst = (float4*)(C + ((int64_t)bz * geo.M + row) * N2 + n0 + col);
 #pragma unroll
               for (int i = 0; i < 4 * NB; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            } else if (direct) {
+              float2* base = (float2*)C + roff + lane_off;
+              const uint64_t* ctc = ct + (col - half * CW) / 2;
+              if (direct == 1) {
+#pragma unroll
+                for (int h = 0; h < NB; ++h)
+#pragma unroll
+                  for (int j = 0; j < 8; ++j) base[ctc[8 * h + j]] = make_float2(v[16 * h + 2 * j], v[16 * h + 2 * j + 1]);
+              } else {
+                if (dbit_c == 0) store_pairs<0, NB>(base, ctc, v);
+                else if (dbit_c == 1) store_pairs<1, NB>(base, ctc, v);
+                else store_pairs<2, NB>(base, ctc, v);
+              }
             } else {
               // through the warp's staging blocks: written by (row, column),
               // read back in output order, so that each store covers the

@@ -217,6 +217,48 @@ def test_cgemm_scattered_output(tnc, case):
     assert np.array_equal(np.sort(addr.reshape(-1)), np.arange(addr.size))
 
 
+@pytest.mark.parametrize("case", [(4, 256, 128, 128, 4), (8, 256, 32, 64, 6), (2, 256, 128, 256, 8),
+                                  (2, 256, 64, 128, 10), (4, 256, 128, 128, 13), (2, 256, 128, 512, 14),
+                                  (4, 256, 32, 32, 16), (4, 256, 64, 128, 17), (2, 256, 128, 256, 18)],
+                         ids=lambda c: f"tile{c[4]}")
+@pytest.mark.parametrize("low", [("m", 0, "m", 1), ("n", 1, None, None), ("n", 2, "m", 3), ("m", 2, "n", 2),
+                                 ("m", 4, "n", 0)], ids=lambda x: "".join(str(t) for t in x if t is not None))
+def test_cgemm_direct_store_layout(tnc, case, low):
+    """Output orders whose lowest address bits are bits of an epilogue warp's
+    32 x 8 block: row bits at bits 0 and 1 (direct 8-byte stores), a column
+    bit at bit 0 (direct 16-byte column pairs), a row bit at 0 and a column
+    bit at 1 (through the staging block).  Element by element against NumPy;
+    the scatter is a bijection."""
+    batch, M, N, K, tile = case
+    nN, nM, nB = N.bit_length() - 1, M.bit_length() - 1, batch.bit_length() - 1
+    rng = np.random.default_rng(11 * tile + K)
+    c_pos = np.full(nN + nM + nB, -1, np.int64)
+    fixed = []
+    for at, (kind, bit) in enumerate([(low[0], low[1]), (low[2], low[3])]):
+        if kind is None:
+            continue
+        idx = bit if kind == "n" else nN + bit
+        c_pos[idx] = at
+        fixed.append(at)
+    others = [i for i in range(nN + nM + nB) if c_pos[i] < 0]
+    c_pos[others] = rng.permutation([p for p in range(nN + nM + nB) if p not in fixed])
+    A = _crand(batch * M * K, rng)
+    B = _crand(batch * K * N, rng)
+    got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, 0, 1, "split_bf16",
+                    kernel="tc", tile=tile, c_pos=c_pos).reshape(-1).cpu().numpy()
+    ref = _ref(A, B, batch, M, N, K, 0, 1)
+    b, m, n = np.meshgrid(np.arange(batch), np.arange(M), np.arange(N), indexing="ij")
+    addr = np.zeros(b.shape, np.int64)
+    for i in range(nN):
+        addr |= ((n >> i) & 1) << int(c_pos[i])
+    for i in range(nM):
+        addr |= ((m >> i) & 1) << int(c_pos[nN + i])
+    for i in range(nB):
+        addr |= ((b >> i) & 1) << int(c_pos[nN + nM + i])
+    assert np.array_equal(np.sort(addr.reshape(-1)), np.arange(addr.size))
+    _assert_close(got[addr], ref, "split_bf16", f"{case} direct stores")
+
+
 @pytest.mark.parametrize("shape,tile", [((2, 256, 128, 8, 0, 1), 9), ((2, 256, 128, 8, 0, 1), 10),
                                         ((4, 128, 64, 4, 0, 1), 10), ((1, 512, 256, 16, 1, 0), 9),
                                         ((2, 256, 128, 8, 0, 1), 11), ((1, 256, 256, 4, 0, 1), 11),
