@@ -326,6 +326,7 @@ def test_cgemm_cuda_cores_split_k_small_grid(tnc, kernel, shape):
 NARROW_CASES = [  # batch, M, N, K
     (256, 8192, 16, 16), (4, 2048, 8, 16), (2, 4096, 4, 4), (1, 1 << 16, 2, 2), (8, 512, 1, 16), (3, 256, 16, 1),
     (16, 4, 16, 8), (2, 1, 4, 4), (5, 64, 8, 2), (3, 768, 4, 8), (5, 1 << 16, 2, 16), (2, 4096, 16, 8),
+    (256, 1024, 4, 4), (3, 1280, 16, 4), (1, 1 << 20, 8, 4),
 ]
 NARROW_TILES = (0, 1, 2, 3)  # unrolled; one row per thread; tiled, output staged; A tiles staged by TMA
 
