@@ -211,6 +211,10 @@ void gemm_candidates(const GemmDesc& g0, GemmDesc* out, int* n) {
     if (g0.N >= 64) add(KG_TC, 17);
     if (g0.N >= 128) add(KG_TC, 18);
   }
+  // few output tiles and long K: the plane tiles with K split over CTAs
+  if (g0.form != TNC_FP32 && pow2 && g0.M >= 128 && g0.N >= 32 && g0.K >= 1024 &&
+      (double)(g0.M / 128) * (2.0 * g0.N / (g0.N >= 64 ? 128 : 64)) * g0.batch < (double)sm_count())
+    add(KG_TC, 19);
   *n = k;
 }
 
@@ -221,6 +225,9 @@ uint64_t gemm_scratch_bytes(const GemmDesc& g) {
     // hi/lo planes of A' (batch x M x 2K) and B'^T (batch x 2N x 2K), 2 or 4 bytes each
     const uint64_t es = g.form == TNC_SPLIT_BF16 ? 2 : 4;
     bytes = (uint64_t)g.batch * (g.M * 2 * g.K * 2 + 2 * g.N * 2 * g.K * 2) * es + 4096;
+    // tile 19 (K split over CTAs): partial tiles after the planes, splits x
+    // tiles <= 2 x SMs, each 128 rows x 64 complex columns at most
+    if (g.tile == 19) bytes += 256 + (uint64_t)2 * sm_count() * 128 * 64 * 8;
   }
   if (g.splitk > 1) bytes = std::max<uint64_t>(bytes, (uint64_t)g.splitk * g.batch * g.M * g.N * 8);
   return bytes;

@@ -824,6 +824,17 @@ __global__ void splitk_reduce_kernel(const float2* __restrict__ part, float2* __
   }
 }
 
+}  // namespace
+
+void launch_splitk_reduce(const float2* part, float2* C, int splits, int64_t n, int64_t M, int64_t N, const OutMap& om,
+                          cudaStream_t st) {
+  const int64_t cap = (int64_t)sm_count() * 16;
+  const unsigned blocks = (unsigned)((n + 255) / 256 < cap ? (n + 255) / 256 : cap);
+  if (blocks) splitk_reduce_kernel<<<blocks, 256, 0, st>>>(part, C, splits, n, M, N, om);
+}
+
+namespace {
+
 template <int BM, int BN, int BK, int TM, int TN>
 int run_simt(const GemmDesc& d, const float2* A, const float2* B, float2* C, float2* ws, cudaStream_t st) {
   constexpr int NT = (BM / TM) * (BN / TN);

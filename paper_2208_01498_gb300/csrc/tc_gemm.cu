@@ -36,6 +36,11 @@ namespace tnc {
 
 __device__ int tc_error_flag = 0;
 
+// sum of FP32 split-K partials [splits][n] (FP64 sums) into C in the
+// consumer's layout (kernels.cu)
+void launch_splitk_reduce(const float2* part, float2* C, int splits, int64_t n, int64_t M, int64_t N, const OutMap& om,
+                          cudaStream_t st);
+
 namespace {
 
 constexpr int BM = 128;
@@ -216,7 +221,8 @@ template <bool kTF32, int BN, int STAGES>
 __global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
                    const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
-                   float* __restrict__ C, int M, int N2, int K2, int b0, const __grid_constant__ OutMap om) {
+                   float* __restrict__ C, int M, int N2, int K2, int b0, const __grid_constant__ OutMap om,
+                   int ksplit, int64_t c_split) {
   constexpr int ES = kTF32 ? 4 : 2;
   constexpr int BK = 128 / ES;            // elements per 128-byte row
   constexpr int KSTEP = kTF32 ? 8 : 16;   // K of one MMA instruction
@@ -245,8 +251,14 @@ __global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
   const int m0 = (blockIdx.x % tiles_m) * BM;
   const int n0 = (blockIdx.x / tiles_m) * BN;
   const int bz = b0 + blockIdx.z;
-  const int nk = K2 / BK;
+  // K split over gridDim.y (ksplit > 1): this CTA's k-blocks [kb0, kb0 + nk),
+  // its FP32 partial tile written (plain layout) at C + blockIdx.y * c_split
+  const int nk_all = K2 / BK;
+  const int per = (nk_all + ksplit - 1) / ksplit;
+  const int kb0 = (int)blockIdx.y * per;
+  const int nk = kb0 >= nk_all ? 0 : (nk_all - kb0 < per ? nk_all - kb0 : per);
   const int nchunks = (nk + CHUNK - 1) / CHUNK;
+  C += (int64_t)blockIdx.y * c_split;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -280,10 +292,11 @@ __global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
         if (*(volatile int*)abort_flag) break;
         uint8_t* st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full[s], STAGE_BYTES);
-        tma_load_3d(st, &mA_hi, &full[s], kb * BK, m0, bz);
-        tma_load_3d(st + A_BYTES, &mA_lo, &full[s], kb * BK, m0, bz);
-        tma_load_3d(st + 2 * A_BYTES, &mB_hi, &full[s], kb * BK, n0, bz);
-        tma_load_3d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], kb * BK, n0, bz);
+        const int kx = (kb0 + kb) * BK;
+        tma_load_3d(st, &mA_hi, &full[s], kx, m0, bz);
+        tma_load_3d(st + A_BYTES, &mA_lo, &full[s], kx, m0, bz);
+        tma_load_3d(st + 2 * A_BYTES, &mB_hi, &full[s], kx, n0, bz);
+        tma_load_3d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], kx, n0, bz);
         issued = kb + 1;
       }
     }
@@ -1553,11 +1566,25 @@ int run_tc_hybrid(const GemmDesc& d, const float2* A, const float2* B, float* C,
 }
 
 template <bool kTF32, int BN, int STAGES>
-int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_t* scratch, cudaStream_t st) {
+int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_t* scratch, cudaStream_t st,
+           int ksplit = 1) {
   const int64_t M = d.M, N2 = 2 * d.N, K2 = 2 * d.K, nb = d.batch;
   PlMaps maps;
   int r = prep_planes<kTF32>(d, A, B, scratch, BN, maps, st);
   if (r) return r;
+  // K split over CTAs: FP32 partial tiles after the planes in the scratch,
+  // summed (in FP64) into C in the consumer's layout by splitk_reduce
+  float* part = nullptr;
+  OutMap om = out_map(d);
+  const int64_t nout = nb * M * d.N;  // complex outputs
+  if (ksplit > 1) {
+    const uint64_t es = kTF32 ? 4 : 2;
+    const uint64_t planes = (uint64_t)nb * (M * K2 * 2 + N2 * K2 * 2) * es;
+    const uint64_t off = (planes + 255) / 256 * 256;
+    if (off + (uint64_t)ksplit * nout * 8 > d.scratch_elems * 8) return (int)cudaErrorInvalidValue;
+    part = (float*)(scratch + off);
+    om.ident = 1;
+  }
   const CUtensorMap &mAh = maps.ah, &mAl = maps.al, &mBh = maps.bh, &mBl = maps.bl;
   constexpr uint32_t STAGE_BYTES = 2 * BM * 128 + 2 * BN * 128;
   const size_t smem = 1024 + STAGES * STAGE_BYTES + (2 * STAGES + 5) * 8 + 16 + BN / 2 * 8;
@@ -1567,9 +1594,11 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
   for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
     int64_t cnt = nb - b0 < 65535 ? nb - b0 : 65535;
     dim3 grid((unsigned)tiles, 1, (unsigned)cnt);
-    tc_gemm_kernel<kTF32, BN, STAGES><<<grid, TcShape<BN>::kThreads, smem, st>>>(mAh, mAl, mBh, mBl, C, (int)M, (int)N2,
-                                                                     (int)K2, (int)b0, out_map(d));
+    grid.y = (unsigned)ksplit;
+    tc_gemm_kernel<kTF32, BN, STAGES><<<grid, TcShape<BN>::kThreads, smem, st>>>(
+        mAh, mAl, mBh, mBl, part ? part : C, (int)M, (int)N2, (int)K2, (int)b0, om, ksplit, 2 * nout);
   }
+  if (ksplit > 1) launch_splitk_reduce((const float2*)part, (float2*)C, ksplit, nout, M, d.N, out_map(d), st);
   return (int)cudaGetLastError();
 }
 
@@ -1615,6 +1644,22 @@ int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* 
   // 13: 128 x 256 (K <= 256) with A split on chip and B' from its planes;
   // 14, 15: 128 x 256 split on chip for any K (one TMEM slot + running sum),
   // 15 with the L2 prefetch
+  if (tile == 19) {
+    // plane tiles with K split over CTAs, for nodes with few output tiles
+    // and long K (K a multiple of 32)
+    if (d.K < 32 || d.K % 32 || d.M % BM || d.N < 32) return (int)cudaErrorInvalidValue;
+    const int bn = d.N >= 64 ? 128 : 64;
+    const int64_t tiles = (d.M / BM) * (2 * d.N / bn) * d.batch;
+    const int64_t nk = 2 * d.K / (tf32 ? 32 : 64);
+    int64_t ks = 2 * (int64_t)sm_count() / (tiles > 0 ? tiles : 1);
+    if (ks > nk) ks = nk;
+    if (ks > 65535) ks = 65535;
+    if (ks < 1) ks = 1;
+    if (tf32) return bn == 128 ? run_tc<true, 128, 3>(d, A, B, (float*)C, scratch, st, (int)ks)
+                               : run_tc<true, 64, 4>(d, A, B, (float*)C, scratch, st, (int)ks);
+    return bn == 128 ? run_tc<false, 128, 3>(d, A, B, (float*)C, scratch, st, (int)ks)
+                     : run_tc<false, 64, 4>(d, A, B, (float*)C, scratch, st, (int)ks);
+  }
   if (tile < 1 || tile > 15 || (tile == 2 && d.N < 64) || (tile == 3 && d.N < 128) ||
       (tile >= 4 && tile <= 8 && (d.transA || !d.transB)) || (tile >= 4 && tf32) ||
       ((tile == 4 || tile == 5 || tile == 10) && d.N < 64) ||

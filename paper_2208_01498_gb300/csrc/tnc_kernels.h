@@ -69,7 +69,9 @@ struct GemmDesc {
                         // (K <= 256): A split on chip, B' from its planes; 14, 15 N = 256 split
                         // on chip for any K (one TMEM slot + running sum; 15: with prefetch);
                         // 16 N = 64, 17 N = 128, 18 N = 256 (K <= 256): split on chip from FP32
-                        // tiles that TMA streams into a shared-memory ring (K even, also < 32).
+                        // tiles that TMA streams into a shared-memory ring (K even, also < 32);
+                        // 19: the plane tiles (N = 128, or 64 when N < 64 complex) with K split
+                        // over CTAs and an FP64 sum of the partials, for few tiles and long K.
                         // Narrow kernel: 0 unrolled for K, N in {1, 2, 4, 8, 16} with packed FP32
                         // FMAs (K-major A; else as 1), 1 one row per thread, 2 tiled with the output
                         // staged in address order (powers of two, K-major A; else as 1), 3 A tiles

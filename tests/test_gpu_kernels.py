@@ -295,6 +295,37 @@ def test_cgemm_f32_ring_tiles(tnc, shape, tile):
     _assert_close(got.cpu().numpy(), ref, "split_bf16", f"{shape} tile {tile}")
 
 
+@pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
+@pytest.mark.parametrize("shape,scatter", [((1, 256, 64, 65536), False), ((2, 128, 32, 8192), True),
+                                           ((1, 128, 128, 4096), True), ((4, 256, 32, 1024), False)])
+def test_cgemm_tc_split_k(tnc, shape, scatter, form):
+    """Tile 19: the plane tiles with K split over CTAs (FP32 partial tiles
+    summed in FP64 into the consumer's layout), for nodes with few output
+    tiles and long K; element by element against NumPy."""
+    batch, M, N, K = shape
+    rng = np.random.default_rng(M + N + K + batch)
+    A = _crand(batch * M * K, rng)
+    B = _crand(batch * K * N, rng)
+    ref = _ref(A, B, batch, M, N, K, 0, 1)
+    c_pos = None
+    if scatter:
+        nN, nM, nB = N.bit_length() - 1, M.bit_length() - 1, batch.bit_length() - 1
+        c_pos = rng.permutation(nN + nM + nB)
+    got = tnc.cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), batch, M, N, K, 0, 1, form,
+                    kernel="tc", tile=19, c_pos=c_pos).reshape(-1).cpu().numpy()
+    if scatter:
+        b, m, n = np.meshgrid(np.arange(batch), np.arange(M), np.arange(N), indexing="ij")
+        addr = np.zeros(b.shape, np.int64)
+        for i in range(nN):
+            addr |= ((n >> i) & 1) << int(c_pos[i])
+        for i in range(nM):
+            addr |= ((m >> i) & 1) << int(c_pos[nN + i])
+        for i in range(nB):
+            addr |= ((b >> i) & 1) << int(c_pos[nN + nM + i])
+        got = got[addr]
+    _assert_close(got.reshape(ref.shape), ref, form, f"{shape} split K")
+
+
 @pytest.mark.parametrize("kernel", ["simt_128x64", "simt_64x32", "simt_32x128"])
 @pytest.mark.parametrize("shape", [(1, 64, 64, 4096, 0, 1), (2, 100, 36, 1000, 1, 0), (1, 32, 128, 600, 0, 0)])
 def test_cgemm_cuda_cores_split_k_small_grid(tnc, kernel, shape):
