@@ -518,7 +518,7 @@ def _make_workload(args, rank):
     request, sliced under 180 GB."""
     nsteps = args.warmup + args.steps
     if args.workload == "rand2d_8x8_d16":
-        gl, _ = C.config_circuit(1, args.seed + rank)
+        gl, _ = C.workload("rand2d_8x8_d16", args.seed + rank)
         bits = np.stack([C.random_bitstrings(gl.n_qubits, 1, 7919 * (args.seed + rank) + i) for i in range(nsteps)])
         return "rand2d_8x8_d16_1amp", gl, bits, dict(max_batch=1, mem_cap_bytes=180 * 10**9)
     gl, bits = _workload(args.seed + rank, nsteps, args.rows, args.cols)
@@ -848,7 +848,7 @@ def run_ours(args):
                               "sample": f"{na} bitstrings over {ncores} spawned processes (one thread each), "
                                         f"{dta:.1f} s"}}
     elif rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_oracle_cfg1_reduction()
+        line["cpu_baseline"] = _cpu_oracle_rand2d_8x8_twin()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -856,13 +856,13 @@ def run_ours(args):
     return 0
 
 
-def _cpu_oracle_cfg1_reduction():
+def _cpu_oracle_rand2d_8x8_twin():
     """No CPU oracle reaches a random 64-qubit amplitude; the reported baseline
     is the oracle's CH form on the workload's Clifford twin (same 8 x 8 layout
     and depth-16 schedule, Clifford single-qubit gates), one thread, on a
     bounded sample of seed-random bitstrings."""
     from oracle.stabilizer import stabilizer_amplitudes
-    gl, _ = C.config_circuit(1, 0, clifford=True)
+    gl, _ = C.workload("rand2d_8x8_d16", 0, clifford=True)
     n, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < 10.0 and n < 256:
         stabilizer_amplitudes(gl, C.random_bitstrings(64, 1, 1000 + n))

@@ -58,7 +58,7 @@ __all__ = [
     "iqp", "layered_3d", "ghz", "mirror", "doubled", "pauli_ops", "projector_ops",
     "iqp_paper", "sycamore_periods", "cavity_3d", "fuse_diagonal",
     "random_bitstrings", "serving_pool",
-    "config_circuit", "H", "S", "CZ", "X", "Y", "sqrt_pauli", "fsim",
+    "workload", "WORKLOADS", "H", "S", "CZ", "X", "Y", "sqrt_pauli", "fsim",
 ]
 
 # ---------------------------------------------------------------- matrices
@@ -611,31 +611,34 @@ def serving_pool(seed: int = 0, n_2d: int = 10):
     return pool
 
 
-def config_circuit(cfg: int, seed: int = 0, clifford: bool = False, reduced: bool = False):
-    """The benchmark workloads by number: returns ``(gatelist, info)`` where
+WORKLOADS = ("rand2d_4x4_d8", "rand2d_8x8_d16", "sycamore_7x7_c14", "iqp_5x8")
+
+
+def workload(name: str, seed: int = 0, clifford: bool = False, reduced: bool = False):
+    """The benchmark workloads by name: returns ``(gatelist, info)`` where
     ``info`` holds the bitstrings / open qubits a request asks for.
 
-    * 0: 4x4 depth-8 random 2D circuit, <0...0|C|0...0>.
-    * 1: 8x8 depth-16 random 2D circuit (``reduced``: 6x6 depth 16), one
-      seed-random bitstring.
-    * 2: 7x7 Sycamore-type, 14 cycles, 6 seed-random open qubits and 43 fixed
-      seed-random bits (``reduced``: 4x4, 6 open).
-    * 3: 5x8 IQP, 256 seed-random bitstrings (``reduced``: 4x5).
+    * rand2d_4x4_d8: 4x4 depth-8 random 2D circuit, <0...0|C|0...0>.
+    * rand2d_8x8_d16: 8x8 depth-16 random 2D circuit (``reduced``: 6x6 depth
+      16), one seed-random bitstring.
+    * sycamore_7x7_c14: 7x7 Sycamore-type, 14 cycles, 6 seed-random open
+      qubits and 43 fixed seed-random bits (``reduced``: 4x4, 6 open).
+    * iqp_5x8: 5x8 IQP, 256 seed-random bitstrings (``reduced``: 4x5).
     """
-    if cfg == 0:
+    if name == "rand2d_4x4_d8":
         gl = random_2d(4, 4, 8, seed, clifford)
         return gl, dict(bits=np.zeros((1, 16), np.uint8), open=np.zeros(0, np.int32))
-    if cfg == 1:
+    if name == "rand2d_8x8_d16":
         L = 6 if reduced else 8
         gl = random_2d(L, L, 16, seed, clifford)
         return gl, dict(bits=random_bitstrings(L * L, 1, seed), open=np.zeros(0, np.int32))
-    if cfg == 2:
+    if name == "sycamore_7x7_c14":
         L = 4 if reduced else 7
         gl = sycamore(L, 14, seed, clifford)
         return gl, dict(bits=random_bitstrings(L * L, 1, seed),
                         open=random_open_qubits(L * L, 6, seed))
-    if cfg == 3:
+    if name == "iqp_5x8":
         r, c = (4, 5) if reduced else (5, 8)
         gl = iqp(r, c, seed, clifford)
         return gl, dict(bits=random_bitstrings(r * c, 256, seed), open=np.zeros(0, np.int32))
-    raise ValueError(cfg)
+    raise ValueError(name)

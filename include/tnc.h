@@ -376,7 +376,7 @@ int tnc_contract_amplitudes_static(tnc_plan_t* plan, const uint8_t* bits, int ba
                                    void* cuda_stream);
 
 /* Several requests, possibly on different circuits, contracted together in
- * one stream (the batching of small requests; north_star "Batching").  Their
+ * one stream, so that many small requests share launches.  Their
  * node programs advance in lockstep, in waves (wave w = step w of every
  * request that has one); in each wave the narrow nodes of all requests run as
  * one grouped launch and their CUDA-core cGEMM nodes as one grouped launch

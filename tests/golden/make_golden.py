@@ -1,13 +1,13 @@
 """Writes the stored expected values under tests/golden/ by calling only the
 FP64 oracle (never the CUDA path).
 
-* cfg1_6x6_sidewise.json -- the 6 x 6 depth-16 reduction of the 8 x 8 random
+* rand2d_6x6_d16_sidewise.json -- the 6 x 6 depth-16 reduction of the 8 x 8 random
   circuit workload (same generation rules, seed 0), one amplitude of a
   seed-random bitstring, by the oracle's side-wise (left-to-right) FP64
   contraction (the naive-order scheme of the paper's Thm. 2 discussion).
   Takes tens of minutes and ~30 GB of host memory.
 
-Usage: python tests/golden/make_golden.py [cfg1_6x6]
+Usage: python tests/golden/make_golden.py [rand2d_6x6_d16]
 """
 import json
 import os
@@ -23,25 +23,25 @@ import circuits as C  # noqa: E402
 import oracle as O  # noqa: E402
 
 
-def cfg1_6x6(seed: int = 0):
-    gl, info = C.config_circuit(1, seed, reduced=True)
+def rand2d_6x6_d16(seed: int = 0):
+    gl, info = C.workload("rand2d_8x8_d16", seed, reduced=True)
     t0 = time.time()
     a = O.sidewise_amplitudes(gl, info["bits"], order="columns")
     dt = time.time() - t0
     out = {
         "description": "6x6 depth-16 random circuit (Haar 1q, CZ on brick patterns ABCD), seed %d; amplitude "
                        "<x|C|0> of the seed-random bitstring x by the oracle's side-wise FP64 contraction" % seed,
-        "generator": "circuits.config_circuit(1, %d, reduced=True)" % seed,
+        "generator": "circuits.workload('rand2d_8x8_d16', %d, reduced=True)" % seed,
         "bits": info["bits"][0].tolist(),
         "amplitude": [float(a[0, 0].real), float(a[0, 0].imag)],
         "oracle_seconds": round(dt, 1),
     }
-    with open(os.path.join(HERE, "cfg1_6x6_sidewise.json"), "w") as f:
+    with open(os.path.join(HERE, "rand2d_6x6_d16_sidewise.json"), "w") as f:
         json.dump(out, f, indent=1)
     print(out)
 
 
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["cfg1_6x6"]
-    if "cfg1_6x6" in which:
-        cfg1_6x6()
+    which = sys.argv[1:] or ["rand2d_6x6_d16"]
+    if "rand2d_6x6_d16" in which:
+        rand2d_6x6_d16()

@@ -15,7 +15,7 @@ SLICING_CAPS = [(1 << 16, 0), (1 << 15, 3), (1 << 14, 6)]
 PARTIAL_CASE = dict(open=[1], batch=2, cap=1 << 16, max_group_log2=0)
 
 # the 6 x 6 depth-16 reduction of the 8 x 8 depth-16 workload: cap that slices it
-CFG1_REDUCED_CAP = 256 << 20
+RAND6X6_D16_CAP = 256 << 20
 
 # the 8 x 8 depth-16 workload at full size
-CFG1_CAP = 180 * 10**9
+RAND8X8_D16_CAP = 180 * 10**9

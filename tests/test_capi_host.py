@@ -80,8 +80,8 @@ def test_unsatisfiable_memory_cap():
 
 
 @pytest.mark.parametrize("oq,batch", [([], 1), ([1, 5], 1), ([], 4), ([3, 9, 12], 3)])
-def test_tree_and_program_match_oracle_cfg0(oq, batch):
-    gl, _ = C.config_circuit(0, 0)
+def test_tree_and_program_match_oracle_rand2d_4x4_d8(oq, batch):
+    gl, _ = C.workload("rand2d_4x4_d8", 0)
     p = tnc.Plan(tnc.Network(gl), open_qubits=oq, max_batch=batch)
     e = p.export()
     bits = C.random_bitstrings(16, batch, 3)
@@ -158,7 +158,7 @@ def test_grouped_slices_run_as_batch():
 
 def test_plan_cost_equals_counted_work():
     """Sum over nodes of 2 M (Eq. 3) equals the work the program issues."""
-    gl, _ = C.config_circuit(0, 1)
+    gl, _ = C.workload("rand2d_4x4_d8", 1)
     p = tnc.Plan(tnc.Network(gl), open_qubits=[4], max_batch=2)
     e = p.export()
     eq3 = sum(2 * 2.0 ** n["cost_log2"] for n in e["nodes"] if n["left"] >= 0)
@@ -181,7 +181,7 @@ def test_tree_order_independence_on_host():
 
 
 def test_every_leaf_and_label_is_used_once():
-    gl, _ = C.config_circuit(2, 0, reduced=True)
+    gl, _ = C.workload("sycamore_7x7_c14", 0, reduced=True)
     e = tnc.Plan(tnc.Network(gl), open_qubits=[1, 3]).export()
     leaves_in_tree = sorted(n["leaf"] for n in e["nodes"] if n["left"] < 0)
     assert leaves_in_tree == list(range(len(e["leaves"])))

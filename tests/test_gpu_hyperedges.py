@@ -36,8 +36,8 @@ def _run(tnc, gl, bits, oq, form, **kw):
 
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("seed", [0, 1])
-def test_config0_hyperedges(tnc, form, seed):
-    gl, info = C.config_circuit(0, seed)
+def test_rand2d_4x4_d8_hyperedges(tnc, form, seed):
+    gl, info = C.workload("rand2d_4x4_d8", seed)
     bits = C.random_bitstrings(16, 4, seed)
     ref = O.statevector_amplitudes(gl, bits, [3])
     got, _ = _run(tnc, gl, bits, [3], form)
@@ -45,16 +45,16 @@ def test_config0_hyperedges(tnc, form, seed):
 
 
 @pytest.mark.parametrize("form", FORMS)
-def test_config3_full_size_hyperedges(tnc, form):
-    gl, info = C.config_circuit(3, 0)
+def test_iqp_5x8_full_size_hyperedges(tnc, form):
+    gl, info = C.workload("iqp_5x8", 0)
     ref = O.iqp_transfer_amplitudes(gl, info["bits"])
     got, p = _run(tnc, gl, info["bits"], [], form)
     assert p.report["tree_cost_log2"] < 30  # against about 2^34.6 without hyper-edges
     assert O.rel_error(got, ref, 40).max() <= TOL[form]
 
 
-def test_config3_clifford_twin_hyperedges(tnc):
-    gl, info = C.config_circuit(3, 1, clifford=True)
+def test_iqp_5x8_clifford_twin_hyperedges(tnc):
+    gl, info = C.workload("iqp_5x8", 1, clifford=True)
     bits = info["bits"][:32]
     ref = stabilizer_amplitudes(gl, bits)
     got, _ = _run(tnc, gl, bits, [], "split_bf16")

@@ -43,8 +43,8 @@ def _check(got, ref, n, form="fp32"):
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_config0_single_amplitude(tnc, seed):
-    gl, info = C.config_circuit(0, seed)
+def test_rand2d_4x4_d8_single_amplitude(tnc, seed):
+    gl, info = C.workload("rand2d_4x4_d8", seed)
     ref = O.statevector_amplitudes(gl, info["bits"])
     got, _ = _run(tnc, gl, info["bits"])
     _check(got, ref, 16)
@@ -153,23 +153,23 @@ def test_partial_slice_groups_add_up(tnc):
     assert O.rel_error((a + b).cpu().numpy(), full.cpu().numpy(), 20).max() < 1e-9
 
 
-def test_config0_clifford_twin(tnc):
-    gl, _ = C.config_circuit(0, 3, clifford=True)
+def test_rand2d_4x4_d8_clifford_twin(tnc):
+    gl, _ = C.workload("rand2d_4x4_d8", 3, clifford=True)
     bits = C.random_bitstrings(16, 8, 2)
     ref = stabilizer_amplitudes(gl, bits, [0, 5])
     got, _ = _run(tnc, gl, bits, [0, 5])
     _check(got, ref, 16)
 
 
-def test_config2_reduced(tnc):
-    gl, info = C.config_circuit(2, 0, reduced=True)
+def test_sycamore_4x4_c14(tnc):
+    gl, info = C.workload("sycamore_7x7_c14", 0, reduced=True)
     ref = O.statevector_amplitudes(gl, info["bits"], info["open"])
     got, _ = _run(tnc, gl, info["bits"], info["open"])
     _check(got, ref, 16)
 
 
 @pytest.fixture(scope="module")
-def config2_5x5():
+def sycamore_5x5_c14():
     """The Sycamore-type rules on a 5 x 5 grid (14 cycles of fSim(pi/2, pi/6)
     on the staggered ABCD matchings, 6 seed-random open qubits, one
     seed-random bitstring for the other 19): 25 qubits, within the state
@@ -181,22 +181,22 @@ def config2_5x5():
 
 
 @pytest.mark.parametrize("form", ["fp32", "split_bf16", "3xtf32"])
-def test_config2_reduced_5x5(tnc, config2_5x5, form):
-    gl, bits, oq, ref = config2_5x5
+def test_sycamore_5x5_c14(tnc, sycamore_5x5_c14, form):
+    gl, bits, oq, ref = sycamore_5x5_c14
     got, p = _run(tnc, gl, bits, oq, form=form)
     assert got.shape == (1, 64)
     _check(got, ref, 25, form)
 
 
-def test_config3_reduced_wht(tnc):
-    gl, info = C.config_circuit(3, 0, reduced=True)
+def test_iqp_4x5_wht(tnc):
+    gl, info = C.workload("iqp_5x8", 0, reduced=True)
     ref = O.iqp_wht_amplitudes(gl, info["bits"])
     got, _ = _run(tnc, gl, info["bits"])
     _check(got, ref, 20)
 
 
 @pytest.mark.parametrize("L", [4, 5])
-def test_config4_layered_instances(tnc, L):
+def test_serving_pool_layered_instances(tnc, L):
     gl = C.layered_3d(L, 4, seed=100 + L)
     bits = C.random_bitstrings(L * L, 16, 1)
     ref = O.statevector_amplitudes(gl, bits)
@@ -204,16 +204,16 @@ def test_config4_layered_instances(tnc, L):
     _check(got, ref, L * L)
 
 
-def test_config3_full_size_transfer_matrix(tnc):
+def test_iqp_5x8_full_size_transfer_matrix(tnc):
     """40 qubits, 256 bitstrings: the benchmark workload, FP32 form."""
-    gl, info = C.config_circuit(3, 0)
+    gl, info = C.workload("iqp_5x8", 0)
     ref = O.iqp_transfer_amplitudes(gl, info["bits"])
     got, _ = _run(tnc, gl, info["bits"])
     _check(got, ref, 40)
 
 
-def test_config3_full_size_clifford_twin(tnc):
-    gl, info = C.config_circuit(3, 1, clifford=True)
+def test_iqp_5x8_full_size_clifford_twin(tnc):
+    gl, info = C.workload("iqp_5x8", 1, clifford=True)
     bits = info["bits"][:64]
     ref = stabilizer_amplitudes(gl, bits)
     got, _ = _run(tnc, gl, bits)

@@ -20,12 +20,12 @@ import pytest
 
 import circuits as C
 import oracle as O
-from plan_cases import CFG1_REDUCED_CAP
+from plan_cases import RAND6X6_D16_CAP
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cfg1_6x6_sidewise.json")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "rand2d_6x6_d16_sidewise.json")
 TOL = {"fp32": 1e-5, "3xtf32": 1e-5, "split_bf16": 1e-4}
 
 
@@ -37,7 +37,7 @@ def case():
         pytest.skip("golden amplitude not generated")
     with open(GOLDEN) as f:
         g = json.load(f)
-    gl, info = C.config_circuit(1, 0, reduced=True)
+    gl, info = C.workload("rand2d_8x8_d16", 0, reduced=True)
     bits = np.asarray(g["bits"], np.uint8)[None, :]
     assert np.array_equal(bits, info["bits"][:1])  # the generator still yields the stored case
     ref = np.array([[complex(*g["amplitude"])]])
@@ -46,10 +46,10 @@ def case():
 
 
 @pytest.mark.parametrize("form", ["fp32", "split_bf16", "3xtf32"])
-def test_cfg1_6x6_depth16_against_sidewise_oracle(case, form):
+def test_rand2d_6x6_d16_against_sidewise_oracle(case, form):
     tnc, gl, bits, ref = case
-    p = tnc.Plan(tnc.Network(gl), max_batch=1, form=form, mem_cap_bytes=CFG1_REDUCED_CAP, ssa_trials=64)
-    assert p.ws_bytes < 1.5 * CFG1_REDUCED_CAP
+    p = tnc.Plan(tnc.Network(gl), max_batch=1, form=form, mem_cap_bytes=RAND6X6_D16_CAP, ssa_trials=64)
+    assert p.ws_bytes < 1.5 * RAND6X6_D16_CAP
     assert p.report["n_sliced"] >= 1
     got = tnc.contract_amplitudes(p, bits).cpu().numpy()
     torch.cuda.synchronize()

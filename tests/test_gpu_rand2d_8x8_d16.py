@@ -17,13 +17,13 @@ import pytest
 import circuits as C
 import oracle as O
 from oracle.stabilizer import stabilizer_amplitudes
-from plan_cases import CFG1_CAP
+from plan_cases import RAND8X8_D16_CAP
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {"3xtf32": 1e-5, "split_bf16": 1e-4}
-CAP = CFG1_CAP
+CAP = RAND8X8_D16_CAP
 
 
 @pytest.fixture(scope="module")
@@ -61,8 +61,8 @@ def _nonzero_clifford_bits(gl, seed):
 
 
 @pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
-def test_cfg1_clifford_twin_full_size(tnc, form):
-    gl, _ = C.config_circuit(1, 0, clifford=True)
+def test_rand2d_8x8_d16_clifford_twin_full_size(tnc, form):
+    gl, _ = C.workload("rand2d_8x8_d16", 0, clifford=True)
     bits, ref = _nonzero_clifford_bits(gl, 0)
     got, rep = _amp(tnc, gl, bits, form)
     assert rep["n_sliced"] >= 1
@@ -70,8 +70,8 @@ def test_cfg1_clifford_twin_full_size(tnc, form):
     assert err <= TOL[form], f"{form}: rel error {err:.3g} (|a_ref| = {abs(ref[0, 0]):.3g})"
 
 
-def test_cfg1_random_circuit_forms_agree(tnc):
-    gl, info = C.config_circuit(1, 0)
+def test_rand2d_8x8_d16_forms_agree(tnc):
+    gl, info = C.workload("rand2d_8x8_d16", 0)
     bits = info["bits"][:1]
     a_bf16, _ = _amp(tnc, gl, bits, "split_bf16")
     a_tf32, _ = _amp(tnc, gl, bits, "3xtf32")

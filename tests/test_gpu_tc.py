@@ -45,10 +45,10 @@ def test_single_tensor_core_node(tnc, form):
 
 
 @pytest.mark.parametrize("form", ["split_bf16", "3xtf32"])
-def test_config3_full_size(tnc, form):
+def test_iqp_5x8_full_size(tnc, form):
     """The benchmark workload (40 qubits, 256 bitstrings) against the
     transfer-matrix closed form, and against the FP32 form."""
-    gl, info = C.config_circuit(3, 0)
+    gl, info = C.workload("iqp_5x8", 0)
     ref = O.iqp_transfer_amplitudes(gl, info["bits"])
     got, p = _run(tnc, gl, info["bits"], form)
     assert _n_tc(p) >= 3
@@ -94,7 +94,7 @@ def test_bounded_wait_gives_up_and_device_stays_usable(tnc):
     assert flag.value == 0
 
 
-def test_config3_full_size_autotuned_as_benchmarked(tnc):
+def test_iqp_5x8_full_size_autotuned_as_benchmarked(tnc):
     """The benchmark's own plan (5 x 8 IQP, 256 bitstrings, split-BF16, the
     same planner seed and trials), autotuned as the benchmark does, against
     the transfer-matrix closed form: the kernel variants the benchmark times

@@ -118,8 +118,8 @@ def test_sidewise_sycamore_reduction():
     assert np.allclose(a, b, atol=1e-15, rtol=1e-12)
 
 
-def test_config0_statevector_vs_sidewise():
-    gl, info = C.config_circuit(0, 0)
+def test_rand2d_4x4_d8_statevector_vs_sidewise():
+    gl, info = C.workload("rand2d_4x4_d8", 0)
     a = O.statevector_amplitudes(gl, info["bits"])
     b = O.sidewise_amplitudes(gl, info["bits"])
     assert abs(a - b).max() < 1e-15
@@ -146,9 +146,9 @@ def test_stabilizer_random_clifford_vs_statevector(seed):
         assert np.allclose(a, s, atol=1e-13)
 
 
-@pytest.mark.parametrize("cfg", [0, 2, 3])
-def test_stabilizer_twins_reduced_vs_statevector(cfg):
-    gl, info = C.config_circuit(cfg, 1, clifford=True, reduced=True)
+@pytest.mark.parametrize("name", ["rand2d_4x4_d8", "sycamore_7x7_c14", "iqp_5x8"])
+def test_stabilizer_twins_reduced_vs_statevector(name):
+    gl, info = C.workload(name, 1, clifford=True, reduced=True)
     bits = info["bits"][:6]
     a = O.statevector_amplitudes(gl, bits, info["open"])
     s = stabilizer_amplitudes(gl, bits, info["open"])
@@ -157,7 +157,7 @@ def test_stabilizer_twins_reduced_vs_statevector(cfg):
 
 def test_clifford_amplitude_values_are_exact():
     # |a| in {0, 2^{-r/2}}, phase in (pi/4) Z
-    gl, info = C.config_circuit(2, 0, clifford=True, reduced=True)
+    gl, info = C.workload("sycamore_7x7_c14", 0, clifford=True, reduced=True)
     a = stabilizer_amplitudes(gl, info["bits"], info["open"]).ravel()
     nz = a[np.abs(a) > 1e-12]
     assert len(nz) > 0
@@ -168,7 +168,7 @@ def test_clifford_amplitude_values_are_exact():
 
 
 def test_iqp_closed_forms_agree():
-    gl, _ = C.config_circuit(3, 2, reduced=True)
+    gl, _ = C.workload("iqp_5x8", 2, reduced=True)
     bits = C.random_bitstrings(20, 32, 3)
     a = O.statevector_amplitudes(gl, bits)
     b = O.iqp_wht_amplitudes(gl, bits)
@@ -178,7 +178,7 @@ def test_iqp_closed_forms_agree():
 
 
 def test_iqp_commuting_gate_reorder():
-    gl, _ = C.config_circuit(3, 4, reduced=True)
+    gl, _ = C.workload("iqp_5x8", 4, reduced=True)
     n = gl.n_qubits
     mid = gl.gates[n:-n]
     rng = np.random.default_rng(0)
@@ -189,7 +189,7 @@ def test_iqp_commuting_gate_reorder():
 
 
 def test_iqp_full_size_twin_transfer_vs_stabilizer():
-    gl, info = C.config_circuit(3, 0, clifford=True)
+    gl, info = C.workload("iqp_5x8", 0, clifford=True)
     bits = info["bits"][:64]
     a = O.iqp_transfer_amplitudes(gl, bits)
     s = stabilizer_amplitudes(gl, bits)

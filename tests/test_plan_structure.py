@@ -12,7 +12,7 @@ refused.
 import pytest
 
 import circuits as C
-from plan_cases import CFG1_CAP, CFG1_REDUCED_CAP, GROUPED_CASE, PARTIAL_CASE, SLICING_CAPS, TC_CASE
+from plan_cases import RAND8X8_D16_CAP, RAND6X6_D16_CAP, GROUPED_CASE, PARTIAL_CASE, SLICING_CAPS, TC_CASE
 
 tnc = pytest.importorskip("paper_2208_01498_gb300.tnc")
 
@@ -48,26 +48,26 @@ def test_grouped_case_groups_a_label():
 
 
 @pytest.mark.parametrize("form", ["fp32", "split_bf16", "3xtf32"])
-def test_cfg1_reduction_slices_under_its_cap(form):
-    gl, _ = C.config_circuit(1, 0, reduced=True)
-    p = tnc.Plan(tnc.Network(gl), max_batch=1, form=form, mem_cap_bytes=CFG1_REDUCED_CAP, ssa_trials=64)
+def test_rand2d_6x6_d16_slices_under_its_cap(form):
+    gl, _ = C.workload("rand2d_8x8_d16", 0, reduced=True)
+    p = tnc.Plan(tnc.Network(gl), max_batch=1, form=form, mem_cap_bytes=RAND6X6_D16_CAP, ssa_trials=64)
     assert p.report["n_sliced"] >= 1
-    assert p.ws_bytes < 1.5 * CFG1_REDUCED_CAP
+    assert p.ws_bytes < 1.5 * RAND6X6_D16_CAP
     if form != "fp32":
         assert _n_tc(p) >= 1
 
 
 @pytest.mark.parametrize("clifford", [False, True])
-def test_cfg1_full_size_plans_under_180_gb(clifford):
+def test_rand2d_8x8_d16_plans_under_180_gb(clifford):
     """The 8 x 8 depth-16 workload: sliced under 180 GB at a small multiple of
     its unsliced tree's work (about 5e15 real flops, against 8e18 for the
     greedy slicer over the plain separator tree)."""
-    gl, _ = C.config_circuit(1, 0, clifford=clifford)
+    gl, _ = C.workload("rand2d_8x8_d16", 0, clifford=clifford)
     net = tnc.Network(gl)
     for form in ("split_bf16", "3xtf32"):
-        p = tnc.Plan(net, max_batch=1, form=form, mem_cap_bytes=CFG1_CAP, ssa_trials=64)
+        p = tnc.Plan(net, max_batch=1, form=form, mem_cap_bytes=RAND8X8_D16_CAP, ssa_trials=64)
         r = p.report
-        assert r["ws_bytes"] <= CFG1_CAP
+        assert r["ws_bytes"] <= RAND8X8_D16_CAP
         assert 1e15 < r["real_flops"] < 1e16, r["real_flops"]
         assert r["n_sliced"] >= 1
         unsliced = 4 * 2.0 ** r["tree_cost_log2"]  # real flops of the tree without slicing
