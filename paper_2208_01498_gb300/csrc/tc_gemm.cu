@@ -1014,6 +1014,8 @@ __global__ void __launch_bounds__(Cf::kThreads, 1)
         break;
       }
       ft_load<Cf>(R, ring + f * Cf::kF32StageBytes, ct);
+      // reads of the ring stage ordered before the producer's next TMA write into it
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&fempty[f])) : "memory");
       if (++f == SF) {
         f = 0;
@@ -1803,6 +1805,9 @@ __global__ void __launch_bounds__(kNtRows, 2)
         an[2 * c + 1] = make_float2(-v.w, -v.w);
       }
     }
+    // the stage is rewritten next by TMA (the async proxy): order this
+    // thread's reads of it before that write, then meet at the barrier
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (__syncthreads_or(!ok)) {
       failed_at = j;
       break;
