@@ -327,9 +327,11 @@ def test_cgemm_tc_split_k(tnc, shape, scatter, form):
 
 
 @pytest.mark.parametrize("kernel", ["simt_128x64", "simt_64x32", "simt_32x128"])
-@pytest.mark.parametrize("shape", [(1, 64, 64, 4096, 0, 1), (2, 100, 36, 1000, 1, 0), (1, 32, 128, 600, 0, 0)])
+@pytest.mark.parametrize("shape", [(1, 64, 64, 4096, 0, 1), (2, 100, 36, 1000, 1, 0), (1, 32, 128, 600, 0, 0),
+                                   (256, 32, 16, 2048, 0, 1)])
 def test_cgemm_cuda_cores_split_k_small_grid(tnc, kernel, shape):
-    """Nodes with fewer output tiles than SMs and K >= 512 run the CUDA-core
+    """Nodes with fewer output tiles than SMs and K >= 512, or one to four
+    waves of tiles and K >= 2048 (batch 256, M 32, N 16), run the CUDA-core
     kernels with K split over blocks and an FP64 reduction: every tile shape,
     ragged sizes included, against NumPy; the power-of-two shape also with a
     scattered output."""
