@@ -416,7 +416,7 @@ def op_counts(reps: int = 10, seed: int = 0):
 
     def ssa(gl):
         ops = C.projector_ops(range(gl.n_qubits), [0] * gl.n_qubits)
-        return tnc.Plan(tnc.Network(C.doubled(gl, ops)), seed=1).report["tree_cost_log2"]
+        return tnc.Plan(tnc.Network(C.doubled(gl, ops)), seed=1, tree_only=True).report["tree_cost_log2"]
 
     families = {
         "iqp_paper (T = L^2, gamma = 3)": ([3, 4, 5, 6, 7, 8], lambda L, s: C.iqp_paper(L, s)),

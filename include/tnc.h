@@ -94,6 +94,11 @@ typedef struct {
                                re-association of windows of up to this many subtrees (an addition to
                                the paper's method; it never raises the Eq. 3 cost nor enlarges the
                                largest intermediate) */
+  int tree_only;            /* 1: build and report the contraction tree only (Eq. 3 cost in
+                               tree_cost_log2 and paper_ops, n_leaves, max_rank; tnc_plan_export_json
+                               gives the tree): no slicing and no device program, so networks whose
+                               intermediates exceed the executor's 48 binary indices can be costed;
+                               tnc_plan_upload and every contraction call return TNC_ESTATE */
 } tnc_plan_opts;
 
 #define TNC_EMBED_AUTO 0

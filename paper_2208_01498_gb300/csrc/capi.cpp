@@ -291,7 +291,9 @@ int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** o
   for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cands[a].cost < cands[b].cost - 1e-9; });
   int pick = -1;
-  if (!opts->mem_cap_bytes) {
+  if (opts->tree_only) {
+    pick = idx[0];  // nothing is compiled: the cheapest tree whatever its largest intermediate
+  } else if (!opts->mem_cap_bytes) {
     for (int i : idx)
       if (cands[i].max_rank <= kMaxRank) {
         pick = i;
@@ -322,6 +324,17 @@ int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** o
     p.rep.n_refined = c.n_refined;
   }
   p.rep.tree_cost_log2 = tree_cost_log2(p.tree);
+  if (opts->tree_only) {
+    // the tree and its Eq. 3 cost only: no slicing, no device program
+    p.tree_only = true;
+    p.rep.paper_ops = std::exp2(p.rep.tree_cost_log2);
+    p.rep.n_leaves = (int)p.net.leaves.size();
+    p.rep.max_rank = tree_max_rank(p.tree);
+    p.rep.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) *rep = p.rep;
+    *out = tp;
+    return TNC_OK;
+  }
   int rc = plan_slices(p, opts->mem_cap_bytes);
   if (rc == TNC_OK) rc = compile_program(p);
   if (rc == TNC_OK && opts->mem_cap_bytes && p.prog.ws_bytes > opts->mem_cap_bytes * 1.5 + (1 << 20)) {
@@ -489,6 +502,10 @@ int tnc_plan_upload(tnc_plan_t* plan, void* stream) {
     return TNC_EINVAL;
   }
   Plan& p = plan->p;
+  if (p.tree_only) {
+    set_error("tnc_plan_upload: the plan was built with tree_only and has no device program");
+    return TNC_ESTATE;
+  }
   std::lock_guard<std::mutex> lk(p.mu);
   int dev = 0;
   cudaError_t e;
@@ -829,6 +846,10 @@ int tnc_plan_autotune(tnc_plan_t* plan, void* d_ws, size_t ws_bytes, void* strea
     return TNC_EINVAL;
   }
   Plan& p = plan->p;
+  if (p.tree_only) {
+    set_error("tnc_plan_autotune: the plan was built with tree_only and has no device program");
+    return TNC_ESTATE;
+  }
   if (ws_bytes < p.prog.ws_bytes || ((uintptr_t)d_ws & 255)) {
     set_error("tnc_plan_autotune: workspace too small or not 256-byte aligned");
     return ws_bytes < p.prog.ws_bytes ? TNC_ENOMEM : TNC_EINVAL;

@@ -137,6 +137,7 @@ struct Plan {
   std::vector<int> sliced_serial, sliced_par;
   Program prog;
   tnc_plan_report rep{};
+  bool tree_only = false;  // built with tnc_plan_opts.tree_only: no device program
   // per-step CUDA-event profiling
   bool profiling = false;
   struct ProfRec {

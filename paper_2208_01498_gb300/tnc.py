@@ -57,7 +57,7 @@ class PlanOpts(C.Structure):
                 ("mem_cap_bytes", C.c_size_t), ("form", C.c_int), ("seed", C.c_uint64),
                 ("ssa_trials", C.c_int), ("leaf_size", C.c_int), ("max_group_log2", C.c_int),
                 ("use_graph", C.c_int), ("embedding", C.c_int), ("n_starts", C.c_int),
-                ("refine_window", C.c_int)]
+                ("refine_window", C.c_int), ("tree_only", C.c_int)]
 
 
 class PlanReport(C.Structure):
@@ -216,7 +216,7 @@ class Plan:
     def __init__(self, net: Network, open_qubits=(), max_batch: int = 1, mem_cap_bytes: int = 0,
                  form: str = "fp32", seed: int = 1, ssa_trials: int = 32, leaf_size: int = 8,
                  max_group_log2: int = 6, use_graph: bool = True, embedding: str = "auto",
-                 n_starts: int = 0, refine_window: int | None = None):
+                 n_starts: int = 0, refine_window: int | None = None, tree_only: bool = False):
         o = PlanOpts()
         lib.tnc_plan_opts_default(C.byref(o))
         self._open = np.ascontiguousarray(sorted(int(q) for q in open_qubits), np.int32)
@@ -235,6 +235,7 @@ class Plan:
             o.n_starts = int(n_starts)
         if refine_window is not None:
             o.refine_window = int(refine_window)
+        o.tree_only = int(bool(tree_only))
         rep = PlanReport()
         h = C.c_void_p()
         _check(lib.tnc_plan(net.handle, C.byref(o), C.byref(h), C.byref(rep)), "tnc_plan")

@@ -7,7 +7,7 @@ they name (a tcgen05 step, sliced and grouped labels) and pin the planner's
 invariants: the refinement never raises the Eq. 3 cost nor enlarges the
 largest intermediate, slicing meets the cap, the 8 x 8 depth-16 workload
 plans under 180 GB, and trees beyond the executor's 48 binary indices are
-refused.
+refused for execution (and costed with tree_only).
 """
 import pytest
 
@@ -114,6 +114,26 @@ def test_rank_beyond_the_executor_is_refused():
         tnc.Plan(net, max_batch=16, n_starts=1)
     assert ei.value.status == tnc.TNC_ENOMEM
     assert "binary indices" in str(ei.value)
+
+
+def test_tree_only_costs_trees_beyond_the_executor():
+    """tree_only: the same network gets its tree and Eq. 3 cost (no device
+    program, so no rank limit), costed no higher than any compiled tree the
+    planner could pick; the plan refuses upload and autotuning."""
+    net = tnc.Network(C.random_2d(10, 10, 20, 3))
+    p = tnc.Plan(net, max_batch=16, n_starts=1, tree_only=True)
+    r = p.report
+    assert r["max_rank"] > 48 and 0 < r["tree_cost_log2"] < 200
+    assert abs(r["paper_ops"] - 2.0 ** r["tree_cost_log2"]) <= 1e-9 * r["paper_ops"]
+    assert r["ws_bytes"] == 0 and r["n_launches"] == 0
+    e = p.export()
+    assert len(e["nodes"]) == 2 * r["n_leaves"] - 1 and e["program"]["ws_bytes"] == 0
+    assert tnc.lib.tnc_plan_upload(p.handle, None) == tnc.TNC_ESTATE  # refused before any CUDA call
+    # a compilable network: tree_only reports the same tree cost as the full plan
+    small = tnc.Network(C.random_2d(4, 4, 8, 1))
+    full = tnc.Plan(small, max_batch=16).report
+    only = tnc.Plan(small, max_batch=16, tree_only=True).report
+    assert abs(full["tree_cost_log2"] - only["tree_cost_log2"]) < 1e-9
 
 
 def test_invalid_planner_options():
