@@ -1610,6 +1610,10 @@ int run_tc(const GemmDesc& d, const float2* A, const float2* B, float* C, uint8_
 // (checked again below); the scratch holds the four planes.
 int launch_tc_gemm(const GemmDesc& d, const float2* A, const float2* B, float2* C, void* scratch_ptr,
                    cudaStream_t st) {
+  // every epilogue may store 16 bytes at a time (plain layouts, column pairs):
+  // the output must be 16-byte aligned (the plans' workspace offsets are
+  // 256-byte aligned; a caller's misaligned buffer is refused, not faulted)
+  if ((uintptr_t)C & 15) return (int)cudaErrorInvalidValue;
   // the persistent plane tiles (9, 10) also take short K (a power of two
   // >= 4): TMA fills the k-block beyond the plane rows with zeros
   const bool short_k = (((d.tile >= 9 && d.tile <= 12) || (d.tile == 13 && d.K >= 16)) && d.K >= 4 && d.K < 32 &&
