@@ -119,3 +119,18 @@ def test_fuse_diagonal_keeps_the_circuit(seed):
                        atol=1e-14)
     with pytest.raises(ValueError):
         C.fuse_diagonal(C.random_2d(2, 2, 2, 0))
+
+
+def test_op_count_trees_beyond_the_executor():
+    """The op-count curves cost the separator tree of c = <0|U^dagger P U|0>
+    with projectors on every qubit for the paper's IQP family up to L = 8,
+    whose largest intermediates exceed the executor's 48 binary indices: a
+    tree-only plan gives the tree, with the fused circuit far cheaper than the
+    gate-by-gate one and both below left-to-right contraction."""
+    gl = C.iqp_paper(8, 0)
+    ops = C.projector_ops(range(gl.n_qubits), [0] * gl.n_qubits)
+    full = tnc.Plan(tnc.Network(C.doubled(gl, ops)), seed=1, tree_only=True).report
+    fused = tnc.Plan(tnc.Network(C.doubled(C.fuse_diagonal(gl), ops)), seed=1, tree_only=True).report
+    assert full["max_rank"] > 48
+    b = tnc.Network(gl).bounds()
+    assert fused["tree_cost_log2"] + 40 < full["tree_cost_log2"] < b["sidewise_log2"]
