@@ -211,7 +211,9 @@ def load_network(gatelist) -> Network:
 
 
 class Plan:
-    """``tnc_plan``: separator tree, slicing and compiled program."""
+    """``tnc_plan``: separator tree, slicing and compiled program (options as
+    in ``tnc_plan_opts``; ``tree_only``: the tree and its Eq. 3 cost only, for
+    cost studies of networks the executor cannot run)."""
 
     def __init__(self, net: Network, open_qubits=(), max_batch: int = 1, mem_cap_bytes: int = 0,
                  form: str = "fp32", seed: int = 1, ssa_trials: int = 32, leaf_size: int = 8,
